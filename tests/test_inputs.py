@@ -1,0 +1,44 @@
+"""The seeded input generators: determinism, independence of chunking, properties."""
+import numpy as np
+
+import coulomb_inputs as ci
+
+
+def test_splitmix_reference_values():
+    # SplitMix64 seeded with 0: first outputs of the published generator
+    key = 0
+    got = [int(x) for x in ci.draw(key, np.arange(3, dtype=np.uint64))]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_quads_conserving_and_chunk_independent():
+    R = 5
+    B = ci.sphere_vectors(R)
+    q = ci.quads(R, 0, 3000)
+    v = B[q]
+    assert np.all(v[:, 1] - v[:, 0] + v[:, 3] - v[:, 2] == 0)
+    assert q.min() >= 0 and q.max() < len(B)
+    a = ci.quads(R, 1000, 500)
+    assert np.array_equal(a, q[1000:1500])
+    assert np.array_equal(ci.quads(R, 0, 3000), q)
+    # ids are spread over the whole basis
+    assert len(np.unique(q[:, 0])) > 0.9 * len(B)
+
+
+def test_planted_fractions():
+    q = ci.quads(6, 0, 40000, stream=ci.STREAM_PLANTED)
+    B = ci.sphere_vectors(6)
+    v = B[q]
+    nonc = np.any(v[:, 1] - v[:, 0] + v[:, 3] - v[:, 2] != 0, axis=1)
+    same = np.all(v[:, 1] == v[:, 0], axis=1)
+    assert 0.04 < nonc.mean() < 0.06
+    assert 0.008 < same.mean() < 0.013
+
+
+def test_box_params_ranges():
+    boxes = ci.box_params(256)
+    assert len(boxes) == 256
+    for b in boxes:
+        assert 4 <= b["R"] <= 24 and 8 <= b["L"] < 30 and 16 <= b["S"] <= 96
+        assert 1 <= b["R_F"] <= b["R"]
+    assert ci.box_params(3) == boxes[:3]
