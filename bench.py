@@ -1,0 +1,363 @@
+"""Benchmark of the compressed Coulomb-integral engine on one GB300 (one JSON line).
+
+Workload (the paper's 9171-planewave scale): cutoff |n| <= 13 (Nb = 9171 planewaves),
+L = 20 bohr, 64 quadrature nodes (58 kept), Fermi radius 8 (Mocc = 2109).  One step is
+one pass of the whole hot path over one batch of synthetic input:
+  1. reconstruct 1e8 seeded momentum-conserving quadruples (IJ|KL)  (16 B in, 4 B out each)
+  2. all Nb^2 = 8.41e7 exchange-type pair integrals V(k_i - k_j)
+  3. exchange sums eps(k) on the (2R+1)^3 grid and E_x by Toeplitz mode products
+     (plain FP32 path; mixed bf16x3 path as well when --mixed), FP64 E_x reduction.
+metric value = Coulomb evaluations per second = (1e8 + Nb^2 + Nb * Mocc) / step time,
+the exchange counted as the Nb * Mocc pair evaluations its sums replace.
+Inputs (1.6 GB of quadruples) are larger than L2 (129 MB), so no flush is needed.
+
+--impl reference times the FP64 CPU oracle (the slow, plainly correct restatement of the
+paper) on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R, L, S, R_F = 13, 20.0, 64, 8
+N_QUADS = 100_000_000
+METRIC = "pair-Coulomb evals/s and integrals/s on 1 GB300, mixed vs FP32 at <=1e-4 rel err"
+UNIT = "Coulomb evals/s"
+WORKLOAD = ("paper scale: |n|<=13 (9171 planewaves), L=20 bohr, 64 nodes, R_F=8 (2109 occ); "
+            "1e8 conserving quadruples + all 9171^2 pairs + exchange sums")
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.p = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    Nb, Mg = t.info["Nb"], t.info["Mg"]
+    Mocc = 2109
+    n = args.quads
+    # every rank owns its own slice of the quadruple stream (weak scaling, no collective)
+    q = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    ci.quads_device(R, rank * n, n, q)
+    vals = torch.empty(n, dtype=torch.float32, device=dev)
+    pairs = torch.empty((Nb, Nb), dtype=torch.float32, device=dev)
+    eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+    eps_mx = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+    Ex = torch.empty(2, dtype=torch.float64, device=dev)
+    Ex_mx = torch.empty(2, dtype=torch.float64, device=dev)
+    lookup = args.lookup
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+
+    def step(k=None):
+        if k is not None:
+            ev[k][0].record(st)
+        cc.reconstruct_integrals(t, q, vals, lookup=lookup)
+        if k is not None:
+            ev[k][1].record(st)
+        cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup)
+        cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")
+        if args.mixed:
+            cc.exchange_sums(t, R_F, eps_mx, Ex_mx, precision="bf16x3")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for k in range(args.steps):
+        step(k)
+    t1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    k_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    if world > 1:
+        v = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        ms = float(v.item())
+
+    # per-part timing (outside the timed region; for the breakdown only)
+    def time_it(fn, reps=5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        fn()
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    parts = {
+        "reconstruct_ms": k_ms,
+        "pairs_ms": time_it(lambda: cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup)),
+        "exchange_fp32_ms": time_it(lambda: cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")),
+    }
+    other = "separable" if lookup == "collapsed" else "collapsed"
+    parts[f"reconstruct_{other}_ms"] = time_it(
+        lambda: cc.reconstruct_integrals(t, q, vals, lookup=other))
+    if args.mixed:
+        parts["exchange_bf16x3_ms"] = time_it(
+            lambda: cc.exchange_sums(t, R_F, eps_mx, Ex_mx, precision="bf16x3"))
+
+    evals = n + Nb * Nb + Nb * Mocc
+    value = world * evals / (ms * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        hq = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+        hq.copy_(q.cpu())
+        hv = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        hp = torch.empty((Nb, Nb), dtype=torch.float32, pin_memory=True)
+        he = torch.empty(Mg ** 3, dtype=torch.float32, pin_memory=True)
+        hx = torch.empty(2, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            q.copy_(hq, non_blocking=True)
+            cc.reconstruct_integrals(t, q, vals, lookup=lookup)
+            cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup)
+            cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")
+            hv.copy_(vals, non_blocking=True)
+            hp.copy_(pairs, non_blocking=True)
+            he.copy_(eps, non_blocking=True)
+            hx.copy_(Ex, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ks = max(2, min(args.steps, 5))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(ks):
+            e2e_step()
+        b.record(st)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / ks
+        if world > 1:
+            v = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            ems = float(v.item())
+        e2e = {"value": world * evals / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(n * 16),
+               "d2h_bytes_per_step": int(n * 4 + Nb * Nb * 4 + Mg ** 3 * 4 + 16),
+               "ms_per_step": ems}
+
+    peak, peak_kind = _peaks()
+    if lookup == "collapsed":
+        algo_bytes = 20.0 * n          # 16 B quadruple in, 4 B value out
+        achieved = algo_bytes / (k_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_col",
+                    "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind}
+    else:
+        algo_bytes = 20.0 * n
+        achieved = algo_bytes / (k_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_sep",
+                    "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind}
+
+    n_launch = 2 + 8 + (args.mixed_launches if args.mixed else 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64 quadruples; shell-closed Fermi sphere)",
+        "config": {"workload": WORKLOAD, "R": R, "L_bohr": L, "S": S,
+                   "S_eff": t.info["S_eff"], "R_F": R_F, "Nb": Nb, "Mocc": Mocc,
+                   "quadruples": n, "pairs": Nb * Nb, "lookup": lookup,
+                   "evals_per_step": evals, "l2_policy": "inputs larger than L2 (1.6 GB)",
+                   "parallelism": f"replicas x{world} (independent quadruple slices)"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": n_launch * args.steps,
+        "clocks": clk, "breakdown": parts,
+        "rates": {"integrals_per_s": n / (k_ms * 1e-3),
+                  "pairs_per_s": Nb * Nb / (parts["pairs_ms"] * 1e-3)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    t.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------- oracle
+def oracle_sample(budget_s: float):
+    """Run the FP64 oracle on a bounded sample of the workload; returns (evals, seconds,
+    description)."""
+    import coulomb_inputs as ci
+    from oracle import exchange as ox
+    from oracle import quadrature as oq
+    from oracle import reconstruct as orc
+    n_sub, q_tail = oq.default_periodic_mesh(S, R)
+    a, w, _ = oq.laplace_mesh(S, n_sub, q_tail)
+    keep = oq.prune_periodic(a, w, R, 1e-9)
+    a, w = a[keep], w[keep]
+    Nb, Mocc = 9171, 2109
+    nq, rows, nk = 0, 0, 0
+    chunk_q, chunk_r, chunk_k = 200_000, 20, 64
+    t0 = time.perf_counter()
+    # the same mix as a GPU step: quadruples : pairs : exchange = 1e8 : Nb^2 : Nb Mocc
+    while time.perf_counter() - t0 < budget_s:
+        q = ci.quads(R, nq, chunk_q)
+        orc.reconstruct(q, R, L, "separable", a=a, w=w)
+        nq += chunk_q
+        orc.pair_matrix(R, L, rows=np.arange(rows, rows + chunk_r) % Nb, value="separable", a=a, w=w)
+        rows += chunk_r
+        ox.eps_separable(R, R_F, L, a, w, k_idx=np.arange(nk, nk + chunk_k) % Nb)
+        nk += chunk_k
+    dt = time.perf_counter() - t0
+    evals = nq + rows * Nb + nk * Mocc
+    desc = (f"{nq} quadruples + {rows} pair rows x {Nb} + eps at {nk} k x {Mocc} occupied, "
+            f"FP64 numpy node sums (oracle as it stands), single thread")
+    return evals, dt, desc
+
+
+def cpu_baseline(seconds=12.0):
+    evals, dt, desc = oracle_sample(seconds)
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+            "seconds": dt, "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(0.2)
+    tot_e, tot_t, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        e, dt, desc = oracle_sample(args.ref_seconds)
+        tot_e += e
+        tot_t += dt
+    v = tot_e / tot_t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 quadruples; shell-closed Fermi sphere)",
+            "config": {"workload": WORKLOAD, "R": R, "L_bohr": L, "S": S, "R_F": R_F,
+                       "lookup": "separable", "parallelism": "oracle, rank 0 only"},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": desc, "value": v,
+                             "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--lookup", default="collapsed", choices=["collapsed", "separable"])
+    ap.add_argument("--quads", type=int, default=N_QUADS)
+    ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--mixed-launches", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=2.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

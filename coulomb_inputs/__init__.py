@@ -15,7 +15,7 @@ All randomness is counter-based SplitMix64 (Steele, Lea and Flood, "Fast splitta
 pseudorandom number generators", OOPSLA 2014): output number c of a generator started at
 state k is mix64(k + (c + 1) * GAMMA).  Every draw is a pure function of
 (seed, stream, counter), so any quadruple can be regenerated on its own, on the host or
-on the device (the CUDA twin lives in coulomb_inputs_gen.cu and is tested for bit
+on the device (the CUDA twin lives in coulomb_inputs/gen.cu and is tested for bit
 equality against this file).
 """
 from __future__ import annotations
@@ -94,8 +94,10 @@ def cube_id_map(R: int, vec: np.ndarray) -> np.ndarray:
 
 
 def quads(R: int, start: int, count: int, seed: int = SEED, stream: int = STREAM_CLEAN,
-          vec: np.ndarray | None = None, idmap: np.ndarray | None = None) -> np.ndarray:
-    """Quadruples number start .. start+count-1 of `stream`, as int32[count, 4] ids.
+          vec: np.ndarray | None = None, idmap: np.ndarray | None = None,
+          indices=None) -> np.ndarray:
+    """Quadruples number start .. start+count-1 of `stream` (or the quadruple numbers in
+    `indices`, when given), as int32[count, 4] ids.
 
     Quadruple i, attempt a, component c (0: I, 1: J, 2: K, 3: planting) uses counter
     (i * ATTEMPTS + a) * 4 + c.  I, J, K are uniform ids; L is the id of
@@ -108,7 +110,11 @@ def quads(R: int, start: int, count: int, seed: int = SEED, stream: int = STREAM
     Nb = len(vec)
     G = 2 * R + 1
     key = stream_key(seed, stream)
-    i = np.arange(start, start + count, dtype=np.uint64)
+    if indices is not None:
+        i = np.asarray(indices, dtype=np.uint64)
+        count = len(i)
+    else:
+        i = np.arange(start, start + count, dtype=np.uint64)
     out = np.empty((count, 4), dtype=np.int32)
     done = np.zeros(count, dtype=bool)
     first = None
@@ -177,3 +183,50 @@ def box_params(nbox: int = 256, seed: int = SEED):
         S = 16 + int(np.floor(81 * u[3]))
         boxes.append({"R": R, "L": L, "R_F": RF, "S": S})
     return boxes
+
+
+# --------------------------------------------------------------------------------------
+# device twin (coulomb_inputs/gen.cu -> libccgen.so): same quadruples, generated on the GPU
+# --------------------------------------------------------------------------------------
+_GEN_LIB = None
+_GEN_TABLES = {}
+
+
+def _gen_lib():
+    global _GEN_LIB
+    if _GEN_LIB is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libccgen.so")
+        if not os.path.exists(path):
+            raise ImportError("coulomb_inputs/libccgen.so is not built (run the package build)")
+        L = ctypes.CDLL(path)
+        P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+        L.ccgen_quads.restype = I
+        L.ccgen_quads.argtypes = [I, I, P, P, ctypes.c_ulonglong, LL, LL, I, P, P]
+        _GEN_LIB = L
+    return _GEN_LIB
+
+
+def quads_device(R: int, start: int, count: int, out, seed: int = SEED,
+                 stream: int = STREAM_CLEAN, cuda_stream=None):
+    """Fill the int32[count, 4] CUDA tensor `out` with quadruples start .. start+count-1,
+    bit-identical to quads(R, start, count, seed, stream)."""
+    import torch
+    dev = out.device
+    key_t = (R, dev.index)
+    if key_t not in _GEN_TABLES:
+        vec = sphere_vectors(R)
+        v4 = np.zeros((len(vec), 4), dtype=np.int8)
+        v4[:, :3] = vec
+        _GEN_TABLES[key_t] = (torch.from_numpy(v4).to(dev), torch.from_numpy(cube_id_map(R, vec)).to(dev),
+                              len(vec))
+    v4, idm, Nb = _GEN_TABLES[key_t]
+    assert out.dtype == torch.int32 and out.is_contiguous() and out.shape[0] >= count
+    s = torch.cuda.current_stream(dev).cuda_stream if cuda_stream is None else cuda_stream
+    rc = _gen_lib().ccgen_quads(R, Nb, v4.data_ptr(), idm.data_ptr(), stream_key(seed, stream),
+                                start, count, 1 if stream == STREAM_PLANTED else 0,
+                                out.data_ptr(), s)
+    if rc != 0:
+        raise RuntimeError(f"ccgen_quads failed ({rc})")
+    return out

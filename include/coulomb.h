@@ -1,0 +1,197 @@
+/*
+ * coulomb.h -- C ABI of the compressed Coulomb-integral engine for planewave bases
+ * (Pederson, "Practical and Rigorous Reduction of the Many-Electron Quantum Mechanical
+ * Coulomb Problem to O(N^{2/3}) Storage", arXiv:1502.08043).
+ *
+ * The Coulomb kernel is factorised through a Laplace transform (Sec. II, Eqs. 3-7), the
+ * change of variable t = alpha^{-1/2} for the infinite interval (Eq. 11) and Gauss
+ * quadrature (Eqs. 12-14) into S one-dimensional tables T_s[Delta] with weights w_s, so
+ * that every two-electron integral is rebuilt from O(N^{2/3}) numbers (Sec. III).
+ *
+ * Conventions shared by every entry point
+ *  - Units: Hartree atomic units; box side L in bohr.
+ *  - Basis: integer vectors n with |n|^2 <= R^2 (planewaves exp(i 2 pi n.r / L)),
+ *    lexicographic (n_x, n_y, n_z) order; the id of a function is its rank.
+ *  - Integrals are chemists' (IJ|KL) with complex conjugates on I and K:
+ *    nonzero only if n_J - n_I + n_L - n_K = 0, then V(q), q = n_J - n_I.
+ *  - Kernels: CC_KERNEL_PERIODIC, V(q) = 4 pi / (Omega |q|^2) = 1/(pi L |n|^2), with the
+ *    q = 0 term excluded (returned as 0).  CC_KERNEL_BOX, the free-space Coulomb kernel
+ *    inside a finite box of side L (the model of the paper's Table I); q = 0 included.
+ *  - Memory: every pointer named *_dev is device memory owned by the caller; *_host is
+ *    host memory owned by the caller.  Tables are owned by the library behind the
+ *    opaque handle.  No hot call (reconstruct, pair matrix, exchange) allocates.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Hot calls are asynchronous and stream ordered; argument errors are
+ *    returned synchronously before anything is enqueued.  Build, info, save, load and
+ *    free synchronise.
+ *  - Errors: every function returns a cc_status; no C++ exception crosses the ABI, no
+ *    device trap or assert is used.  Data-dependent problems found on the device
+ *    (out-of-range ids) are counted in caller-provided counters, never fatal.
+ *  - Threading: a handle is immutable after build and may be used from several host
+ *    threads at once for different calls on different streams, except that two calls
+ *    of cc_exchange_sums on one handle share its workspace and must be stream ordered.
+ */
+#ifndef COULOMB_H_
+#define COULOMB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CC_OK = 0,
+  CC_ERR_ARG = 1,      /* invalid argument (NULL pointer, size, enum) */
+  CC_ERR_RANGE = 2,    /* size beyond a documented limit */
+  CC_ERR_CUDA = 3,     /* a CUDA runtime call failed (message: cc_last_error) */
+  CC_ERR_ALLOC = 4,    /* device or host allocation failed */
+  CC_ERR_TIMEOUT = 5,  /* a bounded device wait ran out */
+  CC_ERR_NOTSUPP = 6,  /* valid but unsupported combination */
+  CC_ERR_IO = 7        /* file read/write or format error */
+} cc_status;
+
+typedef enum { CC_KERNEL_PERIODIC = 0, CC_KERNEL_BOX = 1 } cc_kernel;
+
+typedef enum {
+  CC_PREC_FP64 = 0,    /* double tables, double outputs */
+  CC_PREC_FP32 = 1,    /* float tables, float outputs (plain FP32 path) */
+  CC_PREC_BF16X3 = 2,  /* exchange only: bf16 hi+lo split operands on tensor cores */
+  CC_PREC_FP16X3 = 3   /* exchange only: fp16 hi+lo split with per-node exponent scaling */
+} cc_precision;
+
+typedef enum {
+  CC_LOOKUP_SEPARABLE = 0, /* Eq. 14 node sum: sum_s w_s T_s[q_x] T_s[q_y] T_s[q_z] */
+  CC_LOOKUP_COLLAPSED = 1  /* periodic only: one table over m = |q|^2 (node sum folded) */
+} cc_lookup;
+
+typedef enum {
+  CC_QUAD_IDS_I32 = 0, /* int32[n][4] basis ids (I, J, K, L) */
+  CC_QUAD_VEC_I8X4 = 1 /* int8[n][4][4]: the four vectors (n_x, n_y, n_z, unused) */
+} cc_quad_format;
+
+/* Quadrature and table parameters (Sec. II Eqs. 11-14 and the Table I meshes).
+ *   kernel    cc_kernel.
+ *   R         basis cutoff |n|^2 <= R^2, 1 <= R <= 127.  Tables cover Delta = 0..2R.
+ *   L         box side (bohr), > 0.
+ *   S         total number of quadrature nodes, 2 <= S <= 1024.
+ *   n_sub     interval [0, alpha_c] is split at alpha_c 5^-n_sub, ..., alpha_c/5
+ *             (n_sub + 1 Gauss-Legendre sub-intervals; 0 = one interval, the paper's
+ *             Mesh 1; 7 = the paper's Mesh 2).  < 0 selects the default rule.
+ *   q_tail    Gauss-Legendre points in t = alpha^{-1/2} on (0, alpha_c^{-1/2}] (Eq. 11);
+ *             < 0 selects the default rule.
+ *   alpha_c   split point (Sec. II fixes alpha_c = 1).  PERIODIC: in index units
+ *             a = alpha (2 pi / L)^2; BOX: in bohr^2.  <= 0 selects 1.
+ *   prune_tol PERIODIC only: drop node s when w_s exp(-a_s) < prune_tol / (12 R^2);
+ *             0 keeps all nodes.  Negative selects 1e-9.  Ignored for BOX.
+ * Default rule: (S, R) = (32, 4) -> (2, 10); (64, 13) -> (3, 21); (96, 31) -> (4, 29);
+ * (128, 63) -> (5, 34); otherwise n_sub = max(1, floor(log5(12 R^2)) - 1) and
+ * q_tail = round(0.3 S).  Every sub-interval gets floor((S - q_tail)/(n_sub + 1))
+ * points and the first (S - q_tail) mod (n_sub + 1) get one more. */
+typedef struct {
+  int kernel;
+  int R;
+  double L;
+  int S;
+  int n_sub;
+  int q_tail;
+  double alpha_c;
+  double prune_tol;
+} cc_table_params;
+
+typedef struct cc_tables_s* cc_tables;
+
+typedef struct {
+  int kernel, R, S, n_sub, q_tail;
+  double L, alpha_c, prune_tol;
+  int S_eff;          /* nodes kept after pruning */
+  int Nb;             /* basis size */
+  int Mg;             /* grid side 2R + 1 */
+  int m_max;          /* collapsed table covers m = 0..m_max = 4 R^2 */
+  size_t device_bytes; /* device memory held by the handle (tables + workspace) */
+  size_t table_bytes;  /* of which the FP32 lookup tables (the stored compression) */
+} cc_tables_info_t;
+
+/* Build the node set, weights and tables on the device of the current context
+ * (Sec. II Eqs. 11-14; nodes, weights and table entries in FP64 on the GPU).  Also
+ * allocates the exchange workspace of this cutoff.  Synchronous.
+ * Errors: CC_ERR_ARG / CC_ERR_RANGE for bad parameters, CC_ERR_ALLOC, CC_ERR_CUDA. */
+cc_status cc_build_tables(const cc_table_params* params, void* stream, cc_tables* out);
+
+/* Sizes and resolved parameters of a handle. */
+cc_status cc_tables_info(cc_tables t, cc_tables_info_t* info);
+
+/* Copy the full node set (before pruning) to the host: alpha[S], w[S] (Laplace
+ * variable of the kernel's units and Eq. 14 weights), part[S] (0: [0, alpha_c],
+ * 1: tail), kept[S] (1 if the node survives pruning).  Any pointer may be NULL. */
+cc_status cc_tables_nodes(cc_tables t, double* alpha_host, double* w_host, int* part_host,
+                          int* kept_host);
+
+/* Copy the FP64 per-node tables of the kept nodes to the host:
+ * table_host[S_eff][2R + 1] = T_s[Delta] (PERIODIC exp(-a_s Delta^2), BOX A(alpha_s, Delta)). */
+cc_status cc_tables_values(cc_tables t, double* table_host);
+
+/* Checkpoint: write / read the node set and the FP64 tables (the "stored forever"
+ * table of Sec. II) to a flat versioned file with a checksum.  Load rebuilds the
+ * derived device tables on the current device.  CC_ERR_IO on a bad file. */
+cc_status cc_tables_save(cc_tables t, const char* path);
+cc_status cc_tables_load(const char* path, void* stream, cc_tables* out);
+
+cc_status cc_tables_free(cc_tables t);
+
+/* Basis of cutoff R (Sec. II Eq. 1 with |n|^2 <= R^2) in canonical order.  Writes the
+ * count to *Nb; if vec_host is not NULL it must hold 4 * Nb int8 and receives
+ * (n_x, n_y, n_z, 0) per function.  1 <= R <= 127. */
+cc_status cc_basis(int R, int* Nb, int8_t* vec_host);
+
+/* Reconstruct (IJ|KL) for n quadruples (Sec. II Eq. 14; momentum conservation Sec. III).
+ *   quads_dev     n quadruples in `format`, 16 bytes each, 16-byte aligned.
+ *   lookup        CC_LOOKUP_SEPARABLE (any kernel) or CC_LOOKUP_COLLAPSED (PERIODIC).
+ *   precision     CC_PREC_FP32 (out float[n]) or CC_PREC_FP64 (out double[n]).
+ *   counters_dev  NULL or unsigned long long[3], ADDED to (not cleared):
+ *                 [0] non-conserving quadruples, [1] periodic q = 0 (excluded) terms,
+ *                 [2] ids outside [0, Nb) or vectors outside the cutoff sphere.
+ *                 Each of these quadruples gets the value 0.
+ *   BOX kernel: only momentum-conserving quadruples are represented by the per-axis
+ *   tables; non-conserving ones get 0 and are counted in [0].
+ * n may be 0.  Errors: CC_ERR_ARG, CC_ERR_NOTSUPP (collapsed BOX, mixed precision). */
+cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n, int format,
+                                   int lookup, int precision, void* out_dev,
+                                   unsigned long long* counters_dev, void* stream);
+
+/* Exchange-type pair integrals (ij|ji) = V(n_j - n_i) for basis rows
+ * i = row0 .. row0 + nrows - 1 and every column j:  out_dev[nrows][Nb] (float or double
+ * by precision), row major.  Diagonal of the PERIODIC kernel: 0 (q = 0 excluded). */
+cc_status cc_pair_matrix(cc_tables t, int64_t row0, int64_t nrows, int lookup, int precision,
+                         void* out_dev, void* stream);
+
+/* Exchange sums of the uniform electron gas (Sec. III):
+ *   eps(k) = -sum_{j in F} V(k - n_j) on the (2R+1)^3 grid k in [-R, R]^3, row major
+ *   [k_x + R][k_y + R][k_z + R], 0 outside the basis sphere |k| <= R.  F is the Fermi
+ *   sphere |n| <= R_F (1 <= R_F <= R).  PERIODIC excludes j = k, BOX includes it.
+ *   Computed as mode products of the occupation tensor with the Toeplitz matrices
+ *   T_s[a][b] = T_s[|a - b|] along x, y and z, accumulated over the nodes s.
+ *   Ex_dev[0] = E_x^sigma = 1/2 sum_{k in F} eps(k) (per spin, FP64 reduction),
+ *   Ex_dev[1] = 2 E_x^sigma (unpolarised total).
+ *   precision: CC_PREC_FP64 / CC_PREC_FP32 (eps double / float, SIMT), CC_PREC_BF16X3 /
+ *   CC_PREC_FP16X3 (eps float, tcgen05 tensor cores).  Uses the handle's workspace:
+ *   calls on one handle must not overlap on the GPU. */
+cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, double* Ex_dev,
+                           void* stream);
+
+/* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
+ * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the
+ * products with an Mg^2-long side, each 0 = 64x64, 1 = 32x32, 2 = 64x32 outputs per CTA;
+ * threshold = grid side up to which 32x32 tiles are always used (< 0 keeps it).
+ * Process-wide setting; not part of the paper (a tuning knob of this implementation). */
+cc_status cc_set_gemm_tiles(int precision, int small_tile, int large_tile, int threshold);
+
+/* Human-readable name of a status; detail of the last CUDA failure of this thread. */
+const char* cc_status_string(cc_status s);
+const char* cc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COULOMB_H_ */

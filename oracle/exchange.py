@@ -45,11 +45,14 @@ def eps_exact(R: int, R_F: int, L: float, k_idx=None, chunk: int = 256):
     return _pairs(R, R_F, k_idx, chunk, lambda d: V_exact(d, L))
 
 
-def eps_separable(R: int, R_F: int, L: float, a, w, k_idx=None, chunk: int = 64):
-    """Same sum with V replaced by its Eq. 14 node sum (j = k still excluded)."""
+def eps_separable(R: int, R_F: int, L: float, a, w, k_idx=None, chunk: int = 256):
+    """Same sum with V replaced by its Eq. 14 node sum (j = k still excluded).  The node
+    sum is evaluated once for every integer m = |k - n_j|^2 that can occur and indexed."""
+    m_all = np.arange((R + R_F) ** 2 * 3 + 1)
+    Vm = V_of_m_separable(m_all, L, a, w)
+
     def val(d):
-        m = (d * d).sum(axis=-1)
-        return V_of_m_separable(m, L, a, w)
+        return Vm[(d * d).sum(axis=-1)]
     return _pairs(R, R_F, k_idx, chunk, val)
 
 
@@ -120,7 +123,8 @@ def Ex_separable_periodic(R_F: int, L: float, a, w, C=None) -> float:
     r, C = _hist_vectors(C)
     m = r[:, None, None] ** 2 + r[None, :, None] ** 2 + r[None, None, :] ** 2
     nz = m > 0
-    return -0.5 * float((C[nz] * V_of_m_separable(m[nz], L, a, w)).sum())
+    Vm = V_of_m_separable(np.arange(int(m.max()) + 1), L, a, w)
+    return -0.5 * float((C[nz] * Vm[m[nz]]).sum())
 
 
 def Ex_box(R_F: int, L: float, alpha, omega, C=None, table=None) -> float:

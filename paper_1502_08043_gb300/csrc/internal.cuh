@@ -1,0 +1,102 @@
+// Internal declarations shared by the translation units of libcoulomb.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "coulomb.h"
+
+namespace cc {
+
+// ---------------------------------------------------------------- error plumbing
+void set_last_error(const char* what, cudaError_t e);
+
+#define CC_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      ::cc::set_last_error(#call, e_);                 \
+      return CC_ERR_CUDA;                              \
+    }                                                  \
+  } while (0)
+
+#define CC_TRY(call)                  \
+  do {                                \
+    cc_status s_ = (call);            \
+    if (s_ != CC_OK) return s_;       \
+  } while (0)
+
+// limits
+constexpr int kMaxR = 127;          // Delta = 0..254 fits the 8-bit packed deltas
+constexpr int kMaxS = 1024;
+constexpr int kBoxGLPoints = 1200;  // Gauss-Legendre points of one box axis integral
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device buffers owned by a table handle.  All tables are for the kept nodes only.
+struct DevTables {
+  double* T64 = nullptr;      // [S_eff][Dmax+1]  T_s[Delta]
+  double* w64 = nullptr;      // [S_eff]
+  double* a64 = nullptr;      // [S_eff]
+  double* sep64 = nullptr;    // [Dmax+1][S_pad]  cbrt(pref w_s) T_s[Delta], 0 padded
+  float* sep32 = nullptr;     // same, FP32
+  double* Vm64 = nullptr;     // [m_max+1] collapsed pref sum_s w_s exp(-a_s m) (PERIODIC)
+  float* Vm32 = nullptr;
+  int8_t* basis = nullptr;    // [Nb][4]
+  // dense Mg x Mg Toeplitz matrices for the mode products
+  double* Tm64 = nullptr;     // [S_eff][Mg][Mg]  T_s[|a-b|]
+  double* WDm64 = nullptr;    // [S_eff][Mg][Mg]  w_s D_s (D = T - I periodic, T box)
+  double* Dbar64 = nullptr;   // [Mg][Mg] sum_s w_s D_s (periodic)
+  float* Tm32 = nullptr;
+  float* WDm32 = nullptr;
+  float* Dbar32 = nullptr;
+};
+
+// Exchange workspace (allocated with the handle; a chunk of nodes at a time).
+struct Workspace {
+  int chunk = 0;              // nodes per chunk
+  void* occ = nullptr;        // [Mg^3] occupation tensor (float or double, by call)
+  void* P = nullptr;          // [chunk][Mg^3]
+  void* Q = nullptr;          // [chunk][Mg^3]
+  void* E = nullptr;          // [Mg^3] accumulator
+  double* part = nullptr;     // [kRedBlocks] FP64 partial sums of E_x
+  size_t bytes = 0;
+  // mixed-precision (tensor core) workspace, see umma.cu
+  void* mx = nullptr;
+  size_t mx_bytes = 0;
+};
+
+constexpr int kRedBlocks = 608;
+
+}  // namespace cc
+
+struct cc_tables_s {
+  cc_table_params p;          // resolved parameters
+  int device = 0;
+  int S = 0, S_eff = 0, S_pad = 0, Nb = 0, Mg = 0, Dmax = 0, m_max = 0;
+  double pref = 0.0;          // 1/(pi L) periodic, 1/(2 pi^2) box
+  std::vector<double> alpha, w;   // full node set (host copy)
+  std::vector<int> part, kept;    // part: 0 interval 1, 1 tail; kept flags
+  std::vector<int> kept_idx;      // indices of kept nodes
+  cc::DevTables d;
+  cc::Workspace ws;
+  size_t table_bytes = 0;
+  size_t device_bytes = 0;
+};
+
+namespace cc {
+// tables.cu
+cc_status resolve_params(const cc_table_params* in, cc_table_params* out);
+void default_mesh(int S, int R, int* n_sub, int* q_tail);
+std::vector<int8_t> make_basis(int R);
+// exchange.cu
+cc_status workspace_alloc(cc_tables t);
+void workspace_free(cc_tables t);
+// umma.cu
+cc_status mixed_workspace_alloc(cc_tables t);
+void mixed_workspace_free(cc_tables t);
+cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
+                         cudaStream_t st);
+}  // namespace cc

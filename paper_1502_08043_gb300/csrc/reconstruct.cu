@@ -1,0 +1,407 @@
+// K2: reconstruction of (IJ|KL) from the per-node tables (Sec. II Eq. 14) with the
+// momentum-conservation bookkeeping of planewaves (Sec. I and III: the product of two
+// planewaves is a planewave, so (IJ|KL) vanishes unless n_J - n_I + n_L - n_K = 0).
+//
+// SEPARABLE: V(q) = sum_s c_s T_s[|q_x|] c_s T_s[|q_y|] c_s T_s[|q_z|] with c_s^3 = pref w_s
+// folded into the table.  A warp takes 32 quadruples; lane l owns nodes l, l+32, ...;
+// for every quadruple all lanes read one table row segment (32 consecutive words: no
+// bank conflict), and a 31-shuffle butterfly transposes and sums the 32 x 32 partial
+// sums so that lane l ends with the total of quadruple l.
+// COLLAPSED (periodic kernel): prod_x exp(-a_s q_x^2) = exp(-a_s |q|^2), so the node sum
+// is a function of the integer m = |q|^2 <= 4 R^2 only; one table of 4R^2 + 1 values,
+// one shared-memory gather per integral; the kernel streams 16 B in and 4 B out.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace cc {
+
+constexpr unsigned kFull = 0xffffffffu;
+enum : int { kNonCons = 1, kQZero = 2, kRange = 4, kInvalid = 8 };
+
+__device__ __forceinline__ char4 as_c4(int v) {
+  char4 c;
+  c.x = (signed char)(v & 0xff);
+  c.y = (signed char)((v >> 8) & 0xff);
+  c.z = (signed char)((v >> 16) & 0xff);
+  c.w = (signed char)((v >> 24) & 0xff);
+  return c;
+}
+
+__device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+
+// q = n_J - n_I; conservation n_J - n_I + n_L - n_K == 0; flags; |q| per axis
+template <bool kPeriodic>
+__device__ __forceinline__ int classify(char4 a, char4 b, char4 c, char4 d, int& qx, int& qy,
+                                        int& qz) {
+  qx = (int)b.x - (int)a.x;
+  qy = (int)b.y - (int)a.y;
+  qz = (int)b.z - (int)a.z;
+  const bool cons = (qx + (int)d.x - (int)c.x) == 0 && (qy + (int)d.y - (int)c.y) == 0 &&
+                    (qz + (int)d.z - (int)c.z) == 0;
+  int f = 0;
+  if (!cons) f = kNonCons;
+  else if (kPeriodic && (qx | qy | qz) == 0) f = kQZero;
+  qx = abs(qx);
+  qy = abs(qy);
+  qz = abs(qz);
+  return f;
+}
+
+struct IdsSrc {
+  const int4* q;
+  const char4* basis;
+  int Nb;
+  template <bool kPeriodic>
+  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
+    const int4 v = ld_stream(q + i);
+    if ((unsigned)v.x >= (unsigned)Nb || (unsigned)v.y >= (unsigned)Nb ||
+        (unsigned)v.z >= (unsigned)Nb || (unsigned)v.w >= (unsigned)Nb) {
+      qx = qy = qz = 0;
+      return kRange;
+    }
+    return classify<kPeriodic>(basis[v.x], basis[v.y], basis[v.z], basis[v.w], qx, qy, qz);
+  }
+};
+
+struct VecSrc {
+  const int4* q;
+  const char4* basis;  // unused
+  int R2;
+  __device__ __forceinline__ static bool in_sphere(char4 a, int R2) {
+    return (int)a.x * a.x + (int)a.y * a.y + (int)a.z * a.z <= R2;
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
+    const int4 v = ld_stream(q + i);
+    const char4 a = as_c4(v.x), b = as_c4(v.y), c = as_c4(v.z), d = as_c4(v.w);
+    if (!in_sphere(a, R2) || !in_sphere(b, R2) || !in_sphere(c, R2) || !in_sphere(d, R2)) {
+      qx = qy = qz = 0;
+      return kRange;
+    }
+    return classify<kPeriodic>(a, b, c, d, qx, qy, qz);
+  }
+};
+
+// exchange-type pairs (ij|ji): item = row * Nb + col, q = n_col - n_row
+struct PairSrc {
+  const int4* q;  // unused
+  const char4* basis;
+  int Nb;
+  int64_t row0;
+  template <bool kPeriodic>
+  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
+    const int64_t r = row0 + i / Nb;
+    const int c = (int)(i % Nb);
+    const char4 a = basis[r], b = basis[c];
+    return classify<kPeriodic>(a, b, b, a, qx, qy, qz);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+__device__ __forceinline__ void flush_counts(unsigned long long* counters, unsigned c0,
+                                             unsigned c1, unsigned c2) {
+  if (!counters) return;
+  if (c0) atomicAdd(counters + 0, (unsigned long long)c0);
+  if (c1) atomicAdd(counters + 1, (unsigned long long)c1);
+  if (c2) atomicAdd(counters + 2, (unsigned long long)c2);
+}
+
+// ---------------------------------------------------------------- separable kernel
+template <typename T, typename Src, bool kPeriodic>
+__global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __restrict__ gtab,
+                                             int Dmax, int S_pad, T* __restrict__ out,
+                                             unsigned long long* counters, int basis_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* tab = reinterpret_cast<T*>(smem);
+  const int tab_elems = (Dmax + 1) * S_pad;
+  for (int i = threadIdx.x; i < tab_elems; i += blockDim.x) tab[i] = gtab[i];
+  if (basis_smem > 0) {
+    const size_t off = ((size_t)tab_elems * sizeof(T) + 15) & ~(size_t)15;
+    char4* sb = reinterpret_cast<char4*>(smem + off);
+    for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
+    src.basis = sb;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nch = S_pad >> 5;
+  unsigned c0 = 0, c1 = 0, c2 = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * 32; base < n;
+       base += (int64_t)gridDim.x * nw * 32) {
+    const int64_t i = base + lane;
+    int qx = 0, qy = 0, qz = 0, flag = kInvalid;
+    if (i < n) flag = src.template decode<kPeriodic>(i, qx, qy, qz);
+    if (flag) qx = qy = qz = 0;
+    const unsigned pk = (unsigned)qx | ((unsigned)qy << 8) | ((unsigned)qz << 16);
+    c0 += __popc(__ballot_sync(kFull, flag == kNonCons));
+    c1 += __popc(__ballot_sync(kFull, flag == kQZero));
+    c2 += __popc(__ballot_sync(kFull, flag == kRange));
+    T acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const unsigned p = __shfl_sync(kFull, pk, k);
+      const T* rx = tab + (p & 255u) * S_pad + lane;
+      const T* ry = tab + ((p >> 8) & 255u) * S_pad + lane;
+      const T* rz = tab + ((p >> 16) & 255u) * S_pad + lane;
+      T a = T(0);
+      for (int c = 0; c < nch; ++c) a = fma_t(rx[c * 32] * ry[c * 32], rz[c * 32], a);
+      acc[k] = a;
+    }
+    // butterfly transpose-reduce: afterwards lane l holds the sum over lanes of acc[l]
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < o; ++j) {
+        const T send = up ? acc[j] : acc[j + o];
+        const T keep = up ? acc[j + o] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(kFull, send, o);
+      }
+    }
+    if (i < n) out[i] = flag ? T(0) : acc[0];
+  }
+  if (lane == 0) flush_counts(counters, c0, c1, c2);
+}
+
+// ---------------------------------------------------------------- collapsed kernel
+template <typename T, typename Src>
+__global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __restrict__ gVm,
+                                             int m_max, T* __restrict__ out,
+                                             unsigned long long* counters, int basis_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Vm = reinterpret_cast<T*>(smem);
+  for (int i = threadIdx.x; i <= m_max; i += blockDim.x) Vm[i] = gVm[i];
+  if (basis_smem > 0) {
+    const size_t off = ((size_t)(m_max + 1) * sizeof(T) + 15) & ~(size_t)15;
+    char4* sb = reinterpret_cast<char4*>(smem + off);
+    for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
+    src.basis = sb;
+  }
+  __syncthreads();
+  unsigned c0 = 0, c1 = 0, c2 = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = 4;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (U - 1) * stride < n; i += U * stride) {
+    int f[U], m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int qx, qy, qz;
+      f[u] = src.template decode<true>(i + u * stride, qx, qy, qz);
+      m[u] = qx * qx + qy * qy + qz * qz;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c0 += f[u] == kNonCons;
+      c1 += f[u] == kQZero;
+      c2 += f[u] == kRange;
+      __stcs(out + i + u * stride, f[u] ? T(0) : Vm[m[u]]);
+    }
+  }
+  for (; i < n; i += stride) {
+    int qx, qy, qz;
+    const int f = src.template decode<true>(i, qx, qy, qz);
+    c0 += f == kNonCons;
+    c1 += f == kQZero;
+    c2 += f == kRange;
+    __stcs(out + i, f ? T(0) : Vm[qx * qx + qy * qy + qz * qz]);
+  }
+  c0 = __reduce_add_sync(kFull, c0);
+  c1 = __reduce_add_sync(kFull, c1);
+  c2 = __reduce_add_sync(kFull, c2);
+  if ((threadIdx.x & 31) == 0) flush_counts(counters, c0, c1, c2);
+}
+
+// all-pairs, collapsed: out[r][j] = V_m[|n_j - n_{row0+r}|^2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_col(const char4* __restrict__ gbasis, int Nb,
+                                                  int64_t row0, int64_t nrows,
+                                                  const T* __restrict__ gVm, int m_max,
+                                                  T* __restrict__ out, int basis_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Vm = reinterpret_cast<T*>(smem);
+  for (int i = threadIdx.x; i <= m_max; i += blockDim.x) Vm[i] = gVm[i];
+  const char4* basis = gbasis;
+  if (basis_smem > 0) {
+    const size_t off = ((size_t)(m_max + 1) * sizeof(T) + 15) & ~(size_t)15;
+    char4* sb = reinterpret_cast<char4*>(smem + off);
+    for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = gbasis[i];
+    basis = sb;
+  }
+  __syncthreads();
+  for (int64_t r = blockIdx.y; r < nrows; r += gridDim.y) {
+    const char4 a = gbasis[row0 + r];
+    T* orow = out + r * (int64_t)Nb;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Nb; j += gridDim.x * blockDim.x) {
+      const char4 b = basis[j];
+      const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+      __stcs(orow + j, Vm[dx * dx + dy * dy + dz * dz]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launch helpers
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <typename K>
+static cc_status grid_for(K kernel, int threads, size_t smem, int64_t work_items, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) {
+    set_last_error("cudaFuncSetAttribute", e);
+    return CC_ERR_CUDA;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (e != cudaSuccess || per_sm <= 0) {
+    set_last_error("occupancy", e);
+    return CC_ERR_CUDA;
+  }
+  int64_t b = (int64_t)per_sm * num_sms();
+  const int64_t need = (work_items + threads - 1) / threads;
+  if (need < b) b = need < 1 ? 1 : need;
+  *blocks = (int)b;
+  return CC_OK;
+}
+
+static constexpr size_t kSmemCap = 200 * 1024;
+
+template <typename T, typename Src, bool kPeriodic>
+static cc_status launch_sep(cc_tables t, Src src, int64_t n, T* out,
+                            unsigned long long* counters, cudaStream_t st) {
+  const T* tab;
+  if constexpr (sizeof(T) == 4) tab = reinterpret_cast<const T*>(t->d.sep32);
+  else tab = reinterpret_cast<const T*>(t->d.sep64);
+  const size_t tb = (((size_t)(t->Dmax + 1) * t->S_pad * sizeof(T)) + 15) & ~(size_t)15;
+  if (tb > kSmemCap) return CC_ERR_RANGE;
+  int basis_smem = 0;
+  if (tb + (size_t)t->Nb * 4 <= 96 * 1024) basis_smem = t->Nb;
+  const size_t smem = tb + (size_t)basis_smem * 4;
+  auto kern = k_sep<T, Src, kPeriodic>;
+  int blocks = 0;
+  CC_TRY(grid_for(kern, 256, smem, (n + 7) / 8, &blocks));
+  kern<<<blocks, 256, smem, st>>>(src, n, tab, t->Dmax, t->S_pad, out, counters, basis_smem);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+template <typename T, typename Src>
+static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned long long* counters,
+                            cudaStream_t st, bool uses_basis) {
+  const T* Vm;
+  if constexpr (sizeof(T) == 4) Vm = reinterpret_cast<const T*>(t->d.Vm32);
+  else Vm = reinterpret_cast<const T*>(t->d.Vm64);
+  const size_t tb = (((size_t)(t->m_max + 1) * sizeof(T)) + 15) & ~(size_t)15;
+  if (tb > kSmemCap) return CC_ERR_RANGE;
+  int basis_smem = 0;
+  if (uses_basis && tb + (size_t)t->Nb * 4 <= 48 * 1024) basis_smem = t->Nb;
+  const size_t smem = tb + (size_t)basis_smem * 4;
+  auto kern = k_col<T, Src>;
+  int blocks = 0;
+  CC_TRY(grid_for(kern, 512, smem, (n + 3) / 4, &blocks));
+  kern<<<blocks, 512, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+template <typename T>
+static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int format, int lookup,
+                               T* out, unsigned long long* counters, cudaStream_t st) {
+  const bool periodic = t->p.kernel == CC_KERNEL_PERIODIC;
+  const char4* basis = reinterpret_cast<const char4*>(t->d.basis);
+  const int4* q = reinterpret_cast<const int4*>(quads);
+  if (lookup == CC_LOOKUP_COLLAPSED) {
+    if (format == CC_QUAD_IDS_I32) return launch_col<T>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st, true);
+    return launch_col<T>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st, false);
+  }
+  if (format == CC_QUAD_IDS_I32) {
+    if (periodic) return launch_sep<T, IdsSrc, true>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
+    return launch_sep<T, IdsSrc, false>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
+  }
+  if (periodic)
+    return launch_sep<T, VecSrc, true>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st);
+  return launch_sep<T, VecSrc, false>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st);
+}
+
+template <typename T>
+static cc_status pairs_t(cc_tables t, int64_t row0, int64_t nrows, int lookup, T* out,
+                         cudaStream_t st) {
+  const char4* basis = reinterpret_cast<const char4*>(t->d.basis);
+  if (lookup == CC_LOOKUP_COLLAPSED) {
+    const T* Vm;
+    if constexpr (sizeof(T) == 4) Vm = reinterpret_cast<const T*>(t->d.Vm32);
+    else Vm = reinterpret_cast<const T*>(t->d.Vm64);
+    const size_t tb = (((size_t)(t->m_max + 1) * sizeof(T)) + 15) & ~(size_t)15;
+    if (tb > kSmemCap) return CC_ERR_RANGE;
+    int basis_smem = tb + (size_t)t->Nb * 4 <= 48 * 1024 ? t->Nb : 0;
+    const size_t smem = tb + (size_t)basis_smem * 4;
+    auto kern = k_pair_col<T>;
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    const int bx = (t->Nb + 255) / 256 < 8 ? (t->Nb + 255) / 256 : 8;
+    int64_t by = ((int64_t)per_sm * num_sms() + bx - 1) / bx;
+    if (by > nrows) by = nrows;
+    if (by > 65535) by = 65535;
+    if (by < 1) by = 1;
+    kern<<<dim3(bx, (unsigned)by), 256, smem, st>>>(basis, t->Nb, row0, nrows, Vm, t->m_max, out,
+                                                    basis_smem);
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+  }
+  const int64_t n = nrows * (int64_t)t->Nb;
+  if (t->p.kernel == CC_KERNEL_PERIODIC)
+    return launch_sep<T, PairSrc, true>(t, PairSrc{nullptr, basis, t->Nb, row0}, n, out, nullptr, st);
+  return launch_sep<T, PairSrc, false>(t, PairSrc{nullptr, basis, t->Nb, row0}, n, out, nullptr, st);
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n,
+                                              int format, int lookup, int precision,
+                                              void* out_dev, unsigned long long* counters_dev,
+                                              void* stream) {
+  if (!t || n < 0) return CC_ERR_ARG;
+  if (format != CC_QUAD_IDS_I32 && format != CC_QUAD_VEC_I8X4) return CC_ERR_ARG;
+  if (lookup != CC_LOOKUP_SEPARABLE && lookup != CC_LOOKUP_COLLAPSED) return CC_ERR_ARG;
+  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
+  if (lookup == CC_LOOKUP_COLLAPSED && t->p.kernel != CC_KERNEL_PERIODIC) return CC_ERR_NOTSUPP;
+  if (n == 0) return CC_OK;
+  if (!quads_dev || !out_dev) return CC_ERR_ARG;
+  if (((uintptr_t)quads_dev & 15) != 0) return CC_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (precision == CC_PREC_FP32)
+    return reconstruct_t<float>(t, quads_dev, n, format, lookup, (float*)out_dev, counters_dev, st);
+  return reconstruct_t<double>(t, quads_dev, n, format, lookup, (double*)out_dev, counters_dev, st);
+}
+
+extern "C" cc_status cc_pair_matrix(cc_tables t, int64_t row0, int64_t nrows, int lookup,
+                                    int precision, void* out_dev, void* stream) {
+  if (!t || row0 < 0 || nrows < 0 || row0 + nrows > t->Nb) return CC_ERR_ARG;
+  if (lookup != CC_LOOKUP_SEPARABLE && lookup != CC_LOOKUP_COLLAPSED) return CC_ERR_ARG;
+  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
+  if (lookup == CC_LOOKUP_COLLAPSED && t->p.kernel != CC_KERNEL_PERIODIC) return CC_ERR_NOTSUPP;
+  if (nrows == 0) return CC_OK;
+  if (!out_dev) return CC_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (precision == CC_PREC_FP32) return pairs_t<float>(t, row0, nrows, lookup, (float*)out_dev, st);
+  return pairs_t<double>(t, row0, nrows, lookup, (double*)out_dev, st);
+}

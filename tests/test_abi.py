@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every symbol declared in include/*.h (CPU only:
+no call here touches a GPU)."""
+import glob
+import os
+import re
+import ctypes
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:cc_status|const char\*)\s+(cc_\w+)\s*\(", txt, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1502_08043_gb300 as cc
+    from paper_1502_08043_gb300 import build as b
+    b.build()
+    return cc
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 14
+    L = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared:
+        assert hasattr(L, name), name
+    # the binding declares exactly the header's entry points
+    assert declared == set(lib.SIGNATURES)
+
+
+def test_status_strings_and_host_basis(lib):
+    L = lib.lib()
+    assert L.cc_status_string(0) == b"ok"
+    assert L.cc_status_string(6) == b"not supported"
+    from oracle import basis as ob
+    for R in (1, 4, 13):
+        v = lib.basis(R)
+        assert np.array_equal(v[:, :3].astype(np.int64), ob.basis(R))
+        assert np.all(v[:, 3] == 0)
+    with pytest.raises(lib.CoulombError):
+        lib.basis(0)
+    with pytest.raises(lib.CoulombError):
+        lib.basis(128)
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1502_08043_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            txt = open(f).read()
+            assert "import oracle" not in txt and "from oracle" not in txt, f

@@ -1,0 +1,129 @@
+"""GPU parity: exchange sums by Toeplitz mode products vs the FP64 oracle."""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import CFG1, CFG2, CFG3, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes, rel_err
+from oracle import basis as ob
+from oracle import exchange as ox
+from oracle import quadrature as oq
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "table1.txt")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return need_gpu()
+
+
+def _exchange(t, R_F, prec, dev):
+    import torch
+    import paper_1502_08043_gb300 as cc
+    Mg = t.info["Mg"]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    eps = torch.full((Mg ** 3,), float("nan"), dtype=dt, device=dev)
+    Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+    cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+    return eps.cpu().numpy().astype(np.float64).reshape(Mg, Mg, Mg), Ex.cpu().numpy()
+
+
+def _basis_values(R, grid):
+    k = ob.basis(R) + R
+    return grid[k[:, 0], k[:, 1], k[:, 2]]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32", TOL_FP32)])
+def test_small_box(dev, prec, tol):
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = CFG1["R"], CFG1["L"], CFG1["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=CFG1["S"])
+    a, w = oracle_nodes(R, CFG1["S"])
+    grid, Ex = _exchange(t, R_F, prec, dev)
+    ref = ox.eps_separable(R, R_F, L, a, w)
+    refg = ox.eps_on_grid(R, ref)
+    assert np.array_equal(grid == 0, refg == 0)        # zero outside the basis sphere
+    assert rel_err(_basis_values(R, grid), ref) < tol
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w)
+    assert abs(Ex[0] - ex_ref) < tol * abs(ex_ref) and Ex[1] == 2 * Ex[0]
+    # stated method error against the exact pair sums (S = 32 mesh)
+    assert rel_err(_basis_values(R, grid), ox.eps_exact(R, R_F, L)) < 2e-5
+    t.free()
+
+
+def test_paper_scale(dev):
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = CFG2["R"], CFG2["L"], CFG2["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=CFG2["S"])
+    a, w = oracle_nodes(R, CFG2["S"])
+    grid, Ex = _exchange(t, R_F, "fp32", dev)
+    ref = ox.eps_separable(R, R_F, L, a, w)
+    assert rel_err(_basis_values(R, grid), ref) < TOL_FP32
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w)
+    assert abs(Ex[0] - ex_ref) < TOL_FP32 * abs(ex_ref)
+    assert rel_err(_basis_values(R, grid), ox.eps_exact(R, R_F, L)) < 1e-7
+    t.free()
+
+
+def test_precision_form_sampled(dev):
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = CFG3["R"], CFG3["L"], CFG3["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=CFG3["S"])
+    a, w = oracle_nodes(R, CFG3["S"])
+    grid, Ex = _exchange(t, R_F, "fp32", dev)
+    Nb = ob.count(R)
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([rng.integers(0, Nb, 1500), [0, Nb // 2, Nb - 1]]))
+    ref = ox.eps_separable(R, R_F, L, a, w, k_idx=idx)
+    assert rel_err(_basis_values(R, grid)[idx], ref) < TOL_FP32
+    C = ox.difference_histogram(R_F, "fft")
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
+    assert abs(Ex[0] - ex_ref) < TOL_FP32 * abs(ex_ref)
+    t.free()
+
+
+def _table1():
+    rows = [l.split() for l in open(GOLD) if l.strip() and not l.startswith("#")]
+    return [(m, int(q), float(i1), float(tt)) for m, q, i1, tt in rows]
+
+
+@pytest.mark.parametrize("mesh,q,int1,total", [r for r in _table1() if r[1] in (90, 10, 5)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_table1_on_gpu(dev, mesh, q, int1, total, prec):
+    """Table I replayed by the GPU box-kernel mode products (M = 9171, L = 2)."""
+    import paper_1502_08043_gb300 as cc
+    R = 13
+    if mesh == "mesh1":
+        t = cc.build_tables("box", R=R, L=2.0, S=2 * q, n_sub=0, q_tail=q)
+    else:
+        t = cc.build_tables("box", R=R, L=2.0, S=8 * q + 90, n_sub=7, q_tail=90)
+    grid, Ex = _exchange(t, 13, prec, dev)
+    ratio = Ex[0] / ox.E_KS(9171, 2.0)
+    assert abs(ratio - total) < (2e-6 if prec == "fp64" else 5e-6)
+    t.free()
+
+
+def test_box_exchange_vs_oracle(dev):
+    import paper_1502_08043_gb300 as cc
+    R, R_F, L = 5, 3, 3.0
+    ao, wo, _ = oq.paper_mesh2(6, 24)
+    t = cc.build_tables("box", R=R, L=L, S=len(ao), n_sub=7, q_tail=24)
+    ref = ox.eps_box(R, R_F, L, ao, wo)
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-6)):
+        grid, Ex = _exchange(t, R_F, prec, dev)
+        assert rel_err(_basis_values(R, grid), ref) < tol
+    t.free()
+
+
+def test_exchange_errors(dev):
+    import torch
+    import paper_1502_08043_gb300 as cc
+    t = cc.build_tables("periodic", R=4, L=10.0, S=32)
+    eps = torch.empty(729, dtype=torch.float32, device=dev)
+    Ex = torch.empty(2, dtype=torch.float64, device=dev)
+    for R_F in (0, 5):
+        with pytest.raises(cc.CoulombError) as e:
+            cc.exchange_sums(t, R_F, eps, Ex)
+        assert e.value.status == 2
+    t.free()

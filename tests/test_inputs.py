@@ -21,6 +21,8 @@ def test_quads_conserving_and_chunk_independent():
     a = ci.quads(R, 1000, 500)
     assert np.array_equal(a, q[1000:1500])
     assert np.array_equal(ci.quads(R, 0, 3000), q)
+    pick = np.array([2999, 5, 1700, 5])
+    assert np.array_equal(ci.quads(R, 0, 0, indices=pick), q[pick])
     # ids are spread over the whole basis
     assert len(np.unique(q[:, 0])) > 0.9 * len(B)
 
