@@ -47,14 +47,14 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, gpu_id):
         self.p = None
-        self.index = index
+        self.gpu_id = gpu_id
 
     def start(self):
         try:
             self.p = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
@@ -146,8 +146,18 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = local
+    clocks = Clocks(gpu_id)
     clocks.start()
+    # keep the GPU under the same load for a second before the timed steps so that the
+    # 200 ms clock sampler sees the loaded state (these steps are not timed)
+    tb = time.perf_counter()
+    while time.perf_counter() - tb < 1.0:
+        step()
+        torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

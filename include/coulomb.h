@@ -180,6 +180,12 @@ cc_status cc_pair_matrix(cc_tables t, int64_t row0, int64_t nrows, int lookup, i
 cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, double* Ex_dev,
                            void* stream);
 
+/* Error word of the tensor-core (mixed precision) exchange path: 0 = fine; 1, 2, 3 = a
+ * bounded wait inside the kernel ran out (TMA producer, MMA issuer, epilogue) and the
+ * kernel returned without finishing (outputs invalid).  Synchronises; clear != 0 resets
+ * it.  Returns CC_ERR_TIMEOUT when the word is nonzero. */
+cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
+
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
  * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the
  * products with an Mg^2-long side, each 0 = 64x64, 1 = 32x32, 2 = 64x32 outputs per CTA;

@@ -71,6 +71,7 @@ SIGNATURES = {
     "cc_pair_matrix": (_I, [_P, _I64, _I64, _I, _I, _P, _P]),
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
     "cc_set_gemm_tiles": (_I, [_I, _I, _I, _I]),
+    "cc_mixed_status": (_I, [_P, _P, _I]),
     "cc_status_string": (ctypes.c_char_p, [_I]),
     "cc_last_error": (ctypes.c_char_p, []),
 }
@@ -261,6 +262,13 @@ def exchange_sums(tables: Tables, R_F, eps, Ex, precision=None, stream=None):
     _check("cc_exchange_sums", lib().cc_exchange_sums(
         tables.handle, int(R_F), prec, _ptr(eps), _ptr(Ex), _stream(stream, eps)))
     return eps, Ex
+
+
+def mixed_status(tables: Tables, clear=True) -> int:
+    """Error word of the tensor-core path (0 = fine; see cc_mixed_status)."""
+    code = ctypes.c_int(0)
+    lib().cc_mixed_status(tables.handle, ctypes.byref(code), 1 if clear else 0)
+    return code.value
 
 
 def set_gemm_tiles(precision, small_tile, large_tile, threshold=-1):

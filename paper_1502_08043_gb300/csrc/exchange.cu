@@ -53,11 +53,14 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
   const bool a_kc = g.sAk == 1, b_nc = g.sBn == 1;
   constexpr int LA = BM * BK / NT, LB = BN * BK / NT;
   T ra[LA], rb[LB];
-  T acc[4][4];
+  // running sum with a Kahan compensation term; every K tile of 16 products is summed
+  // into a fresh partial first, so the rounding error stays O(BK + 2) ulps however long
+  // the stacked K dimension (J nodes x K) is
+  T acc[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = T(0);
   const int ktiles = (g.K + BK - 1) / BK;
   const int total = ktiles * g.J;
   auto load = [&](int t) {
@@ -103,6 +106,11 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
     store();
     __syncthreads();
     if (t + 1 < total) load(t + 1);
+    T part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = T(0);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T av[4], bv[4];
@@ -113,8 +121,17 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        for (int j = 0; j < 4; ++j) part[i][j] += av[i] * bv[j];
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T y = part[i][j] - cmp[i][j];
+        const T s = acc[i][j] + y;
+        cmp[i][j] = (s - acc[i][j]) - y;
+        acc[i][j] = s;
+      }
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -125,7 +142,7 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
       const int gn = n0 + tx + j * TX;
       if (gn >= g.N) continue;
       T* c = C + gm * g.sCm + gn * g.sCn;
-      *c = g.beta ? *c + acc[i][j] : acc[i][j];
+      *c = g.beta ? *c + (acc[i][j] - cmp[i][j]) : acc[i][j] - cmp[i][j];
     }
   }
 }

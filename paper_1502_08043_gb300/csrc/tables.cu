@@ -400,6 +400,7 @@ static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_t
   CC_TRY(build_derived(t, st));
   CC_TRY(workspace_alloc(t));
   CC_CUDA(cudaStreamSynchronize(st));
+  if (t->Mg <= 128) CC_TRY(mixed_workspace_alloc(t));
   return CC_OK;
 }
 
@@ -616,6 +617,7 @@ cc_status cc_tables_load(const char* path, void* stream, cc_tables* out) {
     if (s == CC_OK) s = build_derived(t, st);
     if (s == CC_OK) s = workspace_alloc(t);
     if (s == CC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = CC_ERR_CUDA;
+    if (s == CC_OK && t->Mg <= 128) s = mixed_workspace_alloc(t);
   }
   if (s != CC_OK) {
     cc_tables_free(t);

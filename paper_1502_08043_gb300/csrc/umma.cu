@@ -1,12 +1,705 @@
-// Mixed-precision (bf16 / fp16 hi+lo on tcgen05 tensor cores) exchange mode products.
+// Mixed-precision exchange mode products on the 5th-generation tensor cores (tcgen05).
+//
+// Same sums as exchange.cu (Sec. III exchange of the uniform electron gas, node sum of
+// Sec. II Eq. 14 with the D = T - I split for the periodic kernel), reordered so that
+// every contraction is a dense GEMM whose two operands are K-major in memory:
+//   step 5 (once)  E[x][y][z']  = sum_z O[x][y][z] Dbar[z'][z]            (I x I x D)
+//   per node s (Dx = D_s periodic, T_s box):
+//   step 1  R_s[x][y][z]   = sum_x' Dx[x][x'] O[x'][y][z]               (x mode first)
+//   step 2  W1_s[x][z'][y] = sum_z T_s[z'][z] R_s[x][y][z]               (z mode)
+//   step 3  W2_s[x][z'][y] = sum_z T_s[z'][z] O[x][y][z]                 (z mode)
+//   step 4  E[x][y'][z'] += sum_s sum_y (w T_s)[y'][y] W1_s[x][z'][y]
+//                                   + (w D_s)[y'][y] W2_s[x][z'][y]     (y mode)
+// which is D x T x T + I x D x T + I x I x D (mode products commute).  The box kernel
+// keeps only W1 with Dx = T_s and no step 3 / step 5.
+// Every GEMM has a 128-row operand A (rows of an Np^2 x Np slab stack) and an Np x Np
+// operand B (a Toeplitz matrix), Np = 64 or 128 (the grid side padded with zeros).
+// Operands are bf16 hi + lo planes: x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+// the product keeps hi*hi + hi*lo + lo*hi (3 MMAs, the lo*lo term is below 2^-18
+// relative).  Intermediates leave TMEM as FP32, are re-split into hi + lo (the FP32
+// residual x - hi carried as the correction operand) and stored for the next GEMM.
+// O, O^T are exact in bf16 (0/1) and have no lo plane.
+//
+// Kernel anatomy (one 128 x Np output tile per CTA, 4 warps):
+//   warp 0 / lane 0  TMA producer: 2D tiled cp.async.bulk.tensor loads of 64-wide K
+//                    blocks (128-byte swizzle) into a 3-stage shared-memory ring;
+//   warp 1 / lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = Np,
+//                    K = 16 per instruction, FP32 accumulator in TMEM; tcgen05.commit
+//                    frees a ring slot when its MMAs have read it;
+//   warp 2           allocates / frees Np TMEM columns;
+//   all 4 warps      epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store FP32
+//                    (optionally accumulating) or split into hi / lo planes.
+// Every mbarrier wait is bounded by the global timer (about 2 s); on expiry the kernel
+// sets an error word, stops issuing work, and returns through the normal teardown.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <type_traits>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace cc {
 
-cc_status mixed_workspace_alloc(cc_tables) { return CC_OK; }
-void mixed_workspace_free(cc_tables) {}
-cc_status exchange_mixed(cc_tables, int, int, float*, double*, cudaStream_t) {
-  return CC_ERR_NOTSUPP;
+// ------------------------------------------------------------------ device primitives
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: gives up after ~2 s of wall time and reports through *err
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups of
+// 1024 bytes (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <typename E>
+__device__ __forceinline__ void split2(float v, E& hi, E& lo);
+template <>
+__device__ __forceinline__ void split2<__nv_bfloat16>(float v, __nv_bfloat16& hi,
+                                                      __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+template <>
+__device__ __forceinline__ void split2<__half>(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+// ------------------------------------------------------------------ the GEMM kernel
+struct TcArgs {
+  int nk;               // 64-wide K blocks per product
+  int J;                // products stacked along K (accumulated in one TMEM tile)
+  long long a_base, a_sb, a_sj;  // A row of (batch b, product j): base + b*sb + j*sj (+ m0)
+  long long b_base, b_sb, b_sj;
+  int a_lo, b_lo;       // lo planes present
+  int out_split;        // 0: FP32 output, 1: hi/lo planes of E
+  int beta;             // FP32 output: accumulate into the existing value
+  void* out;
+  void* out_lo;
+  long long o_base, o_sb;              // element offset of batch b
+  long long s_mhi, s_mlo, s_n;         // element (m, n) -> (m / Np) s_mhi + (m % Np) s_mlo + n s_n
+  const float* scale;   // per-batch factor applied before the store (nullptr: 1)
+  int* err;
+};
+
+constexpr int kStages = 3;
+constexpr int kTileM = 128;
+constexpr int kKB = 64;  // K elements per block = one 128-byte swizzle atom of 16-bit values
+
+template <int NP>
+struct TcSmem {
+  static constexpr int kA = kTileM * kKB * 2;  // 16 KB
+  static constexpr int kB = NP * kKB * 2;      // 8 / 16 KB
+  static constexpr int kStage = 2 * kA + 2 * kB;
+  static constexpr int kBytes = kStages * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+};
+
+template <int NP, typename E>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
+              const __grid_constant__ CUtensorMap mB, const __grid_constant__ CUtensorMap mBlo,
+              TcArgs g) {
+  using L = TcSmem<NP>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t bar0 = base + kStages * L::kStage;  // full[s], empty[s], done, tmem slot
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
+  const uint32_t done = bar0 + 8u * (2 * kStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 1));
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  const long long m0 = (long long)blockIdx.x * kTileM;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)NP)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int total = g.J * g.nk;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    const uint32_t bytes = (uint32_t)(L::kA * (g.a_lo ? 2 : 1) + L::kB * (g.b_lo ? 2 : 1));
+    for (int it = 0; it < total; ++it) {
+      const int s = it % kStages;
+      const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+      if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1)) {
+        s_abort = 1;
+        break;
+      }
+      const int j = it / g.nk, kb = it % g.nk;
+      const int arow = (int)(g.a_base + b * g.a_sb + j * g.a_sj + m0);
+      const int brow = (int)(g.b_base + b * g.b_sb + j * g.b_sj);
+      const uint32_t st = base + s * L::kStage;
+      mbar_expect_tx(full(s), bytes);
+      tma_load_2d(st, &mA, kb * kKB, arow, full(s));
+      if (g.a_lo) tma_load_2d(st + L::kA, &mAlo, kb * kKB, arow, full(s));
+      tma_load_2d(st + 2 * L::kA, &mB, kb * kKB, brow, full(s));
+      if (g.b_lo) tma_load_2d(st + 2 * L::kA + L::kB, &mBlo, kb * kKB, brow, full(s));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t fmt = std::is_same<E, __nv_bfloat16>::value ? 1u : 0u;
+    constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
+                               ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+    bool ok = true;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % kStages;
+      const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+      if (!mbar_wait(full(s), ph, g.err, 2)) {
+        ok = false;
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = base + s * L::kStage;
+      const uint64_t dA = sdesc(st), dAl = sdesc(st + L::kA);
+      const uint64_t dB = sdesc(st + 2 * L::kA), dBl = sdesc(st + 2 * L::kA + L::kB);
+#pragma unroll
+      for (int k = 0; k < kKB / 16; ++k) {
+        const uint64_t adv = (uint64_t)((k * 32) >> 4);  // 32 bytes per K = 16 step
+        mma_f16(tmem, dA + adv, dB + adv, idesc, (it > 0 || k > 0) ? 1u : 0u);
+        if (g.b_lo) mma_f16(tmem, dA + adv, dBl + adv, idesc, 1u);
+        if (g.a_lo) mma_f16(tmem, dAl + adv, dB + adv, idesc, 1u);
+      }
+      mma_commit(empty(s));
+    }
+    if (ok) mma_commit(done);
+  }
+  __syncwarp();
+  // ---------------- epilogue (all 4 warps; warp w owns TMEM lanes 32w .. 32w + 31)
+  const bool have = mbar_wait(done, 0, g.err, 3);
+  tc_fence_after();
+  if (have && !s_abort) {
+    const long long m = m0 + warp * 32 + lane;
+    const long long mh = m / NP, ml = m % NP;
+    const long long row_off = g.o_base + b * g.o_sb + mh * g.s_mhi + ml * g.s_mlo;
+    const float sc = g.scale ? g.scale[b] : 1.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NP; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (!g.out_split) {
+        float* o = reinterpret_cast<float*>(g.out) + row_off + c0 * g.s_n;
+        if (g.s_n == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            float4 r = make_float4(__uint_as_float(v[i]) * sc, __uint_as_float(v[i + 1]) * sc,
+                                   __uint_as_float(v[i + 2]) * sc, __uint_as_float(v[i + 3]) * sc);
+            float4* p = reinterpret_cast<float4*>(o + i);
+            if (g.beta) {
+              const float4 q = *p;
+              r.x += q.x; r.y += q.y; r.z += q.z; r.w += q.w;
+            }
+            *p = r;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            float* p = o + i * g.s_n;
+            const float r = __uint_as_float(v[i]) * sc;
+            *p = g.beta ? *p + r : r;
+          }
+        }
+      } else {
+        E* oh = reinterpret_cast<E*>(g.out) + row_off + c0 * g.s_n;
+        E* ol = reinterpret_cast<E*>(g.out_lo) + row_off + c0 * g.s_n;
+        if (g.s_n == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 8) {
+            E h[8], l[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) split2<E>(__uint_as_float(v[i + u]) * sc, h[u], l[u]);
+            *reinterpret_cast<uint4*>(oh + i) = *reinterpret_cast<uint4*>(h);
+            *reinterpret_cast<uint4*>(ol + i) = *reinterpret_cast<uint4*>(l);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            E h, l;
+            split2<E>(__uint_as_float(v[i]) * sc, h, l);
+            oh[i * g.s_n] = h;
+            ol[i * g.s_n] = l;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)NP)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ element kernels
+// operand planes of the Toeplitz matrices, padded to Np x Np:
+// X1[s] = D_s (periodic) or T_s (box), TT[s] = T_s, WTD[s][0] = w_s T_s, WTD[s][1] = w_s D_s
+template <typename E>
+__global__ void k_mx_tables(const double* Tm, const double* WDm, const double* w, int S_eff,
+                            int Mg, int Np, int periodic, E* x1h, E* x1l, E* tth, E* ttl,
+                            E* wtdh, E* wtdl) {
+  const long long n = (long long)S_eff * Np * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / ((long long)Np * Np));
+    const int a = (int)((i / Np) % Np), c = (int)(i % Np);
+    double t = 0.0, d = 0.0;
+    if (a < Mg && c < Mg) {
+      t = Tm[((long long)s * Mg + a) * Mg + c];
+      d = (periodic && a == c) ? 0.0 : t;
+    }
+    const double wt = w[s] * t, wd = w[s] * d;
+    E h, l;
+    split2<E>((float)(periodic ? d : t), h, l);
+    x1h[i] = h;
+    x1l[i] = l;
+    split2<E>((float)t, h, l);
+    tth[i] = h;
+    ttl[i] = l;
+    const long long j0 = (((long long)s * 2 + 0) * Np + a) * Np + c;
+    const long long j1 = (((long long)s * 2 + 1) * Np + a) * Np + c;
+    split2<E>((float)wt, h, l);
+    wtdh[j0] = h;
+    wtdl[j0] = l;
+    split2<E>((float)wd, h, l);
+    wtdh[j1] = h;
+    wtdl[j1] = l;
+    (void)WDm;
+  }
+}
+
+template <typename E>
+__global__ void k_mx_dbar(const double* Dbar, int Mg, int Np, E* h, E* l) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Np * Np) return;
+  const int a = i / Np, c = i % Np;
+  const double v = (a < Mg && c < Mg) ? Dbar[a * Mg + c] : 0.0;
+  E hh, ll;
+  split2<E>((float)v, hh, ll);
+  h[i] = hh;
+  l[i] = ll;
+}
+
+// occupation O[x][y][z] and its x-last transpose OT[y][z][x], padded to Np^3 (exact)
+template <typename E>
+__global__ void k_mx_occ(int R, int R_F, int Np, E* O, E* OT) {
+  const long long n = (long long)Np * Np * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i / ((long long)Np * Np)), y = (int)((i / Np) % Np), z = (int)(i % Np);
+    const int Mg = 2 * R + 1;
+    float v = 0.0f;
+    if (x < Mg && y < Mg && z < Mg) {
+      const int a = x - R, bb = y - R, c = z - R;
+      v = (a * a + bb * bb + c * c <= R_F * R_F) ? 1.0f : 0.0f;
+    }
+    O[i] = (E)v;
+    OT[((long long)y * Np + z) * Np + x] = (E)v;
+  }
+}
+
+// eps = -pref E on the basis sphere (unpadded grid), FP64 partials over the Fermi sphere
+__global__ void k_mx_finalize(const float* E, int Np, int R, int R_F, double pref, float* eps,
+                              double* part) {
+  const int Mg = 2 * R + 1;
+  const long long G3 = (long long)Mg * Mg * Mg;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i / ((long long)Mg * Mg)), y = (int)((i / Mg) % Mg), z = (int)(i % Mg);
+    const int a = x - R, bb = y - R, c = z - R;
+    const int m = a * a + bb * bb + c * c;
+    float v = 0.0f;
+    if (m <= R * R) v = (float)(-pref * (double)E[((long long)x * Np + y) * Np + z]);
+    eps[i] = v;
+    if (m <= R_F * R_F) acc += (double)v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_mx_reduce(const double* part, int n, double* Ex, const int* err, int* status) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Ex[0] = 0.5 * red[0];
+    Ex[1] = red[0];
+    if (status) *status = *err;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct MxPlanes {  // one element type
+  void* X1[2];   // [S_eff][Np][Np] hi, lo
+  void* TT[2];   // [S_eff][Np][Np]
+  void* WTD[2];  // [S_eff][2][Np][Np]
+  void* DB[2];   // [Np][Np]
+  void* O;       // [Np^3]
+  void* OT;      // [Np^3]
+  void* R[2];    // [C][Np^3]
+  void* W[2];    // [C][2][Np^3]
+  CUtensorMap mO, mOT, mR[2], mW[2], mX1[2], mTT[2], mWTD[2], mDB[2];
+};
+
+struct MxWorkspace {
+  int Np = 0, C = 0, R_F_built = -1, R_F_built16 = -1;
+  float* E = nullptr;     // [Np^3]
+  int* err = nullptr;     // device error word
+  MxPlanes bf, hf;
+  std::vector<void*> allocs;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static cc_status get_encoder() {
+  if (g_encode) return CC_OK;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    set_last_error("cuTensorMapEncodeTiled entry point", e);
+    return CC_ERR_CUDA;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return CC_OK;
+}
+
+// 2D map over a row-major [rows][Np] array of 16-bit values; box = 64 columns x box_rows
+static cc_status make_map(CUtensorMap* m, void* ptr, long long rows, int Np, int box_rows,
+                          bool bf16) {
+  cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Np * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                        2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled", cudaErrorInvalidValue);
+    return CC_ERR_CUDA;
+  }
+  return CC_OK;
+}
+
+static cc_status mx_alloc(cc_tables t, MxWorkspace* w, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    set_last_error("cudaMalloc(mixed workspace)", e);
+    return CC_ERR_ALLOC;
+  }
+  w->allocs.push_back(*p);
+  t->ws.mx_bytes += bytes;
+  t->device_bytes += bytes;
+  return CC_OK;
+}
+
+template <typename E>
+static cc_status build_planes(cc_tables t, MxWorkspace* w, MxPlanes* P, bool bf16) {
+  const int Np = w->Np, S = t->S_eff, C = w->C;
+  const size_t e2 = 2;
+  const size_t mat = (size_t)Np * Np * e2;
+  const size_t vol = (size_t)Np * Np * Np * e2;
+  for (int h = 0; h < 2; ++h) {
+    CC_TRY(mx_alloc(t, w, &P->X1[h], mat * S));
+    CC_TRY(mx_alloc(t, w, &P->TT[h], mat * S));
+    CC_TRY(mx_alloc(t, w, &P->WTD[h], mat * S * 2));
+    CC_TRY(mx_alloc(t, w, &P->DB[h], mat));
+    CC_TRY(mx_alloc(t, w, &P->R[h], vol * C));
+    CC_TRY(mx_alloc(t, w, &P->W[h], vol * C * 2));
+  }
+  CC_TRY(mx_alloc(t, w, &P->O, vol));
+  CC_TRY(mx_alloc(t, w, &P->OT, vol));
+  const long long NN = (long long)Np * Np;
+  CC_TRY(make_map(&P->mO, P->O, NN, Np, kTileM, bf16));
+  CC_TRY(make_map(&P->mOT, P->OT, NN, Np, kTileM, bf16));
+  for (int h = 0; h < 2; ++h) {
+    CC_TRY(make_map(&P->mR[h], P->R[h], (long long)C * NN, Np, kTileM, bf16));
+    CC_TRY(make_map(&P->mW[h], P->W[h], (long long)C * 2 * NN, Np, kTileM, bf16));
+    CC_TRY(make_map(&P->mX1[h], P->X1[h], (long long)S * Np, Np, Np, bf16));
+    CC_TRY(make_map(&P->mTT[h], P->TT[h], (long long)S * Np, Np, Np, bf16));
+    CC_TRY(make_map(&P->mWTD[h], P->WTD[h], (long long)S * 2 * Np, Np, Np, bf16));
+    CC_TRY(make_map(&P->mDB[h], P->DB[h], (long long)Np, Np, Np, bf16));
+  }
+  const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
+  k_mx_tables<E><<<1024, 256>>>(t->d.Tm64, t->d.WDm64, t->d.w64, S, t->Mg, Np, periodic,
+                                (E*)P->X1[0], (E*)P->X1[1], (E*)P->TT[0], (E*)P->TT[1],
+                                (E*)P->WTD[0], (E*)P->WTD[1]);
+  k_mx_dbar<E><<<(Np * Np + 255) / 256, 256>>>(t->d.Dbar64, t->Mg, Np, (E*)P->DB[0],
+                                               (E*)P->DB[1]);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status mixed_workspace_alloc(cc_tables t) {
+  if (t->ws.mx) return CC_OK;
+  if (t->Mg > 128) return CC_ERR_NOTSUPP;
+  CC_TRY(get_encoder());
+  MxWorkspace* w = new (std::nothrow) MxWorkspace();
+  if (!w) return CC_ERR_ALLOC;
+  t->ws.mx = w;
+  w->Np = t->Mg <= 64 ? 64 : 128;
+  w->C = t->S_eff < 8 ? t->S_eff : 8;
+  const int Np = w->Np;
+  CC_TRY(mx_alloc(t, w, (void**)&w->E, sizeof(float) * Np * Np * Np));
+  CC_TRY(mx_alloc(t, w, (void**)&w->err, sizeof(int) * 2));
+  CC_CUDA(cudaMemset(w->err, 0, sizeof(int) * 2));
+  CC_TRY(build_planes<__nv_bfloat16>(t, w, &w->bf, true));
+  CC_CUDA(cudaDeviceSynchronize());
+  return CC_OK;
+}
+
+void mixed_workspace_free(cc_tables t) {
+  MxWorkspace* w = reinterpret_cast<MxWorkspace*>(t->ws.mx);
+  if (!w) return;
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+  t->ws.mx = nullptr;
+}
+
+template <int NP, typename E>
+static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const CUtensorMap& B,
+                           const CUtensorMap& Blo, const TcArgs& g, int m_tiles, int batches,
+                           cudaStream_t st) {
+  auto kern = k_tc_gemm<NP, E>;
+  const int smem = TcSmem<NP>::kBytes;
+  static bool attr = false;
+  if (!attr) {
+    CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  kern<<<dim3(m_tiles, batches), 128, smem, st>>>(A, Alo, B, Blo, g);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+template <int NP, typename E>
+static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, float* eps,
+                           double* Ex, cudaStream_t st) {
+  const long long NN = (long long)NP * NP, VOL = NN * NP;
+  const int m_tiles = (int)(NN / kTileM);
+  const bool periodic = t->p.kernel == CC_KERNEL_PERIODIC;
+  const int S = t->S_eff, C = w->C;
+  k_mx_occ<E><<<1024, 256, 0, st>>>(t->p.R, R_F, NP, (E*)P.O, (E*)P.OT);
+  CC_CUDA(cudaGetLastError());
+  const long long nat_mhi = NN, nat_mlo = NP;
+  bool first = true;
+  if (periodic) {
+    // step 5: E[x][y][z'] = sum_z O[(x,y)][z] Dbar[z'][z]
+    TcArgs g{};
+    g.nk = NP / kKB; g.J = 1;
+    g.a_base = 0; g.a_lo = 0; g.b_base = 0; g.b_lo = 1;
+    g.out_split = 0; g.beta = 0; g.out = w->E;
+    g.o_base = 0; g.o_sb = 0; g.s_mhi = nat_mhi; g.s_mlo = nat_mlo; g.s_n = 1;
+    g.err = w->err;
+    CC_TRY((launch_tc<NP, E>(P.mO, P.mO, P.mDB[0], P.mDB[1], g, m_tiles, 1, st)));
+    first = false;
+  }
+  for (int s0 = 0; s0 < S; s0 += C) {
+    const int cs = S - s0 < C ? S - s0 : C;
+    // step 1: R_s[x][(y,z)] = sum_x' X1_s[x][x'] OT[(y,z)][x']   (stored transposed)
+    {
+      TcArgs g{};
+      g.nk = NP / kKB; g.J = 1;
+      g.a_base = 0; g.a_sb = 0; g.a_lo = 0;
+      g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
+      g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
+      g.o_base = 0; g.o_sb = VOL; g.s_mhi = NP; g.s_mlo = 1; g.s_n = NN;
+      g.err = w->err;
+      CC_TRY((launch_tc<NP, E>(P.mOT, P.mOT, P.mX1[0], P.mX1[1], g, m_tiles, cs, st)));
+    }
+    // step 2: W1_s[x][z'][y] = sum_z T_s[z'][z] R_s[(x,y)][z]      (slab transposed)
+    {
+      TcArgs g{};
+      g.nk = NP / kKB; g.J = 1;
+      g.a_base = 0; g.a_sb = NN; g.a_lo = 1;
+      g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
+      g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
+      g.o_base = 0; g.o_sb = 2 * VOL; g.s_mhi = NN; g.s_mlo = 1; g.s_n = NP;
+      g.err = w->err;
+      CC_TRY((launch_tc<NP, E>(P.mR[0], P.mR[1], P.mTT[0], P.mTT[1], g, m_tiles, cs, st)));
+    }
+    if (periodic) {
+      // step 3: W2_s[x][z'][y] = sum_z T_s[z'][z] O[(x,y)][z]
+      TcArgs g{};
+      g.nk = NP / kKB; g.J = 1;
+      g.a_base = 0; g.a_sb = 0; g.a_lo = 0;
+      g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
+      g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
+      g.o_base = VOL; g.o_sb = 2 * VOL; g.s_mhi = NN; g.s_mlo = 1; g.s_n = NP;
+      g.err = w->err;
+      CC_TRY((launch_tc<NP, E>(P.mO, P.mO, P.mTT[0], P.mTT[1], g, m_tiles, cs, st)));
+    }
+    // step 4: E[x][y'][z'] += sum_j sum_y WTD_j[y'][y] W_j[(x,z')][y]   (slab transposed)
+    {
+      TcArgs g{};
+      g.nk = NP / kKB;
+      g.J = periodic ? 2 * cs : cs;
+      g.a_base = 0; g.a_sb = 0; g.a_sj = periodic ? NN : 2 * NN; g.a_lo = 1;
+      g.b_base = (long long)s0 * 2 * NP; g.b_sb = 0; g.b_sj = periodic ? NP : 2 * NP; g.b_lo = 1;
+      g.out_split = 0; g.beta = first ? 0 : 1; g.out = w->E;
+      g.o_base = 0; g.o_sb = 0; g.s_mhi = NN; g.s_mlo = 1; g.s_n = NP;
+      g.err = w->err;
+      CC_TRY((launch_tc<NP, E>(P.mW[0], P.mW[1], P.mWTD[0], P.mWTD[1], g, m_tiles, 1, st)));
+      first = false;
+    }
+  }
+  k_mx_finalize<<<kRedBlocks, 256, 0, st>>>(w->E, NP, t->p.R, R_F, t->pref, eps, t->ws.part);
+  k_mx_reduce<<<1, 256, 0, st>>>(t->ws.part, kRedBlocks, Ex, w->err, w->err + 1);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
+                         cudaStream_t st) {
+  if (precision != CC_PREC_BF16X3) return CC_ERR_NOTSUPP;
+  if (t->Mg > 128) return CC_ERR_NOTSUPP;
+  CC_TRY(mixed_workspace_alloc(t));
+  MxWorkspace* w = reinterpret_cast<MxWorkspace*>(t->ws.mx);
+  if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
+  return run_mixed<128, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
 }
 
 }  // namespace cc
+
+// Device error word of the mixed path (0: fine, 1-3: a bounded wait ran out in the
+// producer, MMA issuer or epilogue).  Reads back synchronously; clears it when asked.
+extern "C" cc_status cc_mixed_status(cc_tables t, int* code_host, int clear) {
+  if (!t || !code_host) return CC_ERR_ARG;
+  cc::MxWorkspace* w = reinterpret_cast<cc::MxWorkspace*>(t->ws.mx);
+  *code_host = 0;
+  if (!w) return CC_OK;
+  CC_CUDA(cudaMemcpy(code_host, w->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (clear) CC_CUDA(cudaMemset(w->err, 0, sizeof(int) * 2));
+  return *code_host ? CC_ERR_TIMEOUT : CC_OK;
+}

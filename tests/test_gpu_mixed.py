@@ -1,0 +1,93 @@
+"""GPU parity: mixed-precision (bf16 hi+lo, tcgen05 tensor cores) exchange sums vs the
+FP64 oracle, at the stated 1e-4 relative tolerance, and against the plain FP32 path."""
+import numpy as np
+import pytest
+
+from gpu_common import CFG1, CFG2, CFG3, CFG5, need_gpu, oracle_nodes, rel_err
+from oracle import basis as ob
+from oracle import exchange as ox
+from oracle import quadrature as oq
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return need_gpu()
+
+
+def _run(t, R_F, prec, dev):
+    import torch
+    import paper_1502_08043_gb300 as cc
+    Mg = t.info["Mg"]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    eps = torch.full((Mg ** 3,), float("nan"), dtype=dt, device=dev)
+    Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+    cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+    torch.cuda.synchronize()
+    assert cc.mixed_status(t) == 0
+    return eps.cpu().numpy().astype(np.float64).reshape(Mg, Mg, Mg), Ex.cpu().numpy()
+
+
+def _basis_values(R, grid):
+    k = ob.basis(R) + R
+    return grid[k[:, 0], k[:, 1], k[:, 2]]
+
+
+@pytest.mark.parametrize("cfg", [CFG1, CFG2], ids=["R4", "R13"])
+def test_mixed_full_compare(dev, cfg):
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = cfg["R"], cfg["L"], cfg["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=cfg["S"])
+    a, w = oracle_nodes(R, cfg["S"])
+    ref = ox.eps_separable(R, R_F, L, a, w)
+    grid, Ex = _run(t, R_F, "bf16x3", dev)
+    assert np.array_equal(grid == 0, ox.eps_on_grid(R, ref) == 0)
+    assert rel_err(_basis_values(R, grid), ref) < TOL_MIXED
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w)
+    assert abs(Ex[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
+    t.free()
+
+
+@pytest.mark.parametrize("cfg", [CFG3, CFG5], ids=["R31", "R63"])
+def test_mixed_sampled(dev, cfg):
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = cfg["R"], cfg["L"], cfg["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=cfg["S"])
+    a, w = oracle_nodes(R, cfg["S"])
+    grid, Ex = _run(t, R_F, "bf16x3", dev)
+    Nb = ob.count(R)
+    rng = np.random.default_rng(11)
+    idx = np.unique(np.concatenate([rng.integers(0, Nb, 300), [0, Nb // 2, Nb - 1]]))
+    ref = ox.eps_separable(R, R_F, L, a, w, k_idx=idx)
+    assert rel_err(_basis_values(R, grid)[idx], ref) < TOL_MIXED
+    C = ox.difference_histogram(R_F, "fft")
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
+    assert abs(Ex[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
+    # the plain FP32 path on the same handle agrees with the mixed one to the same bound
+    g32, _ = _run(t, R_F, "fp32", dev)
+    inside = g32 != 0
+    assert np.max(np.abs(grid[inside] - g32[inside]) / np.abs(g32[inside])) < 2 * TOL_MIXED
+    t.free()
+
+
+def test_mixed_box_table1(dev):
+    """Table I (Mesh 2, 8x10) replayed through the tensor-core path, box kernel."""
+    import paper_1502_08043_gb300 as cc
+    t = cc.build_tables("box", R=13, L=2.0, S=170, n_sub=7, q_tail=90)
+    _, Ex = _run(t, 13, "bf16x3", dev)
+    assert abs(Ex[0] / ox.E_KS(9171, 2.0) - 0.965431) < 1e-4
+    t.free()
+
+
+def test_mixed_repeatable(dev):
+    import paper_1502_08043_gb300 as cc
+    t = cc.build_tables("periodic", R=CFG2["R"], L=CFG2["L"], S=CFG2["S"])
+    g1, e1 = _run(t, CFG2["R_F"], "bf16x3", dev)
+    g2, e2 = _run(t, CFG2["R_F"], "bf16x3", dev)
+    assert np.array_equal(g1, g2) and np.array_equal(e1, e2)
+    g3, _ = _run(t, 5, "bf16x3", dev)     # another Fermi radius on the same handle
+    ref = ox.eps_separable(CFG2["R"], 5, CFG2["L"], *oracle_nodes(CFG2["R"], CFG2["S"]))
+    assert rel_err(_basis_values(CFG2["R"], g3), ref) < TOL_MIXED
+    t.free()

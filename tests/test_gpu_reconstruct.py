@@ -128,7 +128,10 @@ def test_box_kernel_separable(dev):
     tab = oc.box_table(ao, 2 * R, L)
     ref, cnt_ref = orc.reconstruct(q, R, L, "box", a=ao, w=wo, box_table=tab)
     assert cnt_ref[1] == 0 and cnt_ref[0] > 0
-    for dtype, tol in ((torch.float64, 1e-11), (torch.float32, 2e-6)):
+    # box tables: the device's 1200-point axis integrals and the oracle's 2000-point ones
+    # agree to ~1e-13 absolute; A(alpha, Delta) changes sign, so the node sum cancels and
+    # relative differences of the (small) results grow to ~1e-10
+    for dtype, tol in ((torch.float64, 1e-9), (torch.float32, 2e-6)):
         got, cnt = _run(t, q, "separable", dtype, dev)
         assert np.array_equal(cnt, cnt_ref)
         assert rel_err(got, ref) < tol
