@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
   constexpr int LA = BM * BK / NT, LB = BN * BK / NT;
   T ra[LA], rb[LB];
   // running sum with a Kahan compensation term; every K tile of 16 products is summed
-  // into a fresh partial first, so the rounding error stays O(BK + 2) ulps however long
+  // into fresh partials first, so the rounding error stays O(BK/2 + 3) ulps however long
   // the stacked K dimension (J nodes x K) is
   T acc[4][4], cmp[4][4];
 #pragma unroll
@@ -106,11 +106,14 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
     store();
     __syncthreads();
     if (t + 1 < total) load(t + 1);
-    T part[4][4];
+    // two interleaved partial sums (even / odd k): 8-term chains, then one pairwise add
+    T part[2][4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = T(0);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[h][i][j] = T(0);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T av[4], bv[4];
@@ -121,13 +124,13 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmDesc g) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) part[i][j] += av[i] * bv[j];
+        for (int j = 0; j < 4; ++j) part[k & 1][i][j] += av[i] * bv[j];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const T y = part[i][j] - cmp[i][j];
+        const T y = (part[0][i][j] + part[1][i][j]) - cmp[i][j];
         const T s = acc[i][j] + y;
         cmp[i][j] = (s - acc[i][j]) - y;
         acc[i][j] = s;
