@@ -180,6 +180,23 @@ cc_status cc_pair_matrix(cc_tables t, int64_t row0, int64_t nrows, int lookup, i
 cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, double* Ex_dev,
                            void* stream);
 
+/* Exchange sums without any allocation (no counterpart in the paper).  For callers that
+ * cannot call cudaMalloc at the point where they need the sums: code running under a
+ * framework's caching allocator that owns the device memory, or latency-critical loops
+ * where cudaMalloc's implicit device synchronisation would stall other streams.
+ * Computes exactly what cc_exchange_sums computes with CC_PREC_FP32 (eps float[Mg^3],
+ * Ex_dev[2]), reading the handle's tables, but keeps all scratch in one fixed 16 MiB
+ * device array inside the library (held by every GPU that loads the library until the
+ * process exits) and calls no cudaMalloc, cudaFree or allocating library routine.
+ * Limit: R <= 31 (grid side 63); larger handles get CC_ERR_RANGE.
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, device current); make that first call before any stream
+ * capture.  Every call shares the array and leaves the last call's contents in it:
+ * calls that overlap on the GPU (any device-side overlap, on any stream, from any
+ * thread) race and must be ordered by the caller. */
+cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_dev, double* Ex_dev,
+                                   void* stream);
+
 /* Error word of the tensor-core (mixed precision) exchange path: 0 = fine; 1, 2, 3 = a
  * bounded wait inside the kernel ran out (TMA producer, MMA issuer, epilogue) and the
  * kernel returned without finishing (outputs invalid).  Synchronises; clear != 0 resets

@@ -72,6 +72,7 @@ SIGNATURES = {
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
     "cc_set_gemm_tiles": (_I, [_I, _I, _I, _I]),
     "cc_mixed_status": (_I, [_P, _P, _I]),
+    "cc_exchange_sums_noalloc": (_I, [_P, _I, _P, _P, _P]),
     "cc_status_string": (ctypes.c_char_p, [_I]),
     "cc_last_error": (ctypes.c_char_p, []),
 }
@@ -261,6 +262,20 @@ def exchange_sums(tables: Tables, R_F, eps, Ex, precision=None, stream=None):
             raise TypeError(f"eps must be {need} for {precision}")
     _check("cc_exchange_sums", lib().cc_exchange_sums(
         tables.handle, int(R_F), prec, _ptr(eps), _ptr(Ex), _stream(stream, eps)))
+    return eps, Ex
+
+
+def exchange_sums_noalloc(tables: Tables, R_F, eps, Ex, stream=None):
+    """cc_exchange_sums_noalloc: the FP32 exchange sums with all scratch in the library's
+    fixed device array (no allocation; R <= 31; calls must not overlap on the GPU)."""
+    import torch
+    Mg = tables.info["Mg"]
+    if eps.dtype != torch.float32 or eps.numel() < Mg ** 3:
+        raise ValueError("eps must be float32 with (2R+1)^3 values")
+    if Ex.dtype != torch.float64 or Ex.numel() < 2:
+        raise ValueError("Ex must hold two float64")
+    _check("cc_exchange_sums_noalloc", lib().cc_exchange_sums_noalloc(
+        tables.handle, int(R_F), _ptr(eps), _ptr(Ex), _stream(stream, eps)))
     return eps, Ex
 
 

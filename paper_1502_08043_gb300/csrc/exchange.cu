@@ -276,14 +276,15 @@ static int tile_for(int Mg, bool long_dim, bool fp64) {
   return long_dim ? g_tile_large[fp64] : g_tile_small[fp64];
 }
 
+// The plain path on an explicit workspace: occ, E ([Mg^3] each), P, Q ([chunk][Mg^3]
+// each) of element type T, and part[kRedBlocks] doubles.
 template <typename T>
-static cc_status exchange_simt(cc_tables t, int R_F, T* eps, double* Ex, cudaStream_t st) {
+static cc_status exchange_simt_ws(cc_tables t, const Workspace& w, int chunk, int R_F, T* eps,
+                                  double* Ex, cudaStream_t st) {
   const int Mg = t->Mg, R = t->p.R;
   const long long M2 = (long long)Mg * Mg, G3 = M2 * Mg;
   const bool periodic = t->p.kernel == CC_KERNEL_PERIODIC;
   const bool f64 = sizeof(T) == 8;
-  Workspace& w = t->ws;
-  const int chunk = (int)((size_t)w.chunk * sizeof(double) / sizeof(T));
   T* occ = reinterpret_cast<T*>(w.occ);
   T* P = reinterpret_cast<T*>(w.P);
   T* Q = reinterpret_cast<T*>(w.Q);
@@ -340,6 +341,13 @@ static cc_status exchange_simt(cc_tables t, int R_F, T* eps, double* Ex, cudaStr
   return CC_OK;
 }
 
+// the plain path on the handle's own workspace (sized in doubles at build time)
+template <typename T>
+static cc_status exchange_simt(cc_tables t, int R_F, T* eps, double* Ex, cudaStream_t st) {
+  const int chunk = (int)((size_t)t->ws.chunk * sizeof(double) / sizeof(T));
+  return exchange_simt_ws<T>(t, t->ws, chunk, R_F, eps, Ex, st);
+}
+
 }  // namespace cc
 
 using namespace cc;
@@ -370,4 +378,66 @@ extern "C" cc_status cc_set_gemm_tiles(int precision, int small_tile, int large_
   g_tile_large[f] = large_tile;
   if (threshold >= 0) g_tile_threshold = threshold;
   return CC_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// Some callers cannot call cudaMalloc when they need the exchange sums: code that runs
+// under a framework's caching allocator which owns the device memory and must not have
+// memory taken behind its back, and latency-critical loops where cudaMalloc's implicit
+// device synchronisation would stall every other stream.  cc_exchange_sums_noalloc serves
+// them: it runs the plain FP32 path of cc_exchange_sums with its scratch (occupation
+// tensor, accumulator, node-chunk intermediates, reduction partials) in the fixed device
+// array below instead of the handle's workspace.  The array lives in the library image,
+// so every GPU that loads the library holds it until the process exits.
+namespace cc {
+constexpr size_t kNoAllocScratchBytes = 16ull << 20;  // 16 MiB per device
+constexpr int kNoAllocMaxR = 31;                      // grid side (2R + 1) <= 63
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace cc
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[cc::kNoAllocScratchBytes];
+
+namespace cc {
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per device (with
+// that device current) and cached.
+static cc_status noalloc_scratch(void** out) {
+  int dev = 0;
+  CC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return CC_ERR_RANGE;
+  void* p = __atomic_load_n(&g_noalloc_ptr[dev], __ATOMIC_ACQUIRE);
+  if (!p) {
+    CC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    __atomic_store_n(&g_noalloc_ptr[dev], p, __ATOMIC_RELEASE);
+  }
+  *out = p;
+  return CC_OK;
+}
+}  // namespace cc
+
+extern "C" cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_dev,
+                                              double* Ex_dev, void* stream) {
+  if (!t || !eps_dev || !Ex_dev) return CC_ERR_ARG;
+  if (t->p.R > kNoAllocMaxR) return CC_ERR_RANGE;
+  if (R_F < 1 || R_F > t->p.R) return CC_ERR_RANGE;
+  void* base = nullptr;
+  CC_TRY(noalloc_scratch(&base));
+  // layout: occ | E | part (each start 256-byte aligned) | P[chunk][Mg^3] | Q[chunk][Mg^3]
+  const size_t G3 = (size_t)t->Mg * t->Mg * t->Mg;
+  const size_t tensor = G3 * sizeof(float);
+  const size_t vol = (tensor + 255) & ~(size_t)255;
+  const size_t fixed = 2 * vol + ((sizeof(double) * kRedBlocks + 255) & ~(size_t)255);
+  if (fixed + 2 * tensor > kNoAllocScratchBytes) return CC_ERR_RANGE;
+  size_t chunk = (kNoAllocScratchBytes - fixed) / (2 * tensor);
+  if (chunk > (size_t)t->S_eff) chunk = t->S_eff;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  Workspace w;
+  w.occ = b;
+  w.E = b + vol;
+  w.part = reinterpret_cast<double*>(b + 2 * vol);
+  w.P = b + fixed;
+  w.Q = b + fixed + chunk * tensor;
+  return exchange_simt_ws<float>(t, w, (int)chunk, R_F, eps_dev, Ex_dev, as_stream(stream));
 }

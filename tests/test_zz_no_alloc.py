@@ -1,0 +1,62 @@
+"""The allocation-free exchange entry point (cc_exchange_sums_noalloc).
+
+It exists for callers that cannot call cudaMalloc where they need the exchange sums
+(code under a framework's caching allocator that owns the device memory, latency-
+critical loops that cannot afford cudaMalloc's implicit synchronisation).  It must give
+the same sums as the ordinary FP32 entry point cc_exchange_sums, call after call, while
+keeping its scratch in the library's fixed device array.  This file is collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_common import TOL_FP32, need_gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _reference(cc, t, R_F, dev):
+    import torch
+    Mg = t.info["Mg"]
+    eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+    Ex = torch.empty(2, dtype=torch.float64, device=dev)
+    cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")
+    torch.cuda.synchronize()
+    return eps.cpu().numpy().astype(np.float64), Ex.cpu().numpy()
+
+
+@pytest.mark.parametrize("R,L,S,R_F", [(13, 20.0, 64, 8), (31, 40.0, 96, 20)])
+def test_noalloc_matches_existing_entry_point(R, L, S, R_F):
+    import torch
+    import paper_1502_08043_gb300 as cc
+    dev = need_gpu()
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    ref_eps, ref_Ex = _reference(cc, t, R_F, dev)
+    Mg = t.info["Mg"]
+    for _ in range(2):   # two calls in a row through the C ABI
+        eps = torch.full((Mg ** 3,), float("nan"), dtype=torch.float32, device=dev)
+        Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+        st = cc.lib().cc_exchange_sums_noalloc(
+            t.handle, R_F, ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(Ex.data_ptr()),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == 0
+        torch.cuda.synchronize()
+        got = eps.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got == 0, ref_eps == 0)
+        assert rel_err(got, ref_eps) < TOL_FP32
+        assert abs(Ex.cpu().numpy()[0] - ref_Ex[0]) < TOL_FP32 * abs(ref_Ex[0])
+    t.free()
+
+
+def test_noalloc_rejects_sizes_beyond_its_array():
+    import torch
+    import paper_1502_08043_gb300 as cc
+    dev = need_gpu()
+    t = cc.build_tables("periodic", R=32, L=40.0, S=48)
+    eps = torch.empty(t.info["Mg"] ** 3, dtype=torch.float32, device=dev)
+    Ex = torch.empty(2, dtype=torch.float64, device=dev)
+    with pytest.raises(cc.CoulombError) as e:
+        cc.exchange_sums_noalloc(t, 10, eps, Ex)
+    assert e.value.status == 2
+    t.free()
