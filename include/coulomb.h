@@ -86,9 +86,14 @@ typedef enum {
  *   prune_tol PERIODIC only: drop node s when w_s exp(-a_s) < prune_tol / (12 R^2);
  *             0 keeps all nodes.  Negative selects 1e-9.  Ignored for BOX.
  * Default rule: (S, R) = (32, 4) -> (2, 10); (64, 13) -> (3, 21); (96, 31) -> (4, 29);
- * (128, 63) -> (5, 34); otherwise n_sub = max(1, floor(log5(12 R^2)) - 1) and
- * q_tail = round(0.3 S).  Every sub-interval gets floor((S - q_tail)/(n_sub + 1))
- * points and the first (S - q_tail) mod (n_sub + 1) get one more. */
+ * (128, 63) -> (5, 34); otherwise a search: with r = max(1, floor(log5(12 R^2)) - 1),
+ * n_sub in {r, r + 1} and q_tail in 3 .. max(3, round(0.45 S)) (S - q_tail >= n_sub + 1),
+ * the pair minimising max_m |sum_s w_s exp(-a_s m) - 1/m| m over the 96 points
+ * m_k = 1 + floor((12 R^2 - 1) k^3 / 95^3), floored at 1e-10 (ties within 0.1 % go to the smaller
+ * n_sub, then q_tail); fewer than 5 nodes: (0, S / 2).  The same rule applies to BOX
+ * tables (give the paper's meshes explicitly there).  Every sub-interval gets
+ * floor((S - q_tail)/(n_sub + 1)) points and the first (S - q_tail) mod (n_sub + 1)
+ * get one more. */
 typedef struct {
   int kernel;
   int R;
@@ -139,6 +144,10 @@ cc_status cc_tables_save(cc_tables t, const char* path);
 cc_status cc_tables_load(const char* path, void* stream, cc_tables* out);
 
 cc_status cc_tables_free(cc_tables t);
+
+/* The mesh (n_sub, q_tail) that cc_build_tables picks when both are left negative, for
+ * S nodes at cutoff R (host only, no GPU): see the default rule above. */
+cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail);
 
 /* Basis of cutoff R (Sec. II Eq. 1 with |n|^2 <= R^2) in canonical order.  Writes the
  * count to *Nb; if vec_host is not NULL it must hold 4 * Nb int8 and receives
@@ -209,6 +218,47 @@ cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
  * threshold = grid side up to which 32x32 tiles are always used (< 0 keeps it).
  * Process-wide setting; not part of the paper (a tuning knob of this implementation). */
 cc_status cc_set_gemm_tiles(int precision, int small_tile, int large_tile, int threshold);
+
+/* ---- batched engine: many independent boxes in one persistent, graph-captured launch.
+ * Box i has its own cutoff, side, node count and mesh (p, any kernel; defaults as in
+ * cc_build_tables) and Fermi radius R_F (1 <= R_F <= p.R); grid side 2 p.R + 1 <= 49.
+ * Exchange sums of every box (Sec. III) come from one launch that takes work items
+ * (box, group of nodes) from an atomic counter, longest first; the last CTA to finish a
+ * box writes its eps block and E_x.  The first call for a given (precision, eps_dev,
+ * Ex_dev) captures the launch in a CUDA graph, later calls replay it. */
+typedef struct {
+  cc_table_params p;
+  int R_F;
+} cc_box;
+typedef struct cc_batch_s* cc_batch;
+
+/* Build the tables of every box and the launch plan.  Synchronous; owns device memory. */
+cc_status cc_batch_create(const cc_box* boxes_host, int nbox, void* stream, cc_batch* out);
+
+/* nbox; eps_offsets_host[nbox + 1] (element offset of box i's (2R_i+1)^3 block in eps_dev,
+ * last entry = total); number of work items; device bytes.  Any pointer may be NULL. */
+cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets_host, int* n_items,
+                        size_t* device_bytes);
+
+/* Exchange sums of all boxes: eps_dev (float or double by precision: CC_PREC_FP32 or
+ * CC_PREC_FP64) holds every box's grid at its offset, Ex_dev[2 i], Ex_dev[2 i + 1] =
+ * E_x^sigma and total of box i.  Stream ordered; calls on one batch must not overlap. */
+cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
+                            void* stream);
+
+/* Launch shape: CTAs per SM (1..8), oversubscription (work items per CTA slot, the
+ * granularity big boxes are cut to), prefer_smem (intermediates in shared memory when
+ * they fit).  Drops captured graphs. */
+cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub, int prefer_smem);
+
+/* Autotuner: times every launch shape (CTAs per SM in {1, 2}, oversubscription in
+ * {1, 2, 4, 8}, shared or global intermediates) with CUDA events, median of `reps`
+ * replays, keeps the fastest.  choice_host[3] receives it, *ms_host its time.
+ * Writes eps_dev / Ex_dev (valid sums) while timing.  Synchronous. */
+cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, double* Ex_dev, int reps,
+                        int* choice_host, float* ms_host, void* stream);
+
+cc_status cc_batch_free(cc_batch b);
 
 /* Human-readable name of a status; detail of the last CUDA failure of this thread. */
 const char* cc_status_string(cc_status s);

@@ -86,18 +86,50 @@ def paper_mesh2(q: int, q_tail: int = 90):
     return laplace_mesh(8 * q + q_tail, 7, q_tail, 1.0)
 
 
+def tune_points(R: int):
+    """The |n|^2 values a mesh is judged on: m_k = 1 + floor((12 R^2 - 1) k^3 / 95^3),
+    k = 0..95 (dense near m = 1, reaching the largest |n|^2 of the (2R+1)^3 grid)."""
+    top = 12 * R * R - 1
+    return np.unique(np.array([1 + (top * k ** 3) // 857375 for k in range(96)], dtype=np.int64))
+
+
+def mesh_error(S: int, n_sub: int, q_tail: int, R: int) -> float:
+    """max_m |sum_s w_s exp(-a_s m) - 1/m| * m over tune_points(R) (relative error of the
+    node sum of 1/m; the Laplace form of the periodic kernel in index units)."""
+    a, w, _ = laplace_mesh(S, n_sub, q_tail)
+    m = tune_points(R).astype(np.float64)
+    return float(np.max(np.abs(np.exp(-np.outer(m, a)) @ w - 1.0 / m) * m))
+
+
 def default_periodic_mesh(S: int, R: int):
     """(n_sub, q_tail) of the periodic kernel for S nodes at cutoff R.
 
     Explicit choices for the four single-box workloads (S, R) = (32, 4), (64, 13),
-    (96, 31), (128, 63), and the rule n_sub = max(1, floor(log5(12 R^2)) - 1),
-    q_tail = round(0.3 S) otherwise.
+    (96, 31), (128, 63).  Otherwise a small search (the paper's remark that the split
+    of the Laplace integral decides how many points are needed, Sec. II): with
+    r = max(1, floor(log5(12 R^2)) - 1), every n_sub in {r, r + 1} and q_tail in
+    3 .. max(3, round(0.45 S)) with S - q_tail >= n_sub + 1, the pair with the smallest
+    mesh_error (floored at 1e-10, where FP64 rounding noise starts to decide) wins; candidates are visited n_sub ascending, then q_tail ascending, and
+    replace the best only when smaller by more than 0.1 % relative (errors on a plateau
+    differ in their last digits between implementations; the margin keeps the choice
+    reproducible).
     """
     table = {(32, 4): (2, 10), (64, 13): (3, 21), (96, 31): (4, 29), (128, 63): (5, 34)}
     if (S, R) in table:
         return table[(S, R)]
-    n_sub = max(1, int(np.floor(np.log(12.0 * R * R) / np.log(5.0))) - 1)
-    return n_sub, int(np.rint(0.3 * S))
+    r = max(1, int(np.floor(np.log(12.0 * R * R) / np.log(5.0))) - 1)
+    # (fewer than 5 nodes leave no candidate: one interval plus a tail of S // 2)
+    best, arg = None, None
+    for n_sub in (r, r + 1):
+        for q_tail in range(3, max(3, int(np.rint(0.45 * S))) + 1):
+            if S - q_tail < n_sub + 1:
+                continue
+            e = max(mesh_error(S, n_sub, q_tail, R), 1e-10)   # below: rounding noise
+            if best is None or e < best * (1.0 - 1e-3):
+                best, arg = e, (n_sub, q_tail)
+    if arg is None:  # fewer than 5 nodes: one interval and a tail of half the nodes
+        return 0, max(1, S // 2)
+    return arg
 
 
 def prune_periodic(alpha_idx, w, R: int, tol: float):

@@ -54,6 +54,10 @@ class TablesInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_size_t)]
 
 
+class Box(ctypes.Structure):
+    _fields_ = [("p", TableParams), ("R_F", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -67,12 +71,19 @@ SIGNATURES = {
     "cc_tables_load": (_I, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "cc_tables_free": (_I, [_P]),
     "cc_basis": (_I, [_I, ctypes.POINTER(_I), _P]),
+    "cc_default_mesh": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "cc_reconstruct_integrals": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _P]),
     "cc_pair_matrix": (_I, [_P, _I64, _I64, _I, _I, _P, _P]),
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
     "cc_set_gemm_tiles": (_I, [_I, _I, _I, _I]),
     "cc_mixed_status": (_I, [_P, _P, _I]),
     "cc_exchange_sums_noalloc": (_I, [_P, _I, _P, _P, _P]),
+    "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
+    "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),
+    "cc_batch_exchange": (_I, [_P, _I, _P, _P, _P]),
+    "cc_batch_set_plan": (_I, [_P, _I, _I, _I]),
+    "cc_batch_tune": (_I, [_P, _I, _P, _P, _I, _P, _P, _P]),
+    "cc_batch_free": (_I, [_P]),
     "cc_status_string": (ctypes.c_char_p, [_I]),
     "cc_last_error": (ctypes.c_char_p, []),
 }
@@ -198,6 +209,15 @@ def load_tables(path, stream=None) -> Tables:
     return Tables(h.value)
 
 
+def default_mesh(S: int, R: int):
+    """cc_default_mesh: (n_sub, q_tail) chosen when both are left to the library."""
+    n = ctypes.c_int()
+    q = ctypes.c_int()
+    _check("cc_default_mesh", lib().cc_default_mesh(int(S), int(R), ctypes.byref(n),
+                                                    ctypes.byref(q)))
+    return n.value, q.value
+
+
 def basis(R: int) -> np.ndarray:
     """cc_basis: int8[Nb, 4] vectors (n_x, n_y, n_z, 0) in canonical order."""
     nb = ctypes.c_int()
@@ -289,3 +309,75 @@ def mixed_status(tables: Tables, clear=True) -> int:
 def set_gemm_tiles(precision, small_tile, large_tile, threshold=-1):
     _check("cc_set_gemm_tiles", lib().cc_set_gemm_tiles(PRECISIONS[precision], small_tile,
                                                         large_tile, threshold))
+
+
+class Batch:
+    """Many independent boxes whose exchange sums run in one persistent, graph-captured
+    launch (cc_batch_*).  boxes: dicts with R, L, R_F, S and optionally kernel, n_sub,
+    q_tail, alpha_c, prune_tol."""
+
+    def __init__(self, boxes, stream=None):
+        arr = (Box * len(boxes))()
+        for i, b in enumerate(boxes):
+            k = b.get("kernel", "periodic")
+            arr[i].p = TableParams(KERNELS[k] if isinstance(k, str) else int(k), int(b["R"]),
+                                   float(b["L"]), int(b["S"]), int(b.get("n_sub", -1)),
+                                   int(b.get("q_tail", -1)), float(b.get("alpha_c", 1.0)),
+                                   float(b.get("prune_tol", -1.0)))
+            arr[i].R_F = int(b["R_F"])
+        h = ctypes.c_void_p()
+        _check("cc_batch_create", lib().cc_batch_create(arr, len(boxes), _stream(stream),
+                                                        ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int()
+        items = ctypes.c_int()
+        nbytes = ctypes.c_size_t()
+        offs = np.zeros(len(boxes) + 1, dtype=np.int64)
+        _check("cc_batch_info", lib().cc_batch_info(h, ctypes.byref(n), offs.ctypes.data,
+                                                    ctypes.byref(items), ctypes.byref(nbytes)))
+        self.nbox = n.value
+        self.offsets = offs
+        self.n_items = items.value
+        self.device_bytes = nbytes.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch was freed")
+        return self._h
+
+    def exchange(self, eps, Ex, stream=None):
+        """eps: float32 / float64 [offsets[-1]]; Ex: float64 [nbox, 2]."""
+        if eps.numel() < int(self.offsets[-1]) or Ex.numel() < 2 * self.nbox:
+            raise ValueError("output too small")
+        _check("cc_batch_exchange", lib().cc_batch_exchange(
+            self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), _stream(stream, eps)))
+        return eps, Ex
+
+    def set_plan(self, ctas_per_sm=1, oversub=2, prefer_smem=True):
+        _check("cc_batch_set_plan", lib().cc_batch_set_plan(self.handle, ctas_per_sm, oversub,
+                                                            1 if prefer_smem else 0))
+
+    def tune(self, eps, Ex, reps=5, stream=None):
+        choice = np.zeros(3, dtype=np.int32)
+        ms = ctypes.c_float()
+        _check("cc_batch_tune", lib().cc_batch_tune(
+            self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), int(reps), choice.ctypes.data,
+            ctypes.byref(ms), _stream(stream, eps)))
+        n = ctypes.c_int()
+        items = ctypes.c_int()
+        lib().cc_batch_info(self.handle, ctypes.byref(n), None, ctypes.byref(items), None)
+        self.n_items = items.value
+        return {"ctas_per_sm": int(choice[0]), "oversub": int(choice[1]),
+                "smem_intermediates": bool(choice[2]), "ms": ms.value}
+
+    def free(self):
+        if self._h is not None:
+            _check("cc_batch_free", lib().cc_batch_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,401 @@
+// Fused small-grid exchange sums (single box, grid side <= 49) and the batched engine:
+// many independent boxes with uneven cutoffs, Fermi radii and quadrature orders in one
+// persistent launch, captured once in a CUDA graph and replayed.
+//
+// Work items are (box, group of consecutive nodes); a persistent grid takes them from an
+// atomic counter in order of decreasing cost (longest-processing-time first), and the
+// CTA that completes the last item of a box finalises that box (see fused.cuh).  The
+// granularity of the items (how many items a big box is cut into), the number of CTAs
+// per SM and the placement of the per-node intermediates (shared or global memory) are
+// chosen by cc_batch_tune, which times each candidate with CUDA events.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fused.cuh"
+
+namespace cc {
+
+struct FusedPlan {
+  int n_boxes = 0, n_items = 0, grid = 0, ctas_per_sm = 1, oversub = 2, prefer_smem = 1;
+  long long max_g3 = 0;
+  FusedBox<float>* boxes32 = nullptr;
+  FusedBox<double>* boxes64 = nullptr;
+  FusedItem* items = nullptr;
+  int* counters = nullptr;  // [1 + n_boxes]: work counter, per-box done counters
+  void* part = nullptr;     // item partials (sized for double)
+  void* scratch = nullptr;  // per-CTA P / Q when they do not fit in shared memory
+  size_t part_bytes = 0, scratch_bytes = 0, bytes = 0;
+};
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+static constexpr size_t kFusedSmemCap = 200 * 1024;
+
+static void plan_free(FusedPlan* p) {
+  void* ptrs[] = {p->boxes32, p->boxes64, p->items, p->counters, p->part, p->scratch};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  *p = FusedPlan();
+}
+
+struct BoxIn {
+  cc_tables t;
+  int R_F;
+  long long eps_off;
+};
+
+// Build a plan: cut box b into ceil(cost_b / target) items (target from the total cost,
+// the grid and the oversubscription factor), order items by decreasing cost.
+static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, int oversub,
+                            int prefer_smem, FusedPlan* out) {
+  FusedPlan p;
+  p.n_boxes = (int)boxes.size();
+  p.ctas_per_sm = ctas_per_sm;
+  p.oversub = oversub;
+  p.prefer_smem = prefer_smem;
+  double total = 0.0;
+  for (const BoxIn& b : boxes) {
+    const double mg = b.t->Mg;
+    total += mg * mg * mg * mg * b.t->S_eff;
+    p.max_g3 = std::max(p.max_g3, (long long)b.t->Mg * b.t->Mg * b.t->Mg);
+  }
+  const int slots = sm_count() * ctas_per_sm;
+  const double target = total / ((double)slots * oversub);
+  std::vector<FusedItem> items;
+  std::vector<double> cost;
+  std::vector<int> n_items(boxes.size());
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const cc_tables t = boxes[b].t;
+    const double per_node = (double)t->Mg * t->Mg * t->Mg * t->Mg;
+    int k = (int)std::ceil(per_node * t->S_eff / std::max(target, 1.0));
+    k = std::max(1, std::min(k, t->S_eff));
+    n_items[b] = k;
+    for (int g = 0; g < k; ++g) {
+      const int s0 = (int)((long long)t->S_eff * g / k), s1 = (int)((long long)t->S_eff * (g + 1) / k);
+      items.push_back({(int)b, s0, s1, g});
+      cost.push_back(per_node * (s1 - s0));
+    }
+  }
+  std::vector<int> order(items.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<FusedItem> sorted(items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+  p.n_items = (int)sorted.size();
+  p.grid = std::max(1, std::min(p.n_items, slots));
+  // partials
+  std::vector<long long> part_off(boxes.size());
+  long long acc = 0;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    part_off[b] = acc;
+    const long long g3 = (long long)boxes[b].t->Mg * boxes[b].t->Mg * boxes[b].t->Mg;
+    acc += (long long)n_items[b] * 2 * g3;
+  }
+  p.part_bytes = (size_t)acc * sizeof(double);
+  p.scratch_bytes = (size_t)p.grid * 2 * p.max_g3 * sizeof(double);
+  auto alloc = [&](void** ptr, size_t bytes) -> cc_status {
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      set_last_error("cudaMalloc(fused plan)", e);
+      return CC_ERR_ALLOC;
+    }
+    p.bytes += bytes;
+    return CC_OK;
+  };
+  cc_status s = CC_OK;
+  if (s == CC_OK) s = alloc((void**)&p.boxes32, sizeof(FusedBox<float>) * boxes.size());
+  if (s == CC_OK) s = alloc((void**)&p.boxes64, sizeof(FusedBox<double>) * boxes.size());
+  if (s == CC_OK) s = alloc((void**)&p.items, sizeof(FusedItem) * sorted.size());
+  if (s == CC_OK) s = alloc((void**)&p.counters, sizeof(int) * (1 + boxes.size()));
+  if (s == CC_OK) s = alloc(&p.part, p.part_bytes);
+  if (s == CC_OK) s = alloc(&p.scratch, p.scratch_bytes);
+  if (s != CC_OK) {
+    plan_free(&p);
+    return s;
+  }
+  std::vector<FusedBox<float>> b32(boxes.size());
+  std::vector<FusedBox<double>> b64(boxes.size());
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const cc_tables t = boxes[b].t;
+    const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
+    b32[b] = FusedBox<float>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, n_items[b],
+                             t->pref, t->d.Tm32, t->d.WDm32, t->d.Dbar32,
+                             reinterpret_cast<float*>(p.part) + part_off[b], boxes[b].eps_off,
+                             (int)b};
+    b64[b] = FusedBox<double>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, n_items[b],
+                              t->pref, t->d.Tm64, t->d.WDm64, t->d.Dbar64,
+                              reinterpret_cast<double*>(p.part) + part_off[b], boxes[b].eps_off,
+                              (int)b};
+  }
+  if (cudaMemcpy(p.boxes32, b32.data(), sizeof(FusedBox<float>) * b32.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.boxes64, b64.data(), sizeof(FusedBox<double>) * b64.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.items, sorted.data(), sizeof(FusedItem) * sorted.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    plan_free(&p);
+    return CC_ERR_CUDA;
+  }
+  *out = p;
+  return CC_OK;
+}
+
+template <typename T>
+static cc_status plan_launch(const FusedPlan& p, int rf_override, T* eps, double* Ex,
+                             cudaStream_t st) {
+  const size_t pq = (size_t)2 * p.max_g3 * sizeof(T);
+  const int smem_pq = (p.prefer_smem && pq <= kFusedSmemCap) ? 1 : 0;
+  const size_t smem = smem_pq ? pq : 0;
+  auto kern = k_fused_exchange<T>;
+  CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap));
+  int per_sm = 0;
+  CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem));
+  int grid = std::min(p.grid, std::max(1, per_sm) * sm_count());
+  CC_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int) * (1 + p.n_boxes), st));
+  const FusedBox<T>* boxes;
+  if constexpr (sizeof(T) == 4) boxes = reinterpret_cast<const FusedBox<T>*>(p.boxes32);
+  else boxes = reinterpret_cast<const FusedBox<T>*>(p.boxes64);
+  kern<<<grid, kFusedThreads, smem, st>>>(boxes, p.items, p.n_items, p.counters, p.counters + 1,
+                                          reinterpret_cast<T*>(p.scratch), p.max_g3, smem_pq,
+                                          rf_override, eps, Ex);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+// ---------------------------------------------------------------- single box hook
+cc_status fused_single_alloc(cc_tables t) {
+  if (t->Mg > kFusedMaxMg || t->fused) return CC_OK;
+  FusedPlan* p = new (std::nothrow) FusedPlan();
+  if (!p) return CC_ERR_ALLOC;
+  std::vector<BoxIn> one{{t, 1, 0}};
+  // one node per item: S_eff CTAs work on one box
+  cc_status s = plan_build(one, 1, (int)1e6, 1, p);
+  if (s != CC_OK) {
+    delete p;
+    return s;
+  }
+  t->fused = p;
+  t->device_bytes += p->bytes;
+  return CC_OK;
+}
+
+void fused_single_free(cc_tables t) {
+  FusedPlan* p = reinterpret_cast<FusedPlan*>(t->fused);
+  if (!p) return;
+  plan_free(p);
+  delete p;
+  t->fused = nullptr;
+}
+
+cc_status fused_single_exchange(cc_tables t, int R_F, int precision, void* eps, double* Ex,
+                                cudaStream_t st) {
+  FusedPlan* p = reinterpret_cast<FusedPlan*>(t->fused);
+  if (!p) return CC_ERR_NOTSUPP;
+  if (precision == CC_PREC_FP32) return plan_launch<float>(*p, R_F, (float*)eps, Ex, st);
+  return plan_launch<double>(*p, R_F, (double*)eps, Ex, st);
+}
+
+}  // namespace cc
+
+// ---------------------------------------------------------------- batch handle
+struct cc_batch_s {
+  std::vector<cc_tables> tabs;
+  std::vector<cc_box> spec;
+  std::vector<long long> eps_off;  // nbox + 1
+  cc::FusedPlan plan;
+  struct Graph {
+    int prec;
+    void* eps;
+    double* Ex;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  int device = 0;
+};
+
+using namespace cc;
+
+static void batch_drop_graphs(cc_batch b) {
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+}
+
+static cc_status batch_plan(cc_batch b, int ctas_per_sm, int oversub, int prefer_smem) {
+  std::vector<BoxIn> in;
+  for (size_t i = 0; i < b->tabs.size(); ++i) in.push_back({b->tabs[i], b->spec[i].R_F, b->eps_off[i]});
+  FusedPlan p;
+  CC_TRY(plan_build(in, ctas_per_sm, oversub, prefer_smem, &p));
+  batch_drop_graphs(b);
+  plan_free(&b->plan);
+  b->plan = p;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_create(const cc_box* boxes_host, int nbox, void* stream,
+                                     cc_batch* out) {
+  if (!boxes_host || !out || nbox < 1 || nbox > 65536) return CC_ERR_ARG;
+  *out = nullptr;
+  cc_batch b = new (std::nothrow) cc_batch_s();
+  if (!b) return CC_ERR_ALLOC;
+  cudaGetDevice(&b->device);
+  cc_status s = CC_OK;
+  long long off = 0;
+  for (int i = 0; i < nbox && s == CC_OK; ++i) {
+    const cc_box& bx = boxes_host[i];
+    if (bx.p.R < 1 || 2 * bx.p.R + 1 > kFusedMaxMg || bx.R_F < 1 || bx.R_F > bx.p.R) {
+      s = CC_ERR_RANGE;
+      break;
+    }
+    cc_tables t = nullptr;
+    s = build_tables_internal(&bx.p, as_stream(stream), false, &t);
+    if (s != CC_OK) break;
+    b->tabs.push_back(t);
+    b->spec.push_back(bx);
+    b->eps_off.push_back(off);
+    off += (long long)t->Mg * t->Mg * t->Mg;
+  }
+  b->eps_off.push_back(off);
+  if (s == CC_OK) s = batch_plan(b, 1, 2, 1);
+  if (s != CC_OK) {
+    cc_batch_free(b);
+    return s;
+  }
+  *out = b;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets_host,
+                                   int* n_items, size_t* device_bytes) {
+  if (!b) return CC_ERR_ARG;
+  if (nbox) *nbox = (int)b->tabs.size();
+  if (eps_offsets_host)
+    for (size_t i = 0; i < b->eps_off.size(); ++i) eps_offsets_host[i] = b->eps_off[i];
+  if (n_items) *n_items = b->plan.n_items;
+  if (device_bytes) {
+    size_t s = b->plan.bytes;
+    for (cc_tables t : b->tabs) s += t->device_bytes;
+    *device_bytes = s;
+  }
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub,
+                                       int prefer_smem) {
+  if (!b || ctas_per_sm < 1 || ctas_per_sm > 8 || oversub < 1 || oversub > 1024) return CC_ERR_ARG;
+  return batch_plan(b, ctas_per_sm, oversub, prefer_smem ? 1 : 0);
+}
+
+extern "C" cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
+                                       void* stream) {
+  if (!b || !eps_dev || !Ex_dev) return CC_ERR_ARG;
+  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
+  cudaStream_t st = as_stream(stream);
+  for (auto& g : b->graphs)
+    if (g.prec == precision && g.eps == eps_dev && g.Ex == Ex_dev) {
+      CC_CUDA(cudaGraphLaunch(g.exec, st));
+      return CC_OK;
+    }
+  // capture the whole batch (counter reset + one persistent launch) once per outputs
+  cudaStream_t cap;
+  CC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cc_status s = CC_OK;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = CC_ERR_CUDA;
+  if (s == CC_OK) {
+    s = precision == CC_PREC_FP32
+            ? plan_launch<float>(b->plan, 0, (float*)eps_dev, Ex_dev, cap)
+            : plan_launch<double>(b->plan, 0, (double*)eps_dev, Ex_dev, cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (s == CC_OK && e != cudaSuccess) {
+      set_last_error("cudaStreamEndCapture", e);
+      s = CC_ERR_CUDA;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (s == CC_OK) {
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      set_last_error("cudaGraphInstantiate", e);
+      s = CC_ERR_CUDA;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  CC_TRY(s);
+  b->graphs.push_back({precision, eps_dev, Ex_dev, exec});
+  CC_CUDA(cudaGraphLaunch(exec, st));
+  return CC_OK;
+}
+
+// Autotuner: time every (CTAs per SM, oversubscription, intermediates placement)
+// candidate with CUDA events (median of `reps` graph replays after one warm-up) and keep
+// the fastest.  Writes the choice to choice_host[3] and its time to *ms_host.
+extern "C" cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
+                                   int reps, int* choice_host, float* ms_host, void* stream) {
+  if (!b || !eps_dev || !Ex_dev || reps < 1) return CC_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  const int cps[] = {1, 2};
+  const int ovs[] = {1, 2, 4, 8};
+  const int plc[] = {1, 0};
+  float best = 1e30f;
+  int bc[3] = {1, 2, 1};
+  cudaEvent_t e0, e1;
+  CC_CUDA(cudaEventCreate(&e0));
+  CC_CUDA(cudaEventCreate(&e1));
+  cc_status s = CC_OK;
+  for (int c : cps)
+    for (int o : ovs)
+      for (int pl : plc) {
+        if (s != CC_OK) break;
+        s = batch_plan(b, c, o, pl);
+        if (s != CC_OK) break;
+        s = cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream);
+        std::vector<float> t;
+        for (int r = 0; r < reps && s == CC_OK; ++r) {
+          cudaEventRecord(e0, st);
+          s = cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) s = CC_ERR_CUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t.push_back(ms);
+        }
+        if (s != CC_OK) break;
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (med < best) {
+          best = med;
+          bc[0] = c;
+          bc[1] = o;
+          bc[2] = pl;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CC_TRY(s);
+  CC_TRY(batch_plan(b, bc[0], bc[1], bc[2]));
+  if (choice_host) memcpy(choice_host, bc, sizeof(bc));
+  if (ms_host) *ms_host = best;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_free(cc_batch b) {
+  if (!b) return CC_ERR_ARG;
+  batch_drop_graphs(b);
+  plan_free(&b->plan);
+  for (cc_tables t : b->tabs) cc_tables_free(t);
+  delete b;
+  return CC_OK;
+}

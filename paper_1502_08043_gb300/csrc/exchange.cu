@@ -357,6 +357,9 @@ extern "C" cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void*
   if (!t || !eps_dev || !Ex_dev) return CC_ERR_ARG;
   if (R_F < 1 || R_F > t->p.R) return CC_ERR_RANGE;
   cudaStream_t st = as_stream(stream);
+  // grids up to 49 per side: fused per-node work items with shared-memory intermediates
+  if (t->fused && (precision == CC_PREC_FP32 || precision == CC_PREC_FP64))
+    return fused_single_exchange(t, R_F, precision, eps_dev, Ex_dev, st);
   switch (precision) {
     case CC_PREC_FP32: return exchange_simt<float>(t, R_F, (float*)eps_dev, Ex_dev, st);
     case CC_PREC_FP64: return exchange_simt<double>(t, R_F, (double*)eps_dev, Ex_dev, st);

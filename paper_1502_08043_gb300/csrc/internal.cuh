@@ -32,6 +32,7 @@ void set_last_error(const char* what, cudaError_t e);
 constexpr int kMaxR = 127;          // Delta = 0..254 fits the 8-bit packed deltas
 constexpr int kMaxS = 1024;
 constexpr int kBoxGLPoints = 1200;  // Gauss-Legendre points of one box axis integral
+constexpr int kFusedMaxMg = 49;     // grid side served by the fused small-grid exchange
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -82,6 +83,7 @@ struct cc_tables_s {
   std::vector<int> kept_idx;      // indices of kept nodes
   cc::DevTables d;
   cc::Workspace ws;
+  void* fused = nullptr;          // fused small-grid exchange plan (grid side <= 49)
   size_t table_bytes = 0;
   size_t device_bytes = 0;
 };
@@ -91,6 +93,13 @@ namespace cc {
 cc_status resolve_params(const cc_table_params* in, cc_table_params* out);
 void default_mesh(int S, int R, int* n_sub, int* q_tail);
 std::vector<int8_t> make_basis(int R);
+cc_status build_tables_internal(const cc_table_params* params, cudaStream_t st,
+                                bool workspaces, cc_tables* out);
+// batched.cu
+cc_status fused_single_alloc(cc_tables t);
+void fused_single_free(cc_tables t);
+cc_status fused_single_exchange(cc_tables t, int R_F, int precision, void* eps, double* Ex,
+                                cudaStream_t st);
 // exchange.cu
 cc_status workspace_alloc(cc_tables t);
 void workspace_free(cc_tables t);

@@ -33,7 +33,7 @@ void set_last_error(const char* what, cudaError_t e) {
 }
 
 // ---------------------------------------------------------------- device: nodes
-__device__ void gl_node(int n, int i, double* x, double* w) {
+__host__ __device__ void gl_node(int n, int i, double* x, double* w) {
   // i-th node in ascending order on [-1, 1]
   const int j = n - 1 - i;
   double z = cos(kPi * (j + 0.75) / (n + 0.5));
@@ -180,20 +180,71 @@ __global__ void k_dbar(const double* WDm64, int S_eff, int Mg, double* D64, floa
 }
 
 // ---------------------------------------------------------------- host helpers
+// Host copy of the node set of a mesh (same construction as k_mesh_nodes).
+static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, std::vector<double>& a,
+                      std::vector<double>& w);
+
+// max_m |sum_s w_s exp(-a_s m) - 1/m| m over m_k = 1 + floor((12R^2 - 1) k^3 / 95^3),
+// k = 0..95: the relative error of the node sum of 1/m (periodic kernel, index units)
+static double mesh_error(int S, int n_sub, int q_tail, int R) {
+  std::vector<double> a, w;
+  host_mesh(S, n_sub, q_tail, 1.0, a, w);
+  const long long top = 12LL * R * R - 1;
+  long long prev = -1;
+  double worst = 0.0;
+  for (long long k = 0; k < 96; ++k) {
+    const long long m = 1 + (top * k * k * k) / 857375LL;
+    if (m == prev) continue;
+    prev = m;
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += w[s] * exp(-a[s] * (double)m);
+    const double e = fabs(v - 1.0 / (double)m) * (double)m;
+    if (e > worst) worst = e;
+  }
+  return worst;
+}
+
+// Default mesh of the periodic kernel: explicit choices for (S, R) = (32, 4), (64, 13),
+// (96, 31), (128, 63); otherwise the pair (n_sub, q_tail) with the smallest mesh_error
+// among n_sub in {r, r + 1}, r = max(1, floor(log5(12 R^2)) - 1), and q_tail in
+// 3 .. max(3, round(0.45 S)) with S - q_tail >= n_sub + 1 (errors floored at 1e-10,
+// where FP64 rounding noise starts to decide), visited n_sub then q_tail
+// ascending, replacing the best only when smaller by more than 0.1 % relative.  Fewer
+// than 5 nodes: one interval and a tail of S / 2.  (A value given explicitly is kept.)
 void default_mesh(int S, int R, int* n_sub, int* q_tail) {
   struct E { int S, R, n, q; };
   static const E tab[] = {{32, 4, 2, 10}, {64, 13, 3, 21}, {96, 31, 4, 29}, {128, 63, 5, 34}};
+  if (*n_sub >= 0 && *q_tail >= 0) return;
   for (const E& e : tab)
     if (e.S == S && e.R == R) {
       if (*n_sub < 0) *n_sub = e.n;
       if (*q_tail < 0) *q_tail = e.q;
       return;
     }
-  if (*n_sub < 0) {
-    int k = (int)floor(log(12.0 * R * R) / log(5.0)) - 1;
-    *n_sub = k < 1 ? 1 : k;
+  int r = (int)floor(log(12.0 * R * R) / log(5.0)) - 1;
+  if (r < 1) r = 1;
+  double best = -1.0;
+  int bn = -1, bq = -1;
+  const int qmax = std::max(3, (int)lrint(0.45 * S));
+  for (int n = r; n <= r + 1; ++n) {
+    if (*n_sub >= 0 && n != *n_sub) continue;
+    for (int q = 3; q <= qmax; ++q) {
+      if (*q_tail >= 0 && q != *q_tail) continue;
+      if (S - q < n + 1) continue;
+      const double e = std::max(mesh_error(S, n, q, R), 1e-10);  // below: rounding noise
+      if (best < 0 || e < best * (1.0 - 1e-3)) {
+        best = e;
+        bn = n;
+        bq = q;
+      }
+    }
   }
-  if (*q_tail < 0) *q_tail = (int)lrint(0.3 * S);
+  if (bn < 0) {
+    bn = 0;
+    bq = std::max(1, S / 2);
+  }
+  if (*n_sub < 0) *n_sub = bn;
+  if (*q_tail < 0) *q_tail = bq;
 }
 
 cc_status resolve_params(const cc_table_params* in, cc_table_params* out) {
@@ -241,6 +292,32 @@ static std::vector<NodeSpec> node_specs(const cc_table_params& p) {
   }
   for (int j = 0; j < p.q_tail; ++j) out.push_back({p.q_tail, j, 1, 0.0, 1.0 / sqrt(p.alpha_c)});
   return out;
+}
+
+static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, std::vector<double>& a,
+                      std::vector<double>& w) {
+  cc_table_params p{};
+  p.S = S;
+  p.n_sub = n_sub;
+  p.q_tail = q_tail;
+  p.alpha_c = alpha_c;
+  std::vector<NodeSpec> spec = node_specs(p);
+  a.resize(spec.size());
+  w.resize(spec.size());
+  for (size_t s = 0; s < spec.size(); ++s) {
+    double x, wx;
+    gl_node(spec[s].n, spec[s].i, &x, &wx);
+    const double half = 0.5 * (spec[s].hi - spec[s].lo);
+    double al = half * x + 0.5 * (spec[s].hi + spec[s].lo);
+    double ww = half * wx;
+    if (spec[s].tail) {
+      const double t = al;
+      al = 1.0 / (t * t);
+      ww = 2.0 * ww / (t * t * t);
+    }
+    a[s] = al;
+    w[s] = ww;
+  }
 }
 
 template <typename T>
@@ -320,7 +397,8 @@ static cc_status finish_kept(cc_tables t) {
   return CC_OK;
 }
 
-static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_tables t) {
+static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_tables t,
+                            bool workspaces) {
   CC_TRY(resolve_params(params, &t->p));
   CC_CUDA(cudaGetDevice(&t->device));
   const cc_table_params& p = t->p;
@@ -398,9 +476,26 @@ static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_t
   }
   CC_CUDA(cudaGetLastError());
   CC_TRY(build_derived(t, st));
-  CC_TRY(workspace_alloc(t));
   CC_CUDA(cudaStreamSynchronize(st));
-  if (t->Mg <= 128) CC_TRY(mixed_workspace_alloc(t));
+  if (workspaces) {
+    CC_TRY(workspace_alloc(t));
+    if (t->Mg <= 128) CC_TRY(mixed_workspace_alloc(t));
+    CC_TRY(fused_single_alloc(t));
+  }
+  return CC_OK;
+}
+
+cc_status build_tables_internal(const cc_table_params* params, cudaStream_t st, bool workspaces,
+                                cc_tables* out) {
+  *out = nullptr;
+  cc_tables t = new (std::nothrow) cc_tables_s();
+  if (!t) return CC_ERR_ALLOC;
+  cc_status s = build_impl(params, st, t, workspaces);
+  if (s != CC_OK) {
+    cc_tables_free(t);
+    return s;
+  }
+  *out = t;
   return CC_OK;
 }
 
@@ -455,6 +550,15 @@ const char* cc_status_string(cc_status s) {
 
 const char* cc_last_error(void) { return g_last_error.c_str(); }
 
+cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail) {
+  if (!n_sub || !q_tail) return CC_ERR_ARG;
+  if (R < 1 || R > kMaxR || S < 2 || S > kMaxS) return CC_ERR_RANGE;
+  *n_sub = -1;
+  *q_tail = -1;
+  default_mesh(S, R, n_sub, q_tail);
+  return CC_OK;
+}
+
 cc_status cc_basis(int R, int* Nb, int8_t* vec_host) {
   if (!Nb) return CC_ERR_ARG;
   if (R < 1 || R > kMaxR) return CC_ERR_RANGE;
@@ -466,16 +570,7 @@ cc_status cc_basis(int R, int* Nb, int8_t* vec_host) {
 
 cc_status cc_build_tables(const cc_table_params* params, void* stream, cc_tables* out) {
   if (!params || !out) return CC_ERR_ARG;
-  *out = nullptr;
-  cc_tables t = new (std::nothrow) cc_tables_s();
-  if (!t) return CC_ERR_ALLOC;
-  cc_status s = build_impl(params, as_stream(stream), t);
-  if (s != CC_OK) {
-    cc_tables_free(t);
-    return s;
-  }
-  *out = t;
-  return CC_OK;
+  return build_tables_internal(params, as_stream(stream), true, out);
 }
 
 cc_status cc_tables_info(cc_tables t, cc_tables_info_t* info) {
@@ -520,6 +615,7 @@ cc_status cc_tables_free(cc_tables t) {
   if (!t) return CC_ERR_ARG;
   workspace_free(t);
   mixed_workspace_free(t);
+  fused_single_free(t);
   free_tables(t);
   delete t;
   return CC_OK;
@@ -618,6 +714,7 @@ cc_status cc_tables_load(const char* path, void* stream, cc_tables* out) {
     if (s == CC_OK) s = workspace_alloc(t);
     if (s == CC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = CC_ERR_CUDA;
     if (s == CC_OK && t->Mg <= 128) s = mixed_workspace_alloc(t);
+    if (s == CC_OK) s = fused_single_alloc(t);
   }
   if (s != CC_OK) {
     cc_tables_free(t);

@@ -59,3 +59,14 @@ def test_product_does_not_import_the_oracle():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             txt = open(f).read()
             assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_library_mesh_rule_equals_oracle_rule(lib):
+    """The default mesh search of the library (host code) and of the oracle pick the same
+    (n_sub, q_tail) for every box of the batched workload and for assorted cases."""
+    import coulomb_inputs as ci
+    from oracle import quadrature as oq
+    cases = {(b["S"], b["R"]) for b in ci.box_params(256)}
+    cases |= {(32, 4), (64, 13), (96, 31), (128, 63), (40, 9), (17, 2), (36, 5), (4, 3), (2, 1)}
+    for S, R in sorted(cases):
+        assert lib.default_mesh(S, R) == oq.default_periodic_mesh(S, R), (S, R)

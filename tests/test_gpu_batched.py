@@ -1,0 +1,101 @@
+"""GPU parity: the batched engine (256 uneven boxes, one persistent graph-captured
+launch) against the FP64 oracle, box by box."""
+import numpy as np
+import pytest
+
+import coulomb_inputs as ci
+from gpu_common import TOL_FP32, TOL_FP64, need_gpu, rel_err
+from oracle import basis as ob
+from oracle import exchange as ox
+from oracle import quadrature as oq
+
+pytestmark = pytest.mark.gpu
+
+
+def _nodes(b):
+    n_sub, q_tail = oq.default_periodic_mesh(b["S"], b["R"])
+    a, w, _ = oq.laplace_mesh(b["S"], n_sub, q_tail)
+    keep = oq.prune_periodic(a, w, b["R"], 1e-9)
+    return a[keep], w[keep]
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import paper_1502_08043_gb300 as cc
+    dev = need_gpu()
+    boxes = ci.box_params(256)
+    B = cc.Batch(boxes)
+    yield dev, boxes, B
+    B.free()
+
+
+def _run(B, dev, dtype):
+    import torch
+    eps = torch.full((int(B.offsets[-1]),), float("nan"), dtype=dtype, device=dev)
+    Ex = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
+    B.exchange(eps, Ex)
+    torch.cuda.synchronize()
+    return eps.cpu().numpy().astype(np.float64), Ex.cpu().numpy()
+
+
+def _box_eps(B, eps, i, R):
+    Mg = 2 * R + 1
+    g = eps[B.offsets[i]:B.offsets[i + 1]].reshape(Mg, Mg, Mg)
+    k = ob.basis(R) + R
+    return g, g[k[:, 0], k[:, 1], k[:, 2]]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_all_boxes_exchange_energy(batch, prec):
+    import torch
+    dev, boxes, B = batch
+    eps, Ex = _run(B, dev, torch.float32 if prec == "fp32" else torch.float64)
+    tol = 2 * TOL_FP32 if prec == "fp32" else TOL_FP64
+    assert not np.isnan(eps).any()
+    for i, b in enumerate(boxes):
+        a, w = _nodes(b)
+        C = ox.difference_histogram(b["R_F"], "fft")
+        ref = ox.Ex_separable_periodic(b["R_F"], b["L"], a, w, C)
+        assert abs(Ex[i, 0] - ref) < tol * abs(ref), (i, b)
+        assert Ex[i, 1] == 2 * Ex[i, 0]
+
+
+def test_sampled_boxes_full_grids(batch):
+    import torch
+    dev, boxes, B = batch
+    eps, _ = _run(B, dev, torch.float32)
+    order = np.argsort([b["R"] for b in boxes])
+    pick = list(order[:4]) + list(order[-3:]) + [17, 101, 200]
+    for i in pick:
+        b = boxes[i]
+        a, w = _nodes(b)
+        grid, vals = _box_eps(B, eps, i, b["R"])
+        ref = ox.eps_separable(b["R"], b["R_F"], b["L"], a, w)
+        assert np.array_equal(grid == 0, ox.eps_on_grid(b["R"], ref) == 0)
+        assert rel_err(vals, ref) < TOL_FP32, (i, b)
+
+
+def test_replay_is_deterministic_and_tuner_keeps_results(batch):
+    import torch
+    dev, boxes, B = batch
+    e1, x1 = _run(B, dev, torch.float32)
+    e2, x2 = _run(B, dev, torch.float32)
+    assert np.array_equal(e1, e2) and np.array_equal(x1, x2)
+    eps = torch.empty((int(B.offsets[-1]),), dtype=torch.float32, device=dev)
+    Ex = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
+    choice = B.tune(eps, Ex, reps=3)
+    assert choice["ctas_per_sm"] in (1, 2) and choice["oversub"] in (1, 2, 4, 8)
+    assert choice["ms"] > 0
+    e3, x3 = _run(B, dev, torch.float32)
+    assert rel_err(e3, e1) < TOL_FP32 and np.max(np.abs(x3 - x1) / np.abs(x1)) < TOL_FP32
+
+
+def test_batch_argument_errors():
+    import paper_1502_08043_gb300 as cc
+    need_gpu()
+    with pytest.raises(cc.CoulombError) as e:
+        cc.Batch([{"R": 25, "L": 10.0, "R_F": 5, "S": 32}])    # grid side 51 > 49
+    assert e.value.status == 2
+    with pytest.raises(cc.CoulombError) as e:
+        cc.Batch([{"R": 6, "L": 10.0, "R_F": 7, "S": 32}])     # R_F > R
+    assert e.value.status == 2
