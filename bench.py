@@ -272,6 +272,8 @@ def run_gpu(args):
         "rates": {"integrals_per_s": n / (k_ms * 1e-3),
                   "pairs_per_s": Nb * Nb / (parts["pairs_ms"] * 1e-3)},
     }
+    if rank == 0 and world == 1 and args.mode_products:
+        line["mode_products"] = {n: mode_products(n) for n in args.mode_products.split(",")}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -279,6 +281,64 @@ def run_gpu(args):
     t.free()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- mode products: FP32 vs mixed
+MP_CONFIGS = {"precision": (31, 40.0, 96, 20), "large": (63, 60.0, 128, 40)}
+
+
+def mode_products(name, reps=10, oracle_sample=200, with_fp16=False):
+    """Exchange sums of one single-box workload by the plain FP32 mode products and by the
+    bf16x3 tensor-core path: device time per call (CUDA events, inputs resident), useful
+    flop rate 6 Mg^4 S_eff, and the accuracy of both against the FP64 oracle on a seeded
+    sample of basis functions."""
+    import torch
+
+    import paper_1502_08043_gb300 as cc
+    R, L, S, R_F = MP_CONFIGS[name]
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev)
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    Mg, S_eff = t.info["Mg"], t.info["S_eff"]
+    out = {"R": R, "L_bohr": L, "S": S, "S_eff": S_eff, "R_F": R_F, "Mg": Mg}
+    res = {}
+    precs = ["fp32", "bf16x3"] + (["fp16x3"] if with_fp16 else [])
+    for prec in precs:
+        eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+        Ex = torch.empty(2, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[prec] = (ms, eps.cpu().numpy().astype(np.float64), float(Ex[0].item()))
+        out[prec + "_ms"] = ms
+        out[prec + "_useful_tflops"] = 6.0 * Mg ** 4 * S_eff / (ms * 1e-3) / 1e12
+    out["speedup_bf16x3_vs_fp32"] = res["fp32"][0] / res["bf16x3"][0]
+    if oracle_sample:
+        from oracle import basis as ob
+        from oracle import exchange as ox
+        from oracle import quadrature as oq
+        n_sub, q_tail = oq.default_periodic_mesh(S, R)
+        aa, ww, _ = oq.laplace_mesh(S, n_sub, q_tail)
+        keep = oq.prune_periodic(aa, ww, R, 1e-9)
+        Nb = ob.count(R)
+        idx = np.unique(np.random.default_rng(7).integers(0, Nb, oracle_sample))
+        ref = ox.eps_separable(R, R_F, L, aa[keep], ww[keep], k_idx=idx)
+        k = ob.basis(R)[idx] + R
+        flat = (k[:, 0] * Mg + k[:, 1]) * Mg + k[:, 2]
+        for prec in precs:
+            got = res[prec][1][flat]
+            out[prec + "_max_rel_err_vs_oracle"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+        out["oracle_sample"] = f"{len(idx)} seeded basis functions of {Nb}"
+    t.free()
+    return out
 
 
 # ------------------------------------------------------------------------------- oracle
@@ -358,6 +418,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0)
+    ap.add_argument("--mode-products", default="precision,large",
+                    help="also time FP32 vs bf16x3 exchange mode products at these single-box "
+                         "workloads (precision: |n|<=31, large: |n|<=63); '' to skip")
+    ap.add_argument("--mp-only", default=None,
+                    help="only run the mode-product comparison of this workload, print it")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
@@ -365,6 +430,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mp_only:
+        print(json.dumps({"mode_products": mode_products(args.mp_only, oracle_sample=0)}))
     else:
         run_gpu(args)
 

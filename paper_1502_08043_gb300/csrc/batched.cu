@@ -156,8 +156,10 @@ template <typename T>
 static cc_status plan_launch(const FusedPlan& p, int rf_override, T* eps, double* Ex,
                              cudaStream_t st) {
   const size_t pq = (size_t)2 * p.max_g3 * sizeof(T);
-  const int smem_pq = (p.prefer_smem && pq <= kFusedSmemCap) ? 1 : 0;
-  const size_t smem = smem_pq ? pq : 0;
+  const long long mg = llround(cbrt((double)p.max_g3));
+  const size_t mats = (((size_t)3 * mg * mg * sizeof(T) + (size_t)mg * mg * 4) + 15) & ~(size_t)15;
+  const int smem_pq = (p.prefer_smem && mats + pq <= kFusedSmemCap) ? 1 : 0;
+  const size_t smem = mats + (smem_pq ? pq : 0);
   auto kern = k_fused_exchange<T>;
   CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap));
   int per_sm = 0;

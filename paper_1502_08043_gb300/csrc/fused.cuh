@@ -29,7 +29,7 @@ struct FusedItem {
   int box, s0, s1, g;
 };
 
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;
 
 template <typename T>
 __device__ __forceinline__ void kahan_add(T* e, T* c, long long i, T v) {
@@ -45,25 +45,23 @@ __device__ __forceinline__ bool occ_at(int x, int y, int z, int R, int R_F) {
 }
 
 // z mode on the occupation tensor: P[(x,y)][z'] = sum_z O[x][y][z] M[z][z'] (M symmetric);
-// written (overwrite) or Kahan-added into (E, C)
+// row (x,y) of O is 1 exactly on the contiguous z range zr[row] = (z_lo, z_hi) of the
+// Fermi sphere (empty when z_lo > z_hi); written (overwrite) or Kahan-added into (E, C)
 template <typename T, bool kAcc>
-__device__ void zmode_occ(const T* __restrict__ M, int Mg, int R, int R_F, T* P, T* E, T* C) {
+__device__ void zmode_occ(const T* __restrict__ M, int Mg, const short2* zr, T* P, T* E, T* C) {
   const int rows = Mg * Mg;
   const int rb = (rows + 3) / 4, cb = (Mg + 3) / 4;
   for (int blk = threadIdx.x; blk < rb * cb; blk += blockDim.x) {
     const int r0 = (blk / cb) * 4, c0 = (blk % cb) * 4;
     T acc[4][4] = {};
-    for (int z = 0; z < Mg; ++z) {
-      T m[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) m[j] = (c0 + j < Mg) ? M[z * Mg + c0 + j] : T(0);
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + i;
+      if (r >= rows) continue;
+      const short2 z = zr[r];
+      for (int zz = z.x; zz <= z.y; ++zz) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = r0 + i;
-        if (r < rows && occ_at(r / Mg, r % Mg, z, R, R_F)) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += m[j];
-        }
+        for (int j = 0; j < 4; ++j) acc[i][j] += (c0 + j < Mg) ? M[zz * Mg + c0 + j] : T(0);
       }
     }
 #pragma unroll
@@ -158,10 +156,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   extern __shared__ __align__(16) unsigned char fsmem[];
   __shared__ int s_item, s_last;
   __shared__ double s_red[kFusedThreads];
+  // dynamic shared memory: [Ts | Ws | Db : 3 Mg_max^2] [z ranges: Mg_max^2 short2] [P | Q]
+  const int mgmax = (int)llround(cbrt((double)max_g3));
+  T* sT = reinterpret_cast<T*>(fsmem);
+  T* sW = sT + mgmax * mgmax;
+  T* sD = sW + mgmax * mgmax;
+  short2* zr = reinterpret_cast<short2*>(sD + mgmax * mgmax);
   T* P;
   T* Q;
   if (smem_pq) {
-    P = reinterpret_cast<T*>(fsmem);
+    const size_t off = ((size_t)3 * mgmax * mgmax * sizeof(T) + (size_t)mgmax * mgmax * 4 + 15) &
+                       ~(size_t)15;
+    P = reinterpret_cast<T*>(fsmem + off);
     Q = P + max_g3;
   } else {
     P = gscratch + (long long)blockIdx.x * 2 * max_g3;
@@ -181,20 +187,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     T* E = bx.part + (long long)item.g * 2 * G3;
     T* C = E + G3;
     for (long long i = threadIdx.x; i < 2 * G3; i += blockDim.x) E[i] = T(0);
+    for (int r = threadIdx.x; r < M2; r += blockDim.x) {   // Fermi-sphere z range per row
+      const int x = r / Mg - bx.R, y = r % Mg - bx.R;
+      const int h2 = bx.R_F * bx.R_F - x * x - y * y;
+      short2 z = make_short2(1, 0);
+      if (h2 >= 0) {
+        int h = (int)sqrtf((float)h2);
+        while (h * h > h2) --h;
+        while ((h + 1) * (h + 1) <= h2) ++h;
+        z = make_short2((short)(bx.R - h), (short)(bx.R + h));
+      }
+      zr[r] = z;
+    }
     __syncthreads();
     for (int s = item.s0; s < item.s1; ++s) {
-      const T* Ts = bx.Tm + s * M2;
-      const T* Ws = bx.WD + s * M2;
-      zmode_occ<T, false>(Ts, Mg, bx.R, bx.R_F, P, nullptr, nullptr);   // P = O x3 T
+      for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+        sT[i] = bx.Tm[s * M2 + i];
+        sW[i] = bx.WD[s * M2 + i];
+      }
       __syncthreads();
-      ymode<T, false>(Ts, P, Mg, Q, nullptr, nullptr);                   // Q = P x2 T
-      if (bx.periodic) ymode<T, true>(Ws, P, Mg, nullptr, E, C);         // E += P x2 wD
+      zmode_occ<T, false>(sT, Mg, zr, P, nullptr, nullptr);             // P = O x3 T
       __syncthreads();
-      xmode_acc<T>(Ws, Q, Mg, E, C);                                     // E += Q x1 wD
+      ymode<T, false>(sT, P, Mg, Q, nullptr, nullptr);                   // Q = P x2 T
+      if (bx.periodic) ymode<T, true>(sW, P, Mg, nullptr, E, C);         // E += P x2 wD
+      __syncthreads();
+      xmode_acc<T>(sW, Q, Mg, E, C);                                     // E += Q x1 wD
       __syncthreads();
     }
     if (bx.periodic && item.g == 0) {
-      zmode_occ<T, true>(bx.Db, Mg, bx.R, bx.R_F, nullptr, E, C);       // E += O x3 Dbar
+      for (int i = threadIdx.x; i < M2; i += blockDim.x) sD[i] = bx.Db[i];
+      __syncthreads();
+      zmode_occ<T, true>(sD, Mg, zr, nullptr, E, C);                    // E += O x3 Dbar
       __syncthreads();
     }
     // publish this item; the last item of the box finalises it

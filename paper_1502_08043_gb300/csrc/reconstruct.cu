@@ -3,14 +3,16 @@
 // planewaves is a planewave, so (IJ|KL) vanishes unless n_J - n_I + n_L - n_K = 0).
 //
 // SEPARABLE: V(q) = sum_s c_s T_s[|q_x|] c_s T_s[|q_y|] c_s T_s[|q_z|] with c_s^3 = pref w_s
-// folded into the table.  A warp takes 32 quadruples; lane l owns nodes l, l+32, ...;
-// for every quadruple all lanes read one table row segment (32 consecutive words: no
-// bank conflict), and a 31-shuffle butterfly transposes and sums the 32 x 32 partial
-// sums so that lane l ends with the total of quadruple l.
+// folded into the table.  A warp takes 32 quadruples; lane l owns the S_pad/32 consecutive
+// nodes starting at l S_pad/32; for every quadruple all lanes read one table row (one
+// vector load per axis, conflict free), and a 31-shuffle butterfly transposes and sums
+// the 32 x 32 partial sums so that lane l ends with the total of quadruple l.
 // COLLAPSED (periodic kernel): prod_x exp(-a_s q_x^2) = exp(-a_s |q|^2), so the node sum
 // is a function of the integer m = |q|^2 <= 4 R^2 only; one table of 4R^2 + 1 values,
 // one shared-memory gather per integral; the kernel streams 16 B in and 4 B out.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -52,9 +54,13 @@ struct IdsSrc {
   const int4* q;
   const char4* basis;
   int Nb;
+  __device__ __forceinline__ int4 raw(int64_t i) const { return ld_stream(q + i); }
   template <bool kPeriodic>
   __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
-    const int4 v = ld_stream(q + i);
+    return classify_raw<kPeriodic>(raw(i), qx, qy, qz);
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_raw(const int4 v, int& qx, int& qy, int& qz) const {
     if ((unsigned)v.x >= (unsigned)Nb || (unsigned)v.y >= (unsigned)Nb ||
         (unsigned)v.z >= (unsigned)Nb || (unsigned)v.w >= (unsigned)Nb) {
       qx = qy = qz = 0;
@@ -71,9 +77,13 @@ struct VecSrc {
   __device__ __forceinline__ static bool in_sphere(char4 a, int R2) {
     return (int)a.x * a.x + (int)a.y * a.y + (int)a.z * a.z <= R2;
   }
+  __device__ __forceinline__ int4 raw(int64_t i) const { return ld_stream(q + i); }
   template <bool kPeriodic>
   __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
-    const int4 v = ld_stream(q + i);
+    return classify_raw<kPeriodic>(raw(i), qx, qy, qz);
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_raw(const int4 v, int& qx, int& qy, int& qz) const {
     const char4 a = as_c4(v.x), b = as_c4(v.y), c = as_c4(v.z), d = as_c4(v.w);
     if (!in_sphere(a, R2) || !in_sphere(b, R2) || !in_sphere(c, R2) || !in_sphere(d, R2)) {
       qx = qy = qz = 0;
@@ -114,7 +124,34 @@ __device__ __forceinline__ void flush_counts(unsigned long long* counters, unsig
 }
 
 // ---------------------------------------------------------------- separable kernel
-template <typename T, typename Src, bool kPeriodic>
+// NCH consecutive nodes per lane (S_pad = 32 NCH); NCH = 0 selects a runtime loop
+template <typename T, int NCH>
+__device__ __forceinline__ T node_chunk(const T* rx, const T* ry, const T* rz, int nch) {
+  T a = T(0);
+  if constexpr (sizeof(T) == 4 && (NCH == 2 || NCH == 4)) {
+    // the lane's chunk starts at a multiple of NCH words: one vector load per axis
+    using V = typename std::conditional<NCH == 2, float2, float4>::type;
+    const V x = *reinterpret_cast<const V*>(rx);
+    const V y = *reinterpret_cast<const V*>(ry);
+    const V z = *reinterpret_cast<const V*>(rz);
+    a = fma_t(x.x * y.x, z.x, a);
+    a = fma_t(x.y * y.y, z.y, a);
+    if constexpr (NCH == 4) {
+      a = fma_t(reinterpret_cast<const float4&>(x).z * reinterpret_cast<const float4&>(y).z,
+                reinterpret_cast<const float4&>(z).z, a);
+      a = fma_t(reinterpret_cast<const float4&>(x).w * reinterpret_cast<const float4&>(y).w,
+                reinterpret_cast<const float4&>(z).w, a);
+    }
+  } else if constexpr (NCH > 0) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) a = fma_t(rx[c] * ry[c], rz[c], a);
+  } else {
+    for (int c = 0; c < nch; ++c) a = fma_t(rx[c] * ry[c], rz[c], a);
+  }
+  return a;
+}
+
+template <typename T, typename Src, bool kPeriodic, int NCH>
 __global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __restrict__ gtab,
                                              int Dmax, int S_pad, T* __restrict__ out,
                                              unsigned long long* counters, int basis_smem) {
@@ -146,12 +183,11 @@ __global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __rest
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
       const unsigned p = __shfl_sync(kFull, pk, k);
-      const T* rx = tab + (p & 255u) * S_pad + lane;
-      const T* ry = tab + ((p >> 8) & 255u) * S_pad + lane;
-      const T* rz = tab + ((p >> 16) & 255u) * S_pad + lane;
-      T a = T(0);
-      for (int c = 0; c < nch; ++c) a = fma_t(rx[c * 32] * ry[c * 32], rz[c * 32], a);
-      acc[k] = a;
+      const int lo = lane * nch;  // this lane's nodes lane*nch .. lane*nch + nch - 1
+      const T* rx = tab + (p & 255u) * S_pad + lo;
+      const T* ry = tab + ((p >> 8) & 255u) * S_pad + lo;
+      const T* rz = tab + ((p >> 16) & 255u) * S_pad + lo;
+      acc[k] = node_chunk<T, NCH>(rx, ry, rz, nch);
     }
     // butterfly transpose-reduce: afterwards lane l holds the sum over lanes of acc[l]
 #pragma unroll
@@ -186,14 +222,17 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
   __syncthreads();
   unsigned c0 = 0, c1 = 0, c2 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = 4;
+  constexpr int U = 8;  // 8 x 16 B streaming loads in flight per thread before any use
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + (U - 1) * stride < n; i += U * stride) {
+    int4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = src.raw(i + u * stride);
     int f[U], m[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int qx, qy, qz;
-      f[u] = src.template decode<true>(i + u * stride, qx, qy, qz);
+      f[u] = src.template classify_raw<true>(v[u], qx, qy, qz);
       m[u] = qx * qx + qy * qy + qz * qz;
     }
 #pragma unroll
@@ -293,7 +332,12 @@ static cc_status launch_sep(cc_tables t, Src src, int64_t n, T* out,
   int basis_smem = 0;
   if (tb + (size_t)t->Nb * 4 <= 96 * 1024) basis_smem = t->Nb;
   const size_t smem = tb + (size_t)basis_smem * 4;
-  auto kern = k_sep<T, Src, kPeriodic>;
+  const int nch = t->S_pad / 32;
+  auto kern = nch == 1 ? k_sep<T, Src, kPeriodic, 1>
+            : nch == 2 ? k_sep<T, Src, kPeriodic, 2>
+            : nch == 3 ? k_sep<T, Src, kPeriodic, 3>
+            : nch == 4 ? k_sep<T, Src, kPeriodic, 4>
+                       : k_sep<T, Src, kPeriodic, 0>;
   int blocks = 0;
   CC_TRY(grid_for(kern, 256, smem, (n + 7) / 8, &blocks));
   kern<<<blocks, 256, smem, st>>>(src, n, tab, t->Dmax, t->S_pad, out, counters, basis_smem);
@@ -314,7 +358,7 @@ static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned lo
   const size_t smem = tb + (size_t)basis_smem * 4;
   auto kern = k_col<T, Src>;
   int blocks = 0;
-  CC_TRY(grid_for(kern, 512, smem, (n + 3) / 4, &blocks));
+  CC_TRY(grid_for(kern, 512, smem, (n + 7) / 8, &blocks));
   kern<<<blocks, 512, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);
   CC_CUDA(cudaGetLastError());
   return CC_OK;

@@ -14,9 +14,10 @@
 // keeps only W1 with Dx = T_s and no step 3 / step 5.
 // Every GEMM has a 128-row operand A (rows of an Np^2 x Np slab stack) and an Np x Np
 // operand B (a Toeplitz matrix), Np = 64 or 128 (the grid side padded with zeros).
-// Operands are bf16 hi + lo planes: x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
-// the product keeps hi*hi + hi*lo + lo*hi (3 MMAs, the lo*lo term is below 2^-18
-// relative).  Intermediates leave TMEM as FP32, are re-split into hi + lo (the FP32
+// Operands are bf16 (or fp16) hi + lo planes: x = hi + lo with hi = bf16(x),
+// lo = bf16(x - hi); the product keeps hi*hi + hi*lo + lo*hi (3 MMAs, the lo*lo term is
+// below 2^-18 relative for bf16, 2^-22 for fp16).  fp16 has a narrow exponent range,
+// so its y-mode operands carry a per-node power-of-two scale (see build_planes).  Intermediates leave TMEM as FP32, are re-split into hi + lo (the FP32
 // residual x - hi carried as the correction operand) and stored for the next GEMM.
 // O, O^T are exact in bf16 (0/1) and have no lo plane.
 //
@@ -352,8 +353,8 @@ __global__ void __launch_bounds__(128, 1)
 // X1[s] = D_s (periodic) or T_s (box), TT[s] = T_s, WTD[s][0] = w_s T_s, WTD[s][1] = w_s D_s
 template <typename E>
 __global__ void k_mx_tables(const double* Tm, const double* WDm, const double* w, int S_eff,
-                            int Mg, int Np, int periodic, E* x1h, E* x1l, E* tth, E* ttl,
-                            E* wtdh, E* wtdl) {
+                            int Mg, int Np, int periodic, const float* cs, E* x1h, E* x1l,
+                            E* tth, E* ttl, E* wtdh, E* wtdl) {
   const long long n = (long long)S_eff * Np * Np;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -364,7 +365,9 @@ __global__ void k_mx_tables(const double* Tm, const double* WDm, const double* w
       t = Tm[((long long)s * Mg + a) * Mg + c];
       d = (periodic && a == c) ? 0.0 : t;
     }
-    const double wt = w[s] * t, wd = w[s] * d;
+    // fp16: the weight is split as (w_s / c_s) here and c_s on the intermediates
+    const double ws = cs ? w[s] / (double)cs[s] : w[s];
+    const double wt = ws * t, wd = ws * d;
     E h, l;
     split2<E>((float)(periodic ? d : t), h, l);
     x1h[i] = h;
@@ -468,6 +471,7 @@ struct MxPlanes {  // one element type
   void* R[2];    // [C][Np^3]
   void* W[2];    // [C][2][Np^3]
   CUtensorMap mO, mOT, mR[2], mW[2], mX1[2], mTT[2], mWTD[2], mDB[2];
+  float* cs = nullptr;  // fp16: per-node power-of-two scale of the y-mode operands
 };
 
 struct MxWorkspace {
@@ -552,7 +556,22 @@ static cc_status build_planes(cc_tables t, MxWorkspace* w, MxPlanes* P, bool bf1
     CC_TRY(make_map(&P->mDB[h], P->DB[h], (long long)Np, Np, Np, bf16));
   }
   const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
-  k_mx_tables<E><<<1024, 256>>>(t->d.Tm64, t->d.WDm64, t->d.w64, S, t->Mg, Np, periodic,
+  if (!bf16) {
+    // per-node exponent scaling for fp16: the products w_s T_s W_s are formed as
+    // (w_s / c_s) T_s (c_s W_s) with c_s = 2^min(1, floor(log2 w_s) + 14): the weight
+    // factor stays in fp16's normal range (>= 2^-14 for T ~ 1) and c_s W_s <= 2 Np^2
+    // stays below 65504 (W_s <= Np^2 since every T_s, D_s entry is <= 1)
+    std::vector<float> c(S);
+    for (int i = 0; i < S; ++i) {
+      const double wv = t->w[t->kept_idx[i]];
+      int e = (int)floor(log2(wv)) + 14;
+      if (e > 1) e = 1;
+      c[i] = ldexpf(1.0f, e);
+    }
+    CC_TRY(mx_alloc(t, w, (void**)&P->cs, sizeof(float) * S));
+    CC_CUDA(cudaMemcpy(P->cs, c.data(), sizeof(float) * S, cudaMemcpyHostToDevice));
+  }
+  k_mx_tables<E><<<1024, 256>>>(t->d.Tm64, t->d.WDm64, t->d.w64, S, t->Mg, Np, periodic, P->cs,
                                 (E*)P->X1[0], (E*)P->X1[1], (E*)P->TT[0], (E*)P->TT[1],
                                 (E*)P->WTD[0], (E*)P->WTD[1]);
   k_mx_dbar<E><<<(Np * Np + 255) / 256, 256>>>(t->d.Dbar64, t->Mg, Np, (E*)P->DB[0],
@@ -575,6 +594,7 @@ cc_status mixed_workspace_alloc(cc_tables t) {
   CC_TRY(mx_alloc(t, w, (void**)&w->err, sizeof(int) * 2));
   CC_CUDA(cudaMemset(w->err, 0, sizeof(int) * 2));
   CC_TRY(build_planes<__nv_bfloat16>(t, w, &w->bf, true));
+  CC_TRY(build_planes<__half>(t, w, &w->hf, false));
   CC_CUDA(cudaDeviceSynchronize());
   return CC_OK;
 }
@@ -646,6 +666,7 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
       g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
       g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
       g.o_base = 0; g.o_sb = 2 * VOL; g.s_mhi = NN; g.s_mlo = 1; g.s_n = NP;
+      g.scale = P.cs ? P.cs + s0 : nullptr;
       g.err = w->err;
       CC_TRY((launch_tc<NP, E>(P.mR[0], P.mR[1], P.mTT[0], P.mTT[1], g, m_tiles, cs, st)));
     }
@@ -657,6 +678,7 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
       g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
       g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
       g.o_base = VOL; g.o_sb = 2 * VOL; g.s_mhi = NN; g.s_mlo = 1; g.s_n = NP;
+      g.scale = P.cs ? P.cs + s0 : nullptr;
       g.err = w->err;
       CC_TRY((launch_tc<NP, E>(P.mO, P.mO, P.mTT[0], P.mTT[1], g, m_tiles, cs, st)));
     }
@@ -682,10 +704,14 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
 
 cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
                          cudaStream_t st) {
-  if (precision != CC_PREC_BF16X3) return CC_ERR_NOTSUPP;
+  if (precision != CC_PREC_BF16X3 && precision != CC_PREC_FP16X3) return CC_ERR_NOTSUPP;
   if (t->Mg > 128) return CC_ERR_NOTSUPP;
-  CC_TRY(mixed_workspace_alloc(t));
   MxWorkspace* w = reinterpret_cast<MxWorkspace*>(t->ws.mx);
+  if (!w) return CC_ERR_NOTSUPP;  // handle built without workspaces
+  if (precision == CC_PREC_FP16X3) {
+    if (w->Np == 64) return run_mixed<64, __half>(t, w, w->hf, R_F, eps, Ex, st);
+    return run_mixed<128, __half>(t, w, w->hf, R_F, eps, Ex, st);
+  }
   if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
   return run_mixed<128, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
 }

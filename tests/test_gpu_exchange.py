@@ -62,7 +62,11 @@ def test_paper_scale(dev):
     assert rel_err(_basis_values(R, grid), ref) < TOL_FP32
     ex_ref = ox.Ex_separable_periodic(R_F, L, a, w)
     assert abs(Ex[0] - ex_ref) < TOL_FP32 * abs(ex_ref)
-    assert rel_err(_basis_values(R, grid), ox.eps_exact(R, R_F, L)) < 1e-7
+    # stated method error of the 64-node mesh (oracle node sum vs exact pair sum), and the
+    # FP32 result against the exact sum within method error + FP32 bound
+    exact = ox.eps_exact(R, R_F, L)
+    assert rel_err(ref, exact) < 3e-8
+    assert rel_err(_basis_values(R, grid), exact) < TOL_FP32 + 3e-8
     t.free()
 
 

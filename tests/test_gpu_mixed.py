@@ -91,3 +91,21 @@ def test_mixed_repeatable(dev):
     ref = ox.eps_separable(CFG2["R"], 5, CFG2["L"], *oracle_nodes(CFG2["R"], CFG2["S"]))
     assert rel_err(_basis_values(CFG2["R"], g3), ref) < TOL_MIXED
     t.free()
+
+
+@pytest.mark.parametrize("cfg", [CFG2, CFG3], ids=["R13", "R31"])
+def test_fp16x3_with_exponent_scaling(dev, cfg):
+    """fp16 hi+lo with per-node power-of-two scaling of the y-mode operands."""
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = cfg["R"], cfg["L"], cfg["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=cfg["S"])
+    a, w = oracle_nodes(R, cfg["S"])
+    grid, Ex = _run(t, R_F, "fp16x3", dev)
+    Nb = ob.count(R)
+    idx = np.unique(np.concatenate([np.random.default_rng(5).integers(0, Nb, 300), [0, Nb - 1]]))
+    ref = ox.eps_separable(R, R_F, L, a, w, k_idx=idx)
+    assert rel_err(_basis_values(R, grid)[idx], ref) < TOL_MIXED
+    C = ox.difference_histogram(R_F, "fft")
+    ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
+    assert abs(Ex[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
+    t.free()
