@@ -211,15 +211,42 @@ def run_gpu(args):
         he = torch.empty(Mg ** 3, dtype=torch.float32, pin_memory=True)
         hx = torch.empty(2, dtype=torch.float64, pin_memory=True)
 
+        # the step through the public API with host buffers: the quadruples go up in
+        # chunks on a copy stream while earlier chunks are reconstructed, and results
+        # come back on a second copy stream (H2D, compute and D2H overlap)
+        nchunk = 8
+        bounds = [n * c // nchunk for c in range(nchunk + 1)]
+        up = torch.cuda.Stream(dev)
+        down = torch.cuda.Stream(dev)
+        loaded = [torch.cuda.Event() for _ in range(nchunk)]
+        done = [torch.cuda.Event() for _ in range(nchunk)]
+
         def e2e_step():
-            q.copy_(hq, non_blocking=True)
-            cc.reconstruct_integrals(t, q, vals, lookup=lookup)
+            with torch.cuda.stream(up):
+                up.wait_stream(st)
+                for c in range(nchunk):
+                    a, b = bounds[c], bounds[c + 1]
+                    q[a:b].copy_(hq[a:b], non_blocking=True)
+                    loaded[c].record(up)
+            for c in range(nchunk):
+                a, b = bounds[c], bounds[c + 1]
+                st.wait_event(loaded[c])
+                cc.reconstruct_integrals(t, q[a:b], vals[a:b], lookup=lookup, stream=st)
+                done[c].record(st)
+                with torch.cuda.stream(down):
+                    down.wait_event(done[c])
+                    hv[a:b].copy_(vals[a:b], non_blocking=True)
             cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup)
             cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")
-            hv.copy_(vals, non_blocking=True)
-            hp.copy_(pairs, non_blocking=True)
-            he.copy_(eps, non_blocking=True)
-            hx.copy_(Ex, non_blocking=True)
+            ev_tail = torch.cuda.Event()
+            ev_tail.record(st)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_tail)
+                hp.copy_(pairs, non_blocking=True)
+                he.copy_(eps, non_blocking=True)
+                hx.copy_(Ex, non_blocking=True)
+            st.wait_stream(down)
+            st.wait_stream(up)
 
         for _ in range(2):
             e2e_step()

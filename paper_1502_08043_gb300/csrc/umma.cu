@@ -21,15 +21,17 @@
 // residual x - hi carried as the correction operand) and stored for the next GEMM.
 // O, O^T are exact in bf16 (0/1) and have no lo plane.
 //
-// Kernel anatomy (one 128 x Np output tile per CTA, 4 warps):
-//   warp 0 / lane 0  TMA producer: 2D tiled cp.async.bulk.tensor loads of 64-wide K
-//                    blocks (128-byte swizzle) into a 3-stage shared-memory ring;
-//   warp 1 / lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = Np,
-//                    K = 16 per instruction, FP32 accumulator in TMEM; tcgen05.commit
-//                    frees a ring slot when its MMAs have read it;
-//   warp 2           allocates / frees Np TMEM columns;
-//   all 4 warps      epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store FP32
-//                    (optionally accumulating) or split into hi / lo planes.
+// Kernel anatomy (persistent: one CTA per SM walks 128 x Np output tiles, 6 warps):
+//   warp 4 / lane 0  TMA producer: 2D tiled cp.async.bulk.tensor loads of 64-wide K
+//                    blocks (128-byte swizzle) into a 3-stage shared-memory ring that
+//                    runs on across tiles;
+//   warp 5 / lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = Np,
+//                    K = 16 per instruction, FP32 accumulators in TMEM (two of them, used
+//                    alternately); tcgen05.commit frees a ring slot when its MMAs have
+//                    read it and hands a finished accumulator to the epilogue;
+//   warps 0-3        allocate / free 2 Np TMEM columns; epilogue: tcgen05.ld 32 lanes x 32
+//                    columns, scale, store FP32 (accumulation by reductions) or split into
+//                    hi / lo planes, then release the accumulator.
 // Every mbarrier wait is bounded by the global timer (about 2 s); on expiry the kernel
 // sets an error word, stops issuing work, and returns through the normal teardown.
 #include <cuda.h>
@@ -161,6 +163,7 @@ __device__ __forceinline__ void split2<__half>(float v, __half& hi, __half& lo) 
 
 // ------------------------------------------------------------------ the GEMM kernel
 struct TcArgs {
+  int m_tiles, batches; // output tiles: m_tiles 128-row tiles in each of `batches`
   int nk;               // 64-wide K blocks per product
   int J;                // products stacked along K (accumulated in one TMEM tile)
   long long a_base, a_sb, a_sj;  // A row of (batch b, product j): base + b*sb + j*sj (+ m0)
@@ -179,6 +182,7 @@ struct TcArgs {
 constexpr int kStages = 3;
 constexpr int kTileM = 128;
 constexpr int kKB = 64;  // K elements per block = one 128-byte swizzle atom of 16-bit values
+constexpr int kTcThreads = 192;  // warps 0-3 epilogue, warp 4 TMA producer, warp 5 MMA issuer
 
 template <int NP>
 struct TcSmem {
@@ -188,8 +192,16 @@ struct TcSmem {
   static constexpr int kBytes = kStages * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent, warp-specialised GEMM: CTA c takes output tiles c, c + grid, ... of the
+// m_tiles x batches tile space.  The producer streams operands through a kStages ring
+// continuously across tiles; the MMA warp alternates between two TMEM accumulators so
+// that the epilogue of one tile overlaps the MMAs (and loads) of the next.
 template <int NP, typename E>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
               const __grid_constant__ CUtensorMap mB, const __grid_constant__ CUtensorMap mBlo,
               TcArgs g) {
@@ -198,29 +210,33 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
   uint8_t* gbase = smem_raw + (base - raw);
-  const uint32_t bar0 = base + kStages * L::kStage;  // full[s], empty[s], done, tmem slot
+  const uint32_t bar0 = base + kStages * L::kStage;
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t done = bar0 + 8u * (2 * kStages);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 1));
+  auto tfull = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
+  auto tempty = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
+  uint32_t* tmem_slot =
+      reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 4));
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.y;
-  const long long m0 = (long long)blockIdx.x * kTileM;
+  const int total = g.m_tiles * g.batches;
   if (threadIdx.x == 0) {
     s_abort = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull(a), 1);
+      mbar_init(tempty(a), 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)NP)
+                 "r"((uint32_t)(2 * NP))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -228,122 +244,145 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int total = g.J * g.nk;
+  const int iters = g.J * g.nk;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    const uint32_t bytes = (uint32_t)(L::kA * (g.a_lo ? 2 : 1) + L::kB * (g.b_lo ? 2 : 1));
-    for (int it = 0; it < total; ++it) {
-      const int s = it % kStages;
-      const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-      if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1)) {
-        s_abort = 1;
-        break;
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      const uint32_t bytes = (uint32_t)(L::kA * (g.a_lo ? 2 : 1) + L::kB * (g.b_lo ? 2 : 1));
+      uint32_t n = 0;
+      for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+        const int b = t / g.m_tiles;
+        const long long m0 = (long long)(t % g.m_tiles) * kTileM;
+        for (int it = 0; it < iters; ++it, ++n) {
+          const int s = (int)(n % kStages);
+          const uint32_t ph = (n / kStages) & 1u;
+          if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1)) {
+            s_abort = 1;
+            break;
+          }
+          const int j = it / g.nk, kb = it % g.nk;
+          const int arow = (int)(g.a_base + b * g.a_sb + j * g.a_sj + m0);
+          const int brow = (int)(g.b_base + b * g.b_sb + j * g.b_sj);
+          const uint32_t st = base + s * L::kStage;
+          mbar_expect_tx(full(s), bytes);
+          tma_load_2d(st, &mA, kb * kKB, arow, full(s));
+          if (g.a_lo) tma_load_2d(st + L::kA, &mAlo, kb * kKB, arow, full(s));
+          tma_load_2d(st + 2 * L::kA, &mB, kb * kKB, brow, full(s));
+          if (g.b_lo) tma_load_2d(st + 2 * L::kA + L::kB, &mBlo, kb * kKB, brow, full(s));
+        }
       }
-      const int j = it / g.nk, kb = it % g.nk;
-      const int arow = (int)(g.a_base + b * g.a_sb + j * g.a_sj + m0);
-      const int brow = (int)(g.b_base + b * g.b_sb + j * g.b_sj);
-      const uint32_t st = base + s * L::kStage;
-      mbar_expect_tx(full(s), bytes);
-      tma_load_2d(st, &mA, kb * kKB, arow, full(s));
-      if (g.a_lo) tma_load_2d(st + L::kA, &mAlo, kb * kKB, arow, full(s));
-      tma_load_2d(st + 2 * L::kA, &mB, kb * kKB, brow, full(s));
-      if (g.b_lo) tma_load_2d(st + 2 * L::kA + L::kB, &mBlo, kb * kKB, brow, full(s));
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t fmt = std::is_same<E, __nv_bfloat16>::value ? 1u : 0u;
-    constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
-                               ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-    bool ok = true;
-    for (int it = 0; it < total; ++it) {
-      const int s = it % kStages;
-      const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-      if (!mbar_wait(full(s), ph, g.err, 2)) {
-        ok = false;
-        s_abort = 1;
-        break;
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t fmt = std::is_same<E, __nv_bfloat16>::value ? 1u : 0u;
+      constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
+                                 ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+      uint32_t n = 0, lt = 0;
+      for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x, ++lt) {
+        const uint32_t acc = lt & 1u, use = lt >> 1;
+        if (!mbar_wait(tempty(acc), (use & 1u) ^ 1u, g.err, 4)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + acc * (uint32_t)NP;
+        bool ok = true;
+        for (int it = 0; it < iters; ++it, ++n) {
+          const int s = (int)(n % kStages);
+          const uint32_t ph = (n / kStages) & 1u;
+          if (!mbar_wait(full(s), ph, g.err, 2)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * L::kStage;
+          const uint64_t dA = sdesc(st), dAl = sdesc(st + L::kA);
+          const uint64_t dB = sdesc(st + 2 * L::kA), dBl = sdesc(st + 2 * L::kA + L::kB);
+#pragma unroll
+          for (int k = 0; k < kKB / 16; ++k) {
+            const uint64_t adv = (uint64_t)((k * 32) >> 4);  // 32 bytes per K = 16 step
+            mma_f16(d, dA + adv, dB + adv, idesc, (it > 0 || k > 0) ? 1u : 0u);
+            if (g.b_lo) mma_f16(d, dA + adv, dBl + adv, idesc, 1u);
+            if (g.a_lo) mma_f16(d, dAl + adv, dB + adv, idesc, 1u);
+          }
+          mma_commit(empty(s));
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        mma_commit(tfull(acc));
       }
+    }
+  } else {
+    // ---------------- epilogue (warps 0-3; warp w owns TMEM lanes 32w .. 32w + 31)
+    uint32_t lt = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u, use = lt >> 1;
+      const bool have = mbar_wait(tfull(acc), use & 1u, g.err, 3);
       tc_fence_after();
-      const uint32_t st = base + s * L::kStage;
-      const uint64_t dA = sdesc(st), dAl = sdesc(st + L::kA);
-      const uint64_t dB = sdesc(st + 2 * L::kA), dBl = sdesc(st + 2 * L::kA + L::kB);
-#pragma unroll
-      for (int k = 0; k < kKB / 16; ++k) {
-        const uint64_t adv = (uint64_t)((k * 32) >> 4);  // 32 bytes per K = 16 step
-        mma_f16(tmem, dA + adv, dB + adv, idesc, (it > 0 || k > 0) ? 1u : 0u);
-        if (g.b_lo) mma_f16(tmem, dA + adv, dBl + adv, idesc, 1u);
-        if (g.a_lo) mma_f16(tmem, dAl + adv, dB + adv, idesc, 1u);
-      }
-      mma_commit(empty(s));
-    }
-    if (ok) mma_commit(done);
-  }
-  __syncwarp();
-  // ---------------- epilogue (all 4 warps; warp w owns TMEM lanes 32w .. 32w + 31)
-  const bool have = mbar_wait(done, 0, g.err, 3);
-  tc_fence_after();
-  if (have && !s_abort) {
-    const long long m = m0 + warp * 32 + lane;
-    const long long mh = m / NP, ml = m % NP;
-    const long long row_off = g.o_base + b * g.o_sb + mh * g.s_mhi + ml * g.s_mlo;
-    const float sc = g.scale ? g.scale[b] : 1.0f;
+      if (!have || s_abort) break;
+      const int b = t / g.m_tiles;
+      const long long m = (long long)(t % g.m_tiles) * kTileM + warp * 32 + lane;
+      const long long mh = m / NP, ml = m % NP;
+      const long long row_off = g.o_base + b * g.o_sb + mh * g.s_mhi + ml * g.s_mlo;
+      const float sc = g.scale ? g.scale[b] : 1.0f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < NP; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (!g.out_split) {
-        float* o = reinterpret_cast<float*>(g.out) + row_off + c0 * g.s_n;
-        if (g.s_n == 1) {
+      for (int c0 = 0; c0 < NP; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + acc * (uint32_t)NP + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (!g.out_split) {
+          float* o = reinterpret_cast<float*>(g.out) + row_off + c0 * g.s_n;
+          if (g.beta) {
+            // accumulate with fire-and-forget reductions (every element has one owner)
 #pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            float4 r = make_float4(__uint_as_float(v[i]) * sc, __uint_as_float(v[i + 1]) * sc,
-                                   __uint_as_float(v[i + 2]) * sc, __uint_as_float(v[i + 3]) * sc);
-            float4* p = reinterpret_cast<float4*>(o + i);
-            if (g.beta) {
-              const float4 q = *p;
-              r.x += q.x; r.y += q.y; r.z += q.z; r.w += q.w;
+            for (int i = 0; i < 32; ++i) atomicAdd(o + i * g.s_n, __uint_as_float(v[i]) * sc);
+          } else if (g.s_n == 1) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(o + i) =
+                  make_float4(__uint_as_float(v[i]) * sc, __uint_as_float(v[i + 1]) * sc,
+                              __uint_as_float(v[i + 2]) * sc, __uint_as_float(v[i + 3]) * sc);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) o[i * g.s_n] = __uint_as_float(v[i]) * sc;
+          }
+        } else {
+          E* oh = reinterpret_cast<E*>(g.out) + row_off + c0 * g.s_n;
+          E* ol = reinterpret_cast<E*>(g.out_lo) + row_off + c0 * g.s_n;
+          if (g.s_n == 1) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 8) {
+              E h[8], l[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) split2<E>(__uint_as_float(v[i + u]) * sc, h[u], l[u]);
+              *reinterpret_cast<uint4*>(oh + i) = *reinterpret_cast<uint4*>(h);
+              *reinterpret_cast<uint4*>(ol + i) = *reinterpret_cast<uint4*>(l);
             }
-            *p = r;
-          }
-        } else {
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float* p = o + i * g.s_n;
-            const float r = __uint_as_float(v[i]) * sc;
-            *p = g.beta ? *p + r : r;
-          }
-        }
-      } else {
-        E* oh = reinterpret_cast<E*>(g.out) + row_off + c0 * g.s_n;
-        E* ol = reinterpret_cast<E*>(g.out_lo) + row_off + c0 * g.s_n;
-        if (g.s_n == 1) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 8) {
-            E h[8], l[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) split2<E>(__uint_as_float(v[i + u]) * sc, h[u], l[u]);
-            *reinterpret_cast<uint4*>(oh + i) = *reinterpret_cast<uint4*>(h);
-            *reinterpret_cast<uint4*>(ol + i) = *reinterpret_cast<uint4*>(l);
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            E h, l;
-            split2<E>(__uint_as_float(v[i]) * sc, h, l);
-            oh[i * g.s_n] = h;
-            ol[i * g.s_n] = l;
+            for (int i = 0; i < 32; ++i) {
+              E h, l;
+              split2<E>(__uint_as_float(v[i]) * sc, h, l);
+              oh[i * g.s_n] = h;
+              ol[i * g.s_n] = l;
+            }
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)NP)
+                 "r"((uint32_t)(2 * NP))
                  : "memory");
   }
 }
@@ -607,9 +646,20 @@ void mixed_workspace_free(cc_tables t) {
   t->ws.mx = nullptr;
 }
 
+static int tc_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <int NP, typename E>
 static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const CUtensorMap& B,
-                           const CUtensorMap& Blo, const TcArgs& g, int m_tiles, int batches,
+                           const CUtensorMap& Blo, TcArgs g, int m_tiles, int batches,
                            cudaStream_t st) {
   auto kern = k_tc_gemm<NP, E>;
   const int smem = TcSmem<NP>::kBytes;
@@ -618,7 +668,11 @@ static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const C
     CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
-  kern<<<dim3(m_tiles, batches), 128, smem, st>>>(A, Alo, B, Blo, g);
+  g.m_tiles = m_tiles;
+  g.batches = batches;
+  const int total = m_tiles * batches;
+  const int grid = total < tc_sm_count() ? total : tc_sm_count();  // one CTA per SM, persistent
+  kern<<<grid, kTcThreads, smem, st>>>(A, Alo, B, Blo, g);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }
