@@ -223,8 +223,8 @@ cc_status cc_set_gemm_tiles(int precision, int small_tile, int large_tile, int t
  * Box i has its own cutoff, side, node count and mesh (p, any kernel; defaults as in
  * cc_build_tables) and Fermi radius R_F (1 <= R_F <= p.R); grid side 2 p.R + 1 <= 49.
  * Exchange sums of every box (Sec. III) come from one launch that takes work items
- * (box, group of nodes) from an atomic counter, longest first; the last CTA to finish a
- * box writes its eps block and E_x.  The first call for a given (precision, eps_dev,
+ * (box, x slab, group of nodes) from an atomic counter, longest first; the last CTA to
+ * finish a slab writes that slab of eps, the last to finish a box its E_x.  The first call for a given (precision, eps_dev,
  * Ex_dev) captures the launch in a CUDA graph, later calls replay it. */
 typedef struct {
   cc_table_params p;
@@ -246,15 +246,15 @@ cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets_host, int*
 cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
                             void* stream);
 
-/* Launch shape: CTAs per SM (1..8), oversubscription (work items per CTA slot, the
- * granularity big boxes are cut to), prefer_smem (intermediates in shared memory when
- * they fit).  Drops captured graphs. */
-cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub, int prefer_smem);
+/* Launch shape: CTAs per SM (1..16) and oversubscription (1..64): the plan cuts the
+ * boxes into about (#SMs x CTAs per SM x oversubscription) work items (x slab x node
+ * group), in proportion to each box's cost.  Drops captured graphs. */
+cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub);
 
-/* Autotuner: times every launch shape (CTAs per SM in {1, 2}, oversubscription in
- * {1, 2, 4, 8}, shared or global intermediates) with CUDA events, median of `reps`
- * replays, keeps the fastest.  choice_host[3] receives it, *ms_host its time.
- * Writes eps_dev / Ex_dev (valid sums) while timing.  Synchronous. */
+/* Autotuner: times every launch shape (CTAs per SM in {2, 4, 8}, oversubscription in
+ * {1, 2, 4}) with CUDA events, median of `reps` replays, keeps the fastest.
+ * choice_host[2] receives it, *ms_host its time.  Writes eps_dev / Ex_dev (valid sums)
+ * while timing.  Synchronous. */
 cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, double* Ex_dev, int reps,
                         int* choice_host, float* ms_host, void* stream);
 

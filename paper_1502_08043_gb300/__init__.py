@@ -81,7 +81,7 @@ SIGNATURES = {
     "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
     "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),
     "cc_batch_exchange": (_I, [_P, _I, _P, _P, _P]),
-    "cc_batch_set_plan": (_I, [_P, _I, _I, _I]),
+    "cc_batch_set_plan": (_I, [_P, _I, _I]),
     "cc_batch_tune": (_I, [_P, _I, _P, _P, _I, _P, _P, _P]),
     "cc_batch_free": (_I, [_P]),
     "cc_status_string": (ctypes.c_char_p, [_I]),
@@ -354,12 +354,11 @@ class Batch:
             self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), _stream(stream, eps)))
         return eps, Ex
 
-    def set_plan(self, ctas_per_sm=1, oversub=2, prefer_smem=True):
-        _check("cc_batch_set_plan", lib().cc_batch_set_plan(self.handle, ctas_per_sm, oversub,
-                                                            1 if prefer_smem else 0))
+    def set_plan(self, ctas_per_sm=4, oversub=2):
+        _check("cc_batch_set_plan", lib().cc_batch_set_plan(self.handle, ctas_per_sm, oversub))
 
     def tune(self, eps, Ex, reps=5, stream=None):
-        choice = np.zeros(3, dtype=np.int32)
+        choice = np.zeros(2, dtype=np.int32)
         ms = ctypes.c_float()
         _check("cc_batch_tune", lib().cc_batch_tune(
             self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), int(reps), choice.ctypes.data,
@@ -368,8 +367,7 @@ class Batch:
         items = ctypes.c_int()
         lib().cc_batch_info(self.handle, ctypes.byref(n), None, ctypes.byref(items), None)
         self.n_items = items.value
-        return {"ctas_per_sm": int(choice[0]), "oversub": int(choice[1]),
-                "smem_intermediates": bool(choice[2]), "ms": ms.value}
+        return {"ctas_per_sm": int(choice[0]), "oversub": int(choice[1]), "ms": ms.value}
 
     def free(self):
         if self._h is not None:

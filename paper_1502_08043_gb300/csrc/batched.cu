@@ -1,13 +1,12 @@
-// Fused small-grid exchange sums (single box, grid side <= 49) and the batched engine:
+// Slab-wise exchange sums (single box, grid side <= 49) and the batched engine:
 // many independent boxes with uneven cutoffs, Fermi radii and quadrature orders in one
 // persistent launch, captured once in a CUDA graph and replayed.
 //
 // Work items are (box, group of consecutive nodes); a persistent grid takes them from an
 // atomic counter in order of decreasing cost (longest-processing-time first), and the
 // CTA that completes the last item of a box finalises that box (see fused.cuh).  The
-// granularity of the items (how many items a big box is cut into), the number of CTAs
-// per SM and the placement of the per-node intermediates (shared or global memory) are
-// chosen by cc_batch_tune, which times each candidate with CUDA events.
+// granularity of the items (how many node groups each box is cut into) and the number of
+// CTAs per SM are chosen by cc_batch_tune, which times each candidate with CUDA events.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,15 +18,15 @@
 namespace cc {
 
 struct FusedPlan {
-  int n_boxes = 0, n_items = 0, grid = 0, ctas_per_sm = 1, oversub = 2, prefer_smem = 1;
-  long long max_g3 = 0;
+  int n_boxes = 0, n_items = 0, grid = 0, ctas_per_sm = 4, oversub = 1, max_mg = 0;
+  int n_slabs = 0;
   FusedBox<float>* boxes32 = nullptr;
   FusedBox<double>* boxes64 = nullptr;
   FusedItem* items = nullptr;
-  int* counters = nullptr;  // [1 + n_boxes]: work counter, per-box done counters
-  void* part = nullptr;     // item partials (sized for double)
-  void* scratch = nullptr;  // per-CTA P / Q when they do not fit in shared memory
-  size_t part_bytes = 0, scratch_bytes = 0, bytes = 0;
+  int* counters = nullptr;  // [1 + n_boxes + n_slabs]: work, per-box and per-slab done
+  double* slab_ex = nullptr;
+  void* part = nullptr;     // slab partials (sized for double)
+  size_t bytes = 0;
 };
 
 static int sm_count() {
@@ -41,10 +40,8 @@ static int sm_count() {
   return n;
 }
 
-static constexpr size_t kFusedSmemCap = 200 * 1024;
-
 static void plan_free(FusedPlan* p) {
-  void* ptrs[] = {p->boxes32, p->boxes64, p->items, p->counters, p->part, p->scratch};
+  void* ptrs[] = {p->boxes32, p->boxes64, p->items, p->counters, p->slab_ex, p->part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *p = FusedPlan();
@@ -56,36 +53,47 @@ struct BoxIn {
   long long eps_off;
 };
 
-// Build a plan: cut box b into ceil(cost_b / target) items (target from the total cost,
-// the grid and the oversubscription factor), order items by decreasing cost.
+constexpr int kMaxGroups = 16;
+
+// Build a plan: about slots x oversub items in total, shared among the boxes in
+// proportion to their cost Mg^4 S; a box gets Mg slabs x n_groups node groups
+// (n_groups <= min(S, 16)); items are ordered by decreasing cost.
 static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, int oversub,
-                            int prefer_smem, FusedPlan* out) {
+                            FusedPlan* out) {
   FusedPlan p;
   p.n_boxes = (int)boxes.size();
   p.ctas_per_sm = ctas_per_sm;
   p.oversub = oversub;
-  p.prefer_smem = prefer_smem;
   double total = 0.0;
   for (const BoxIn& b : boxes) {
     const double mg = b.t->Mg;
     total += mg * mg * mg * mg * b.t->S_eff;
-    p.max_g3 = std::max(p.max_g3, (long long)b.t->Mg * b.t->Mg * b.t->Mg);
+    p.max_mg = std::max(p.max_mg, b.t->Mg);
   }
-  const int slots = sm_count() * ctas_per_sm;
-  const double target = total / ((double)slots * oversub);
+  const double want = (double)sm_count() * ctas_per_sm * oversub;
   std::vector<FusedItem> items;
   std::vector<double> cost;
-  std::vector<int> n_items(boxes.size());
+  std::vector<int> groups(boxes.size()), slab0(boxes.size());
+  std::vector<long long> part_off(boxes.size());
+  long long acc = 0;
+  int slabs = 0;
   for (size_t b = 0; b < boxes.size(); ++b) {
     const cc_tables t = boxes[b].t;
-    const double per_node = (double)t->Mg * t->Mg * t->Mg * t->Mg;
-    int k = (int)std::ceil(per_node * t->S_eff / std::max(target, 1.0));
-    k = std::max(1, std::min(k, t->S_eff));
-    n_items[b] = k;
+    const double mg = t->Mg;
+    const double share = want * mg * mg * mg * mg * t->S_eff / std::max(total, 1.0);
+    int k = (int)std::lround(share / mg);
+    k = std::max(1, std::min(k, std::min(t->S_eff, kMaxGroups)));
+    groups[b] = k;
+    slab0[b] = slabs;
+    slabs += t->Mg;
+    part_off[b] = acc;
+    acc += (long long)k * t->Mg * t->Mg * t->Mg;
     for (int g = 0; g < k; ++g) {
       const int s0 = (int)((long long)t->S_eff * g / k), s1 = (int)((long long)t->S_eff * (g + 1) / k);
-      items.push_back({(int)b, s0, s1, g});
-      cost.push_back(per_node * (s1 - s0));
+      for (int x = 0; x < t->Mg; ++x) {
+        items.push_back({(int)b, x, s0, s1, g});
+        cost.push_back(mg * mg * mg * (s1 - s0));
+      }
     }
   }
   std::vector<int> order(items.size());
@@ -94,17 +102,8 @@ static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, in
   std::vector<FusedItem> sorted(items.size());
   for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
   p.n_items = (int)sorted.size();
-  p.grid = std::max(1, std::min(p.n_items, slots));
-  // partials
-  std::vector<long long> part_off(boxes.size());
-  long long acc = 0;
-  for (size_t b = 0; b < boxes.size(); ++b) {
-    part_off[b] = acc;
-    const long long g3 = (long long)boxes[b].t->Mg * boxes[b].t->Mg * boxes[b].t->Mg;
-    acc += (long long)n_items[b] * 2 * g3;
-  }
-  p.part_bytes = (size_t)acc * sizeof(double);
-  p.scratch_bytes = (size_t)p.grid * 2 * p.max_g3 * sizeof(double);
+  p.n_slabs = slabs;
+  p.grid = std::max(1, std::min(p.n_items, sm_count() * ctas_per_sm));
   auto alloc = [&](void** ptr, size_t bytes) -> cc_status {
     cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
     if (e != cudaSuccess) {
@@ -118,25 +117,29 @@ static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, in
   if (s == CC_OK) s = alloc((void**)&p.boxes32, sizeof(FusedBox<float>) * boxes.size());
   if (s == CC_OK) s = alloc((void**)&p.boxes64, sizeof(FusedBox<double>) * boxes.size());
   if (s == CC_OK) s = alloc((void**)&p.items, sizeof(FusedItem) * sorted.size());
-  if (s == CC_OK) s = alloc((void**)&p.counters, sizeof(int) * (1 + boxes.size()));
-  if (s == CC_OK) s = alloc(&p.part, p.part_bytes);
-  if (s == CC_OK) s = alloc(&p.scratch, p.scratch_bytes);
+  if (s == CC_OK) s = alloc((void**)&p.counters, sizeof(int) * (1 + boxes.size() + slabs));
+  if (s == CC_OK) s = alloc((void**)&p.slab_ex, sizeof(double) * slabs);
+  if (s == CC_OK) s = alloc(&p.part, (size_t)acc * sizeof(double));
   if (s != CC_OK) {
     plan_free(&p);
     return s;
   }
+  int* slab_done = p.counters + 1 + boxes.size();
   std::vector<FusedBox<float>> b32(boxes.size());
   std::vector<FusedBox<double>> b64(boxes.size());
   for (size_t b = 0; b < boxes.size(); ++b) {
     const cc_tables t = boxes[b].t;
     const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
-    b32[b] = FusedBox<float>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, n_items[b],
-                             t->pref, t->d.Tm32, t->d.WDm32, t->d.Dbar32,
-                             reinterpret_cast<float*>(p.part) + part_off[b], boxes[b].eps_off,
+    const int n_items = t->Mg * groups[b];
+    b32[b] = FusedBox<float>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, groups[b], n_items,
+                             t->pref, t->d.Tm32, t->d.Tm64, t->d.w64, t->d.Dbar64,
+                             reinterpret_cast<float*>(p.part) + part_off[b],
+                             slab_done + slab0[b], p.slab_ex + slab0[b], boxes[b].eps_off,
                              (int)b};
-    b64[b] = FusedBox<double>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, n_items[b],
-                              t->pref, t->d.Tm64, t->d.WDm64, t->d.Dbar64,
-                              reinterpret_cast<double*>(p.part) + part_off[b], boxes[b].eps_off,
+    b64[b] = FusedBox<double>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, groups[b],
+                              n_items, t->pref, t->d.Tm64, t->d.Tm64, t->d.w64, t->d.Dbar64,
+                              reinterpret_cast<double*>(p.part) + part_off[b],
+                              slab_done + slab0[b], p.slab_ex + slab0[b], boxes[b].eps_off,
                               (int)b};
   }
   if (cudaMemcpy(p.boxes32, b32.data(), sizeof(FusedBox<float>) * b32.size(),
@@ -155,22 +158,17 @@ static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, in
 template <typename T>
 static cc_status plan_launch(const FusedPlan& p, int rf_override, T* eps, double* Ex,
                              cudaStream_t st) {
-  const size_t pq = (size_t)2 * p.max_g3 * sizeof(T);
-  const long long mg = llround(cbrt((double)p.max_g3));
-  const size_t mats = (((size_t)3 * mg * mg * sizeof(T) + (size_t)mg * mg * 4) + 15) & ~(size_t)15;
-  const int smem_pq = (p.prefer_smem && mats + pq <= kFusedSmemCap) ? 1 : 0;
-  const size_t smem = mats + (smem_pq ? pq : 0);
+  const size_t smem = slab_smem_bytes<T>(p.max_mg);
   auto kern = k_fused_exchange<T>;
-  CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap));
+  CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem));
-  int grid = std::min(p.grid, std::max(1, per_sm) * sm_count());
-  CC_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int) * (1 + p.n_boxes), st));
+  const int grid = std::min(p.grid, std::max(1, per_sm) * sm_count());
+  CC_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int) * (1 + p.n_boxes + p.n_slabs), st));
   const FusedBox<T>* boxes;
   if constexpr (sizeof(T) == 4) boxes = reinterpret_cast<const FusedBox<T>*>(p.boxes32);
   else boxes = reinterpret_cast<const FusedBox<T>*>(p.boxes64);
   kern<<<grid, kFusedThreads, smem, st>>>(boxes, p.items, p.n_items, p.counters, p.counters + 1,
-                                          reinterpret_cast<T*>(p.scratch), p.max_g3, smem_pq,
                                           rf_override, eps, Ex);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
@@ -182,8 +180,7 @@ cc_status fused_single_alloc(cc_tables t) {
   FusedPlan* p = new (std::nothrow) FusedPlan();
   if (!p) return CC_ERR_ALLOC;
   std::vector<BoxIn> one{{t, 1, 0}};
-  // one node per item: S_eff CTAs work on one box
-  cc_status s = plan_build(one, 1, (int)1e6, 1, p);
+  cc_status s = plan_build(one, 4, 1, p);
   if (s != CC_OK) {
     delete p;
     return s;
@@ -234,11 +231,11 @@ static void batch_drop_graphs(cc_batch b) {
   b->graphs.clear();
 }
 
-static cc_status batch_plan(cc_batch b, int ctas_per_sm, int oversub, int prefer_smem) {
+static cc_status batch_plan(cc_batch b, int ctas_per_sm, int oversub) {
   std::vector<BoxIn> in;
   for (size_t i = 0; i < b->tabs.size(); ++i) in.push_back({b->tabs[i], b->spec[i].R_F, b->eps_off[i]});
   FusedPlan p;
-  CC_TRY(plan_build(in, ctas_per_sm, oversub, prefer_smem, &p));
+  CC_TRY(plan_build(in, ctas_per_sm, oversub, &p));
   batch_drop_graphs(b);
   plan_free(&b->plan);
   b->plan = p;
@@ -269,7 +266,7 @@ extern "C" cc_status cc_batch_create(const cc_box* boxes_host, int nbox, void* s
     off += (long long)t->Mg * t->Mg * t->Mg;
   }
   b->eps_off.push_back(off);
-  if (s == CC_OK) s = batch_plan(b, 1, 2, 1);
+  if (s == CC_OK) s = batch_plan(b, 4, 2);
   if (s != CC_OK) {
     cc_batch_free(b);
     return s;
@@ -293,10 +290,9 @@ extern "C" cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets
   return CC_OK;
 }
 
-extern "C" cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub,
-                                       int prefer_smem) {
-  if (!b || ctas_per_sm < 1 || ctas_per_sm > 8 || oversub < 1 || oversub > 1024) return CC_ERR_ARG;
-  return batch_plan(b, ctas_per_sm, oversub, prefer_smem ? 1 : 0);
+extern "C" cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub) {
+  if (!b || ctas_per_sm < 1 || ctas_per_sm > 16 || oversub < 1 || oversub > 64) return CC_ERR_ARG;
+  return batch_plan(b, ctas_per_sm, oversub);
 }
 
 extern "C" cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
@@ -341,53 +337,50 @@ extern "C" cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev,
   return CC_OK;
 }
 
-// Autotuner: time every (CTAs per SM, oversubscription, intermediates placement)
-// candidate with CUDA events (median of `reps` graph replays after one warm-up) and keep
-// the fastest.  Writes the choice to choice_host[3] and its time to *ms_host.
+// Autotuner: time every (CTAs per SM, oversubscription) candidate with CUDA events
+// (median of `reps` graph replays after one warm-up) and keep the fastest.  Writes the
+// choice to choice_host[2] and its time to *ms_host.
 extern "C" cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
                                    int reps, int* choice_host, float* ms_host, void* stream) {
   if (!b || !eps_dev || !Ex_dev || reps < 1) return CC_ERR_ARG;
   cudaStream_t st = as_stream(stream);
-  const int cps[] = {1, 2};
-  const int ovs[] = {1, 2, 4, 8};
-  const int plc[] = {1, 0};
+  const int cps[] = {2, 4, 8};
+  const int ovs[] = {1, 2, 4};
   float best = 1e30f;
-  int bc[3] = {1, 2, 1};
+  int bc[2] = {4, 2};
   cudaEvent_t e0, e1;
   CC_CUDA(cudaEventCreate(&e0));
   CC_CUDA(cudaEventCreate(&e1));
   cc_status s = CC_OK;
   for (int c : cps)
-    for (int o : ovs)
-      for (int pl : plc) {
-        if (s != CC_OK) break;
-        s = batch_plan(b, c, o, pl);
-        if (s != CC_OK) break;
+    for (int o : ovs) {
+      if (s != CC_OK) break;
+      s = batch_plan(b, c, o);
+      if (s != CC_OK) break;
+      s = cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream);
+      std::vector<float> tm;
+      for (int r = 0; r < reps && s == CC_OK; ++r) {
+        cudaEventRecord(e0, st);
         s = cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream);
-        std::vector<float> t;
-        for (int r = 0; r < reps && s == CC_OK; ++r) {
-          cudaEventRecord(e0, st);
-          s = cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream);
-          cudaEventRecord(e1, st);
-          if (cudaEventSynchronize(e1) != cudaSuccess) s = CC_ERR_CUDA;
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          t.push_back(ms);
-        }
-        if (s != CC_OK) break;
-        std::sort(t.begin(), t.end());
-        const float med = t[t.size() / 2];
-        if (med < best) {
-          best = med;
-          bc[0] = c;
-          bc[1] = o;
-          bc[2] = pl;
-        }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = CC_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tm.push_back(ms);
       }
+      if (s != CC_OK) break;
+      std::sort(tm.begin(), tm.end());
+      const float med = tm[tm.size() / 2];
+      if (med < best) {
+        best = med;
+        bc[0] = c;
+        bc[1] = o;
+      }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CC_TRY(s);
-  CC_TRY(batch_plan(b, bc[0], bc[1], bc[2]));
+  CC_TRY(batch_plan(b, bc[0], bc[1]));
   if (choice_host) memcpy(choice_host, bc, sizeof(bc));
   if (ms_host) *ms_host = best;
   return CC_OK;

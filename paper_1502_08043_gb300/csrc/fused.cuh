@@ -1,11 +1,23 @@
-// Fused exchange-sum work items for small grids (grid side Mg <= 49): one CTA computes
-// the contribution of a group of quadrature nodes of one box to the exchange sums
-// (Sec. III; node sum of Sec. II Eq. 14 with the D = T - I split of the periodic
-// kernel), keeping the per-node intermediates P_s = O x3 T_s and Q_s = P_s x2 T_s in
-// shared memory when they fit, else in a per-CTA slice of global scratch.  The last
-// CTA to finish a box adds the item partials, writes eps and reduces E_x (FP64).
-// Work items are handed out by an atomic counter to a persistent grid; nothing waits
-// on another CTA, so the scheme cannot deadlock whatever the residency.
+// Slab-wise exchange sums on the SIMT cores (FP32 / FP64), grid side Mg <= 63, used for
+// single boxes and for the batched engine.
+//
+// Sec. III exchange of the uniform electron gas with the node sum of Sec. II Eq. 14.
+// Periodic kernel, D_s = T_s - I (no self term, no cancellation):
+//   E = sum_s w_s (O x1 D x2 T x3 T + O x2 D x3 T) + O x3 Dbar,   Dbar = sum_s w_s D_s
+//     = sum_s w_s [ (R_s x2 T_s + A_s) x3 T_s ] + O x3 Dbar,
+//   R_s = O x1 D_s,  A_s = O x2 D_s.
+// Box kernel: E = sum_s w_s (R_s x2 T_s) x3 T_s with R_s = O x1 T_s, no A, no Dbar term.
+// The occupation is a Fermi sphere, so every line of O along an axis is 1 on one
+// contiguous range [R - h, R + h] (h = floor(sqrt(R_F^2 - u^2 - v^2)) for the other two
+// coordinates u, v).  A mode product of O with M is therefore a difference of two prefix
+// sums of the rows of M; the prefix sums are formed in FP64, so the difference keeps full
+// precision.  What is left per node and x slab are two Mg x Mg x Mg products
+// (U = T R_x + A_x, then U T), all in shared memory.
+// Work item = (box, x slab, group of nodes); the item's slab of E (Kahan-summed over
+// its nodes) goes to a partial buffer; the CTA that completes the last group of a slab
+// adds the slab's partials (Kahan), writes its eps and its FP64 share of E_x, and the
+// CTA that completes the last slab of a box adds the shares in slab order.  Items are
+// taken from an atomic counter by a persistent grid; no CTA ever waits for another.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -13,166 +25,65 @@
 
 namespace cc {
 
+constexpr int kSlabMaxMg = 63;
+
 template <typename T>
 struct FusedBox {
-  int R, R_F, Mg, S_eff, periodic, n_items;
+  int R, R_F, Mg, S_eff, periodic, n_groups, n_items;
   double pref;
-  const T* Tm;   // [S_eff][Mg][Mg]  T_s
-  const T* WD;   // [S_eff][Mg][Mg]  w_s D_s (periodic) or w_s T_s (box)
-  const T* Db;   // [Mg][Mg] sum_s w_s D_s (periodic)
-  T* part;       // [n_items][2][Mg^3]  Kahan sum and compensation per item
-  long long eps_off;  // offset of this box's eps block in the output
-  int ex_idx;         // this box's E_x pair in the output
+  const T* Tm;         // [S_eff][Mg][Mg]  T_s
+  const double* T64;   // [S_eff][Mg][Mg]  T_s in FP64 (prefix sums)
+  const double* w64;   // [S_eff]
+  const double* Db64;  // [Mg][Mg] sum_s w_s D_s (periodic)
+  T* part;             // [n_groups][Mg][Mg][Mg] slab partials
+  int* slab_done;      // [Mg] finished groups per slab
+  double* slab_ex;     // [Mg] FP64 sum of eps over the Fermi sphere, per slab
+  long long eps_off;   // offset of this box's eps block in the output
+  int ex_idx;          // this box's E_x pair in the output
 };
 
 struct FusedItem {
-  int box, s0, s1, g;
+  int box, x, s0, s1, g;
 };
 
-constexpr int kFusedThreads = 512;
+constexpr int kFusedThreads = 128;
+
+// shared-memory layout of one item (Mg = the box's grid side, mm = Mg * Mg):
+//   double CD[Mg][Mg + 1]   prefix sums of the rows of the node's D (or T)
+//   short  H[Mg][Mg]        sphere half-lengths, -1 for an empty line
+//   T      sT[mm], sR[mm], sU[mm], sE[mm], sC[mm]
+template <typename T>
+__host__ __device__ inline size_t slab_smem_bytes(int Mg) {
+  const size_t mm = (size_t)Mg * Mg;
+  size_t b = sizeof(double) * Mg * (Mg + 1);
+  b += ((sizeof(short) * mm + 15) / 16) * 16;
+  b += 5 * mm * sizeof(T);
+  return b;
+}
+
+__device__ __forceinline__ int isqrt_floor(int v) {
+  int h = (int)sqrtf((float)v);
+  while (h * h > v) --h;
+  while ((h + 1) * (h + 1) <= v) ++h;
+  return h;
+}
 
 template <typename T>
-__device__ __forceinline__ void kahan_add(T* e, T* c, long long i, T v) {
-  const T y = v - c[i];
-  const T t = e[i] + y;
-  c[i] = (t - e[i]) - y;
-  e[i] = t;
+__device__ __forceinline__ void kahan_add(T* e, T* c, int o, T v) {
+  const T yv = v - c[o];
+  const T t = e[o] + yv;
+  c[o] = (t - e[o]) - yv;
+  e[o] = t;
 }
 
-__device__ __forceinline__ bool occ_at(int x, int y, int z, int R, int R_F) {
-  const int a = x - R, b = y - R, c = z - R;
-  return a * a + b * b + c * c <= R_F * R_F;
-}
-
-// z mode on the occupation tensor: P[(x,y)][z'] = sum_z O[x][y][z] M[z][z'] (M symmetric);
-// row (x,y) of O is 1 exactly on the contiguous z range zr[row] = (z_lo, z_hi) of the
-// Fermi sphere (empty when z_lo > z_hi); written (overwrite) or Kahan-added into (E, C)
-template <typename T, bool kAcc>
-__device__ void zmode_occ(const T* __restrict__ M, int Mg, const short2* zr, T* P, T* E, T* C) {
-  const int rows = Mg * Mg;
-  const int rb = (rows + 3) / 4, cb = (Mg + 3) / 4;
-  for (int blk = threadIdx.x; blk < rb * cb; blk += blockDim.x) {
-    const int r0 = (blk / cb) * 4, c0 = (blk % cb) * 4;
-    T acc[4][4] = {};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = r0 + i;
-      if (r >= rows) continue;
-      const short2 z = zr[r];
-      for (int zz = z.x; zz <= z.y; ++zz) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += (c0 + j < Mg) ? M[zz * Mg + c0 + j] : T(0);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = r0 + i;
-      if (r >= rows) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (c0 + j >= Mg) continue;
-        const long long o = (long long)r * Mg + c0 + j;
-        if (kAcc) kahan_add(E, C, o, acc[i][j]);
-        else P[o] = acc[i][j];
-      }
-    }
-  }
-}
-
-// y mode: out[x][y'][z] (=|+=) sum_y M[y'][y] X[x][y][z]
-template <typename T, bool kAcc>
-__device__ void ymode(const T* __restrict__ M, const T* X, int Mg, T* out, T* E, T* C) {
-  const int yb = (Mg + 3) / 4, zb = (Mg + 3) / 4;
-  const int nblk = Mg * yb * zb;
-  for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
-    const int x = blk / (yb * zb);
-    const int rem = blk % (yb * zb);
-    const int y0 = (rem / zb) * 4, z0 = (rem % zb) * 4;
-    T acc[4][4] = {};
-    const T* Xx = X + (long long)x * Mg * Mg;
-    for (int y = 0; y < Mg; ++y) {
-      T m[4], v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) m[i] = (y0 + i < Mg) ? M[(y0 + i) * Mg + y] : T(0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = (z0 + j < Mg) ? Xx[y * Mg + z0 + j] : T(0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += m[i] * v[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (y0 + i >= Mg) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (z0 + j >= Mg) continue;
-        const long long o = ((long long)x * Mg + y0 + i) * Mg + z0 + j;
-        if (kAcc) kahan_add(E, C, o, acc[i][j]);
-        else out[o] = acc[i][j];
-      }
-    }
-  }
-}
-
-// x mode (accumulating): E[x][(y,z)] += sum_x' M[x][x'] X[x'][(y,z)]
 template <typename T>
-__device__ void xmode_acc(const T* __restrict__ M, const T* X, int Mg, T* E, T* C) {
-  const int N = Mg * Mg;
-  const int xb = (Mg + 3) / 4, nb = (N + 3) / 4;
-  for (int blk = threadIdx.x; blk < xb * nb; blk += blockDim.x) {
-    const int x0 = (blk / nb) * 4, n0 = (blk % nb) * 4;
-    T acc[4][4] = {};
-    for (int xp = 0; xp < Mg; ++xp) {
-      T m[4], v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) m[i] = (x0 + i < Mg) ? M[(x0 + i) * Mg + xp] : T(0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = (n0 + j < N) ? X[(long long)xp * N + n0 + j] : T(0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += m[i] * v[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (x0 + i >= Mg) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (n0 + j >= N) continue;
-        kahan_add(E, C, (long long)(x0 + i) * N + n0 + j, acc[i][j]);
-      }
-    }
-  }
-}
-
-// One persistent launch over all items of all boxes.  Scratch for P and Q: dynamic
-// shared memory when smem_pq != 0, else gscratch + blockIdx.x * 2 * max_g3.
-template <typename T>
-__global__ void __launch_bounds__(kFusedThreads, 1)
+__global__ void __launch_bounds__(kFusedThreads)
     k_fused_exchange(const FusedBox<T>* __restrict__ boxes, const FusedItem* __restrict__ items,
-                     int n_items, int* work, int* done, T* gscratch, long long max_g3,
-                     int smem_pq, int rf_override, T* eps_out, double* ex_out) {
+                     int n_items, int* work, int* done, int rf_override, T* eps_out,
+                     double* ex_out) {
   extern __shared__ __align__(16) unsigned char fsmem[];
   __shared__ int s_item, s_last;
   __shared__ double s_red[kFusedThreads];
-  // dynamic shared memory: [Ts | Ws | Db : 3 Mg_max^2] [z ranges: Mg_max^2 short2] [P | Q]
-  const int mgmax = (int)llround(cbrt((double)max_g3));
-  T* sT = reinterpret_cast<T*>(fsmem);
-  T* sW = sT + mgmax * mgmax;
-  T* sD = sW + mgmax * mgmax;
-  short2* zr = reinterpret_cast<short2*>(sD + mgmax * mgmax);
-  T* P;
-  T* Q;
-  if (smem_pq) {
-    const size_t off = ((size_t)3 * mgmax * mgmax * sizeof(T) + (size_t)mgmax * mgmax * 4 + 15) &
-                       ~(size_t)15;
-    P = reinterpret_cast<T*>(fsmem + off);
-    Q = P + max_g3;
-  } else {
-    P = gscratch + (long long)blockIdx.x * 2 * max_g3;
-    Q = P + max_g3;
-  }
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
     __syncthreads();
@@ -182,68 +93,132 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const FusedItem item = items[it];
     FusedBox<T> bx = boxes[item.box];
     if (rf_override > 0) bx.R_F = rf_override;
-    const int Mg = bx.Mg;
-    const long long G3 = (long long)Mg * Mg * Mg, M2 = (long long)Mg * Mg;
-    T* E = bx.part + (long long)item.g * 2 * G3;
-    T* C = E + G3;
-    for (long long i = threadIdx.x; i < 2 * G3; i += blockDim.x) E[i] = T(0);
-    for (int r = threadIdx.x; r < M2; r += blockDim.x) {   // Fermi-sphere z range per row
-      const int x = r / Mg - bx.R, y = r % Mg - bx.R;
-      const int h2 = bx.R_F * bx.R_F - x * x - y * y;
-      short2 z = make_short2(1, 0);
-      if (h2 >= 0) {
-        int h = (int)sqrtf((float)h2);
-        while (h * h > h2) --h;
-        while ((h + 1) * (h + 1) <= h2) ++h;
-        z = make_short2((short)(bx.R - h), (short)(bx.R + h));
-      }
-      zr[r] = z;
+    const int Mg = bx.Mg, R = bx.R, mm = Mg * Mg, x = item.x;
+    double* CD = reinterpret_cast<double*>(fsmem);
+    short* H = reinterpret_cast<short*>(CD + Mg * (Mg + 1));
+    T* sT = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(H) +
+                                 ((sizeof(short) * mm + 15) / 16) * 16);
+    T* sR = sT + mm;
+    T* sU = sR + mm;
+    T* sE = sU + mm;
+    T* sC = sE + mm;
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      const int u = i / Mg - R, v = i % Mg - R;
+      const int h2 = bx.R_F * bx.R_F - u * u - v * v;
+      H[i] = (short)(h2 >= 0 ? isqrt_floor(h2) : -1);
+      sE[i] = T(0);
+      sC[i] = T(0);
     }
     __syncthreads();
+    const int cb = (Mg + 3) / 4;
     for (int s = item.s0; s < item.s1; ++s) {
-      for (int i = threadIdx.x; i < M2; i += blockDim.x) {
-        sT[i] = bx.Tm[s * M2 + i];
-        sW[i] = bx.WD[s * M2 + i];
+      const double* Ts64 = bx.T64 + (long long)s * mm;
+      // prefix sums of the rows of X = D_s (periodic) or T_s (box), FP64
+      for (int a = threadIdx.x; a < Mg; a += blockDim.x) {
+        double acc = 0.0;
+        CD[a * (Mg + 1)] = 0.0;
+        for (int k = 0; k < Mg; ++k) {
+          acc += (bx.periodic && k == a) ? 0.0 : Ts64[a * Mg + k];
+          CD[a * (Mg + 1) + k + 1] = acc;
+        }
+      }
+      for (int i = threadIdx.x; i < mm; i += blockDim.x) sT[i] = bx.Tm[(long long)s * mm + i];
+      __syncthreads();
+      // R_x[y][z] = sum_{x' on the x line at (y, z)} X[x][x']
+      for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+        const int h = H[i];
+        sR[i] = h < 0 ? T(0)
+                      : (T)(CD[x * (Mg + 1) + R + h + 1] - CD[x * (Mg + 1) + R - h]);
       }
       __syncthreads();
-      zmode_occ<T, false>(sT, Mg, zr, P, nullptr, nullptr);             // P = O x3 T
+      // U[y'][z] = sum_y T[y'][y] R_x[y][z] + A_x[y'][z],
+      // A_x[y'][z] = sum_{y on the y line at (x, z)} D[y'][y]   (periodic only)
+      for (int blk = threadIdx.x; blk < Mg * cb; blk += blockDim.x) {
+        const int yp = blk / cb, z0 = (blk % cb) * 4;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int y = 0; y < Mg; ++y) {
+          const T tv = sT[yp * Mg + y];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (z0 + j < Mg) acc[j] += tv * sR[y * Mg + z0 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int z = z0 + j;
+          if (z >= Mg) continue;
+          T a = T(0);
+          if (bx.periodic) {
+            const int h = H[x * Mg + z];
+            if (h >= 0) a = (T)(CD[yp * (Mg + 1) + R + h + 1] - CD[yp * (Mg + 1) + R - h]);
+          }
+          sU[yp * Mg + z] = acc[j] + a;
+        }
+      }
       __syncthreads();
-      ymode<T, false>(sT, P, Mg, Q, nullptr, nullptr);                   // Q = P x2 T
-      if (bx.periodic) ymode<T, true>(sW, P, Mg, nullptr, E, C);         // E += P x2 wD
-      __syncthreads();
-      xmode_acc<T>(sW, Q, Mg, E, C);                                     // E += Q x1 wD
+      // E[y'][z'] += w_s sum_z U[y'][z] T[z][z']   (Kahan over the item's nodes)
+      const T ws = (T)bx.w64[s];
+      for (int blk = threadIdx.x; blk < Mg * cb; blk += blockDim.x) {
+        const int yp = blk / cb, z0 = (blk % cb) * 4;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int z = 0; z < Mg; ++z) {
+          const T uv = sU[yp * Mg + z];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (z0 + j < Mg) acc[j] += uv * sT[z * Mg + z0 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (z0 + j < Mg) kahan_add(sE, sC, yp * Mg + z0 + j, ws * acc[j]);
+      }
       __syncthreads();
     }
+    // I x I x D term (periodic, once per slab): E[y][z'] += sum_{z on the z line at (x, y)}
+    // Dbar[z'][z]
     if (bx.periodic && item.g == 0) {
-      for (int i = threadIdx.x; i < M2; i += blockDim.x) sD[i] = bx.Db[i];
+      for (int a = threadIdx.x; a < Mg; a += blockDim.x) {
+        double acc = 0.0;
+        CD[a * (Mg + 1)] = 0.0;
+        for (int k = 0; k < Mg; ++k) {
+          acc += bx.Db64[a * Mg + k];
+          CD[a * (Mg + 1) + k + 1] = acc;
+        }
+      }
       __syncthreads();
-      zmode_occ<T, true>(sD, Mg, zr, nullptr, E, C);                    // E += O x3 Dbar
+      for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+        const int y = i / Mg, zp = i % Mg;
+        const int h = H[x * Mg + y];
+        if (h < 0) continue;
+        kahan_add(sE, sC, i, (T)(CD[zp * (Mg + 1) + R + h + 1] - CD[zp * (Mg + 1) + R - h]));
+      }
       __syncthreads();
     }
-    // publish this item; the last item of the box finalises it
+    // publish the slab partial; the last group of the slab finalises the slab, the last
+    // slab of the box finalises E_x
+    const long long G3 = (long long)mm * Mg;
+    T* P = bx.part + (long long)item.g * G3 + (long long)x * mm;
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) P[i] = sE[i] - sC[i];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(done + item.box, 1) == bx.n_items - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(bx.slab_done + x, 1) == bx.n_groups - 1);
     __syncthreads();
     if (s_last) {
       __threadfence();
       double acc = 0.0;
-      const int R = bx.R;
-      for (long long i = threadIdx.x; i < G3; i += blockDim.x) {
+      const long long base = (long long)x * mm;
+      for (int i = threadIdx.x; i < mm; i += blockDim.x) {
         T sum = T(0), cmp = T(0);
-        for (int g = 0; g < bx.n_items; ++g) {
-          const T* Eg = bx.part + (long long)g * 2 * G3;
-          const T v = __ldcg(Eg + i) - __ldcg(Eg + G3 + i);
-          const T y = v - cmp;
-          const T t = sum + y;
-          cmp = (t - sum) - y;
+        for (int g = 0; g < bx.n_groups; ++g) {
+          const T v = __ldcg(bx.part + (long long)g * G3 + base + i);
+          const T yv = v - cmp;
+          const T t = sum + yv;
+          cmp = (t - sum) - yv;
           sum = t;
         }
-        const int x = (int)(i / M2) - R, y = (int)((i / Mg) % Mg) - R, z = (int)(i % Mg) - R;
-        const int m = x * x + y * y + z * z;
+        const int a = x - R, b = i / Mg - R, c = i % Mg - R;
+        const int m = a * a + b * b + c * c;
         T v = T(0);
         if (m <= R * R) v = (T)(-bx.pref * (double)sum);
-        eps_out[bx.eps_off + i] = v;
+        eps_out[bx.eps_off + base + i] = v;
         if (m <= bx.R_F * bx.R_F) acc += (double)v;
       }
       s_red[threadIdx.x] = acc;
@@ -253,8 +228,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         __syncthreads();
       }
       if (threadIdx.x == 0) {
-        ex_out[2 * bx.ex_idx] = 0.5 * s_red[0];
-        ex_out[2 * bx.ex_idx + 1] = s_red[0];
+        bx.slab_ex[x] = s_red[0];
+        __threadfence();
+        s_last = (atomicAdd(done + item.box, 1) == Mg - 1);
+      }
+      __syncthreads();
+      if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (int k = 0; k < Mg; ++k) tot += __ldcg(bx.slab_ex + k);
+        ex_out[2 * bx.ex_idx] = 0.5 * tot;
+        ex_out[2 * bx.ex_idx + 1] = tot;
       }
     }
     __syncthreads();

@@ -84,7 +84,7 @@ def test_replay_is_deterministic_and_tuner_keeps_results(batch):
     eps = torch.empty((int(B.offsets[-1]),), dtype=torch.float32, device=dev)
     Ex = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
     choice = B.tune(eps, Ex, reps=3)
-    assert choice["ctas_per_sm"] in (1, 2) and choice["oversub"] in (1, 2, 4, 8)
+    assert choice["ctas_per_sm"] in (2, 4, 8) and choice["oversub"] in (1, 2, 4)
     assert choice["ms"] > 0
     e3, x3 = _run(B, dev, torch.float32)
     assert rel_err(e3, e1) < TOL_FP32 and np.max(np.abs(x3 - x1) / np.abs(x1)) < TOL_FP32
