@@ -301,6 +301,9 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and args.mode_products:
         line["mode_products"] = {n: mode_products(n) for n in args.mode_products.split(",")}
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["batched"] = batched()
+        line["large_lookups"] = large_lookups()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -365,6 +368,83 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=False):
             out[prec + "_max_rel_err_vs_oracle"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
         out["oracle_sample"] = f"{len(idx)} seeded basis functions of {Nb}"
     t.free()
+    return out
+
+
+# ---------------------------------------------------------------- batched boxes, large lookups
+def batched(reps=10):
+    """256 boxes (|n| in 4..24, L in 8..30 bohr, R_F 0.4-0.8 of the cutoff, 16..96 nodes) in
+    one persistent graph-captured launch: autotuned launch shape, device time per batch."""
+    import torch
+
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev)
+    boxes = ci.box_params(256)
+    B = cc.Batch(boxes)
+    out = {"boxes": len(boxes), "grid_points": int(B.offsets[-1])}
+    pairs = sum(b_pair(b) for b in boxes)
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64), ("bf16x3", torch.float32)):
+        eps = torch.empty(int(B.offsets[-1]), dtype=dt, device=dev)
+        Ex = torch.empty((B.nbox, 2), dtype=torch.float64, device=dev)
+        choice = B.tune(eps, Ex, reps=3) if prec != "bf16x3" else None
+        B.exchange(eps, Ex, precision=prec)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            B.exchange(eps, Ex, precision=prec)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[prec] = {"ms_per_batch": ms, "boxes_per_s": len(boxes) / (ms * 1e-3),
+                     "pair_evals_per_s": pairs / (ms * 1e-3), "tuned": choice,
+                     "work_items": B.n_items}
+    out["pair_evals_per_batch"] = pairs
+    B.free()
+    return out
+
+
+def b_pair(b):
+    """Pair evaluations an exchange sum of a box replaces: basis size x occupied count."""
+    from coulomb_inputs import sphere_vectors
+    return len(sphere_vectors(b["R"])) * len(sphere_vectors(b["R_F"]))
+
+
+def large_lookups(n=1_000_000_000, reps=3):
+    """1e9 seeded conserving quadruples at |n| <= 63 (1,047,331 planewaves), FP32 tables in
+    shared memory: device time per pass for both table forms."""
+    import torch
+
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev)
+    t = cc.build_tables("periodic", R=63, L=60.0, S=128)
+    q = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    ci.quads_device(63, 0, n, q)
+    vals = torch.empty(n, dtype=torch.float32, device=dev)
+    out = {"quadruples": n, "S_eff": t.info["S_eff"]}
+    peak, _ = _peaks()
+    for lookup in ("collapsed", "separable"):
+        cc.reconstruct_integrals(t, q, vals, lookup=lookup)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            cc.reconstruct_integrals(t, q, vals, lookup=lookup)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = 20.0 * n / (ms * 1e-3) / 1e9
+        out[lookup] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3), "hbm_GBps": gbs,
+                       "hbm_frac": gbs / peak}
+    del q, vals
+    t.free()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -448,6 +528,8 @@ def main():
     ap.add_argument("--mode-products", default="precision,large",
                     help="also time FP32 vs bf16x3 exchange mode products at these single-box "
                          "workloads (precision: |n|<=31, large: |n|<=63); '' to skip")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-boxes and 1e9-lookup sections of the JSON line")
     ap.add_argument("--mp-only", default=None,
                     help="only run the mode-product comparison of this workload, print it")
     ap.add_argument("--traffic", type=float, default=None,

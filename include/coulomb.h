@@ -240,9 +240,13 @@ cc_status cc_batch_create(const cc_box* boxes_host, int nbox, void* stream, cc_b
 cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets_host, int* n_items,
                         size_t* device_bytes);
 
-/* Exchange sums of all boxes: eps_dev (float or double by precision: CC_PREC_FP32 or
- * CC_PREC_FP64) holds every box's grid at its offset, Ex_dev[2 i], Ex_dev[2 i + 1] =
- * E_x^sigma and total of box i.  Stream ordered; calls on one batch must not overlap. */
+/* Exchange sums of all boxes: eps_dev (double for CC_PREC_FP64, float for CC_PREC_FP32
+ * and CC_PREC_BF16X3) holds every box's grid at its offset, Ex_dev[2 i], Ex_dev[2 i + 1] =
+ * E_x^sigma and total of box i.  Stream ordered; calls on one batch must not overlap.
+ * CC_PREC_BF16X3 (periodic boxes only) runs the tensor-core chain for all boxes at once,
+ * a few launches per round of 4 nodes per box, all in the captured graph; its first call
+ * builds the bf16 planes and buffers (synchronous, allocates), later calls allocate
+ * nothing. */
 cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
                             void* stream);
 

@@ -346,12 +346,20 @@ class Batch:
             raise ValueError("batch was freed")
         return self._h
 
-    def exchange(self, eps, Ex, stream=None):
-        """eps: float32 / float64 [offsets[-1]]; Ex: float64 [nbox, 2]."""
+    def exchange(self, eps, Ex, precision=None, stream=None):
+        """eps: float32 / float64 [offsets[-1]]; Ex: float64 [nbox, 2].  precision None
+        follows eps's dtype; "bf16x3" runs the tensor-core form (eps float32)."""
+        import torch
         if eps.numel() < int(self.offsets[-1]) or Ex.numel() < 2 * self.nbox:
             raise ValueError("output too small")
+        if precision is None:
+            prec = _prec_of(eps)
+        else:
+            prec = PRECISIONS[precision]
+            if eps.dtype != (torch.float64 if prec == 0 else torch.float32):
+                raise TypeError("eps dtype does not match the precision")
         _check("cc_batch_exchange", lib().cc_batch_exchange(
-            self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), _stream(stream, eps)))
+            self.handle, prec, _ptr(eps), _ptr(Ex), _stream(stream, eps)))
         return eps, Ex
 
     def set_plan(self, ctas_per_sm=4, oversub=2):

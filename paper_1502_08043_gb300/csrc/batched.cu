@@ -222,6 +222,7 @@ struct cc_batch_s {
   };
   std::vector<Graph> graphs;
   int device = 0;
+  void* mixed = nullptr;  // tensor-core form (periodic boxes), built on first use
 };
 
 using namespace cc;
@@ -298,8 +299,15 @@ extern "C" cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub)
 extern "C" cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
                                        void* stream) {
   if (!b || !eps_dev || !Ex_dev) return CC_ERR_ARG;
-  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
+  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64 && precision != CC_PREC_BF16X3)
+    return CC_ERR_NOTSUPP;
   cudaStream_t st = as_stream(stream);
+  if (precision == CC_PREC_BF16X3 && !b->mixed) {
+    std::vector<int> rf;
+    std::vector<long long> off(b->eps_off.begin(), b->eps_off.end() - 1);
+    for (const cc_box& bx : b->spec) rf.push_back(bx.R_F);
+    CC_TRY(mixed_batch_create(b->tabs, rf, off, &b->mixed));
+  }
   for (auto& g : b->graphs)
     if (g.prec == precision && g.eps == eps_dev && g.Ex == Ex_dev) {
       CC_CUDA(cudaGraphLaunch(g.exec, st));
@@ -312,9 +320,9 @@ extern "C" cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev,
   cc_status s = CC_OK;
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = CC_ERR_CUDA;
   if (s == CC_OK) {
-    s = precision == CC_PREC_FP32
-            ? plan_launch<float>(b->plan, 0, (float*)eps_dev, Ex_dev, cap)
-            : plan_launch<double>(b->plan, 0, (double*)eps_dev, Ex_dev, cap);
+    s = precision == CC_PREC_FP32    ? plan_launch<float>(b->plan, 0, (float*)eps_dev, Ex_dev, cap)
+        : precision == CC_PREC_FP64  ? plan_launch<double>(b->plan, 0, (double*)eps_dev, Ex_dev, cap)
+                                     : mixed_batch_run(b->mixed, (float*)eps_dev, Ex_dev, cap);
     cudaError_t e = cudaStreamEndCapture(cap, &graph);
     if (s == CC_OK && e != cudaSuccess) {
       set_last_error("cudaStreamEndCapture", e);
@@ -390,6 +398,7 @@ extern "C" cc_status cc_batch_free(cc_batch b) {
   if (!b) return CC_ERR_ARG;
   batch_drop_graphs(b);
   plan_free(&b->plan);
+  mixed_batch_free(b->mixed);
   for (cc_tables t : b->tabs) cc_tables_free(t);
   delete b;
   return CC_OK;

@@ -104,6 +104,10 @@ cc_status fused_single_exchange(cc_tables t, int R_F, int precision, void* eps, 
 cc_status workspace_alloc(cc_tables t);
 void workspace_free(cc_tables t);
 // umma.cu
+cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
+                             const std::vector<long long>& eps_off, void** out);
+cc_status mixed_batch_run(void* mb, float* eps, double* Ex, cudaStream_t st);
+void mixed_batch_free(void* mb);
 cc_status mixed_workspace_alloc(cc_tables t);
 void mixed_workspace_free(cc_tables t);
 cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,

@@ -176,8 +176,25 @@ struct TcArgs {
   long long o_base, o_sb;              // element offset of batch b
   long long s_mhi, s_mlo, s_n;         // element (m, n) -> (m / Np) s_mhi + (m % Np) s_mlo + n s_n
   const float* scale;   // per-batch factor applied before the store (nullptr: 1)
+  // optional per-batch table (overrides the affine forms above): for batch b,
+  // btab[4b] = A row base, btab[4b+1] = B row base, btab[4b+2] = output element offset,
+  // btab[4b+3] = number of stacked products J_b
+  const long long* btab;
   int* err;
 };
+
+struct TcBatch {
+  long long abase, bbase, obase;
+  int J;
+};
+
+__device__ __forceinline__ TcBatch tc_batch(const TcArgs& g, int b) {
+  if (g.btab) {
+    const long long* e = g.btab + 4 * b;
+    return {e[0], e[1], e[2], (int)e[3]};
+  }
+  return {g.a_base + b * g.a_sb, g.b_base + b * g.b_sb, g.o_base + b * g.o_sb, g.J};
+}
 
 constexpr int kStages = 3;
 constexpr int kTileM = 128;
@@ -244,7 +261,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int iters = g.J * g.nk;
 
   if (warp == 4) {
     if (lane == 0) {
@@ -253,6 +269,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t n = 0;
       for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
         const int b = t / g.m_tiles;
+        const TcBatch bt = tc_batch(g, b);
+        const int iters = bt.J * g.nk;
         const long long m0 = (long long)(t % g.m_tiles) * kTileM;
         for (int it = 0; it < iters; ++it, ++n) {
           const int s = (int)(n % kStages);
@@ -262,8 +280,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           const int j = it / g.nk, kb = it % g.nk;
-          const int arow = (int)(g.a_base + b * g.a_sb + j * g.a_sj + m0);
-          const int brow = (int)(g.b_base + b * g.b_sb + j * g.b_sj);
+          const int arow = (int)(bt.abase + j * g.a_sj + m0);
+          const int brow = (int)(bt.bbase + j * g.b_sj);
           const uint32_t st = base + s * L::kStage;
           mbar_expect_tx(full(s), bytes);
           tma_load_2d(st, &mA, kb * kKB, arow, full(s));
@@ -288,6 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem + acc * (uint32_t)NP;
+        const int iters = tc_batch(g, t / g.m_tiles).J * g.nk;
         bool ok = true;
         for (int it = 0; it < iters; ++it, ++n) {
           const int s = (int)(n % kStages);
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int b = t / g.m_tiles;
       const long long m = (long long)(t % g.m_tiles) * kTileM + warp * 32 + lane;
       const long long mh = m / NP, ml = m % NP;
-      const long long row_off = g.o_base + b * g.o_sb + mh * g.s_mhi + ml * g.s_mlo;
+      const long long row_off = tc_batch(g, b).obase + mh * g.s_mhi + ml * g.s_mlo;
       const float sc = g.scale ? g.scale[b] : 1.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < NP; c0 += 32) {
@@ -783,3 +802,258 @@ extern "C" cc_status cc_mixed_status(cc_tables t, int* code_host, int clear) {
   if (clear) CC_CUDA(cudaMemset(w->err, 0, sizeof(int) * 2));
   return *code_host ? CC_ERR_TIMEOUT : CC_OK;
 }
+
+// ------------------------------------------------------------------ batched boxes (bf16x3)
+// The tensor-core form of the batched engine: every box (grid side <= 49, padded to
+// Np = 64) goes through the same step 5 / 1 / 2 / 3 / 4 chain as a single box, but each
+// launch covers all boxes at once through a per-batch table of row bases (TcArgs.btab):
+// rounds of C nodes per box, the boxes' planes concatenated in shared arrays.  The whole
+// sequence is enqueued on one stream and captured in one CUDA graph by the caller.
+namespace cc {
+
+struct MxBatchImpl {
+  int nbox = 0, C = 4, rounds = 0;
+  std::vector<int> S;
+  int* R_dev = nullptr;
+  int* RF_dev = nullptr;
+  double* pref_dev = nullptr;
+  long long* eps_off_dev = nullptr;
+  MxPlanes P;  // X1, TT, WTD, DB concatenated over boxes; O, OT [nbox][Np^3]; R, W slots
+  float* E = nullptr;
+  int* err = nullptr;
+  long long* t5 = nullptr;
+  std::vector<long long*> t123[3], t4;
+  std::vector<int> n123, n4;
+  std::vector<void*> allocs;
+};
+
+__global__ void k_mxb_occ(int nbox, const int* R, const int* RF, __nv_bfloat16* O,
+                          __nv_bfloat16* OT) {
+  constexpr int Np = 64;
+  const long long per = (long long)Np * Np * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per * nbox;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per);
+    const long long j = i % per;
+    const int x = (int)(j / (Np * Np)), y = (int)((j / Np) % Np), z = (int)(j % Np);
+    const int Rb = R[b], Mg = 2 * Rb + 1;
+    float v = 0.0f;
+    if (x < Mg && y < Mg && z < Mg) {
+      const int a = x - Rb, bb = y - Rb, c = z - Rb;
+      v = (a * a + bb * bb + c * c <= RF[b] * RF[b]) ? 1.0f : 0.0f;
+    }
+    O[i] = __float2bfloat16_rn(v);
+    OT[b * per + ((long long)y * Np + z) * Np + x] = __float2bfloat16_rn(v);
+  }
+}
+
+// one CTA per box: eps = -pref E on the basis sphere, E_x in FP64
+__global__ void k_mxb_finalize(const int* R, const int* RF, const double* pref,
+                               const long long* eps_off, const float* E, float* eps,
+                               double* Ex) {
+  constexpr int Np = 64;
+  const int b = blockIdx.x;
+  const int Rb = R[b], Mg = 2 * Rb + 1;
+  const long long G3 = (long long)Mg * Mg * Mg;
+  const float* Eb = E + (long long)b * Np * Np * Np;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < G3; i += blockDim.x) {
+    const int x = (int)(i / ((long long)Mg * Mg)), y = (int)((i / Mg) % Mg), z = (int)(i % Mg);
+    const int a = x - Rb, bb = y - Rb, c = z - Rb;
+    const int m = a * a + bb * bb + c * c;
+    float v = 0.0f;
+    if (m <= Rb * Rb) v = (float)(-pref[b] * (double)Eb[((long long)x * Np + y) * Np + z]);
+    eps[eps_off[b] + i] = v;
+    if (m <= RF[b] * RF[b]) acc += (double)v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Ex[2 * b] = 0.5 * red[0];
+    Ex[2 * b + 1] = red[0];
+  }
+}
+
+static cc_status mxb_alloc(MxBatchImpl* m, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    set_last_error("cudaMalloc(mixed batch)", e);
+    return CC_ERR_ALLOC;
+  }
+  m->allocs.push_back(*p);
+  return CC_OK;
+}
+
+template <typename V>
+static cc_status mxb_upload(MxBatchImpl* m, V** dst, const std::vector<V>& src) {
+  CC_TRY(mxb_alloc(m, (void**)dst, sizeof(V) * src.size()));
+  CC_CUDA(cudaMemcpy(*dst, src.data(), sizeof(V) * src.size(), cudaMemcpyHostToDevice));
+  return CC_OK;
+}
+
+void mixed_batch_free(void* p) {
+  MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
+  if (!m) return;
+  for (void* q : m->allocs) cudaFree(q);
+  delete m;
+}
+
+cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
+                             const std::vector<long long>& eps_off, void** out) {
+  *out = nullptr;
+  CC_TRY(get_encoder());
+  constexpr int Np = 64;
+  const long long NN = (long long)Np * Np, VOL = NN * Np;
+  MxBatchImpl* m = new (std::nothrow) MxBatchImpl();
+  if (!m) return CC_ERR_ALLOC;
+  m->nbox = (int)tabs.size();
+  const int nb = m->nbox;
+  cc_status s = CC_OK;
+  std::vector<int> Rv(nb);
+  std::vector<double> pref(nb);
+  std::vector<long long> off_x1(nb), off_wtd(nb);
+  long long rows_x1 = 0;
+  int max_s = 0;
+  for (int b = 0; b < nb; ++b) {
+    const cc_tables t = tabs[b];
+    if (t->Mg > Np || t->p.kernel != CC_KERNEL_PERIODIC) s = CC_ERR_NOTSUPP;
+    Rv[b] = t->p.R;
+    pref[b] = t->pref;
+    m->S.push_back(t->S_eff);
+    off_x1[b] = rows_x1;
+    off_wtd[b] = 2 * rows_x1;
+    rows_x1 += (long long)t->S_eff * Np;
+    max_s = std::max(max_s, t->S_eff);
+  }
+  const int C = m->C;
+  m->rounds = (max_s + C - 1) / C;
+  const size_t e2 = 2;
+  MxPlanes& P = m->P;
+  for (int h = 0; h < 2 && s == CC_OK; ++h) {
+    if (s == CC_OK) s = mxb_alloc(m, &P.X1[h], rows_x1 * Np * e2);
+    if (s == CC_OK) s = mxb_alloc(m, &P.TT[h], rows_x1 * Np * e2);
+    if (s == CC_OK) s = mxb_alloc(m, &P.WTD[h], 2 * rows_x1 * Np * e2);
+    if (s == CC_OK) s = mxb_alloc(m, &P.DB[h], (size_t)nb * NN * e2);
+    if (s == CC_OK) s = mxb_alloc(m, &P.R[h], (size_t)nb * C * VOL * e2);
+    if (s == CC_OK) s = mxb_alloc(m, &P.W[h], (size_t)nb * C * 2 * VOL * e2);
+  }
+  if (s == CC_OK) s = mxb_alloc(m, &P.O, (size_t)nb * VOL * e2);
+  if (s == CC_OK) s = mxb_alloc(m, &P.OT, (size_t)nb * VOL * e2);
+  if (s == CC_OK) s = mxb_alloc(m, (void**)&m->E, (size_t)nb * VOL * sizeof(float));
+  if (s == CC_OK) s = mxb_alloc(m, (void**)&m->err, sizeof(int) * 2);
+  if (s == CC_OK) s = make_map(&P.mO, P.O, nb * NN, Np, kTileM, true);
+  if (s == CC_OK) s = make_map(&P.mOT, P.OT, nb * NN, Np, kTileM, true);
+  for (int h = 0; h < 2 && s == CC_OK; ++h) {
+    if (s == CC_OK) s = make_map(&P.mR[h], P.R[h], (long long)nb * C * NN, Np, kTileM, true);
+    if (s == CC_OK) s = make_map(&P.mW[h], P.W[h], (long long)nb * C * 2 * NN, Np, kTileM, true);
+    if (s == CC_OK) s = make_map(&P.mX1[h], P.X1[h], rows_x1, Np, Np, true);
+    if (s == CC_OK) s = make_map(&P.mTT[h], P.TT[h], rows_x1, Np, Np, true);
+    if (s == CC_OK) s = make_map(&P.mWTD[h], P.WTD[h], 2 * rows_x1, Np, Np, true);
+    if (s == CC_OK) s = make_map(&P.mDB[h], P.DB[h], (long long)nb * Np, Np, Np, true);
+  }
+  // Toeplitz planes of every box, written at the box's row offsets
+  for (int b = 0; b < nb && s == CC_OK; ++b) {
+    const cc_tables t = tabs[b];
+    using E = __nv_bfloat16;
+    k_mx_tables<E><<<256, 256>>>(t->d.Tm64, t->d.WDm64, t->d.w64, t->S_eff, t->Mg, Np, 1,
+                                 nullptr, (E*)P.X1[0] + off_x1[b] * Np,
+                                 (E*)P.X1[1] + off_x1[b] * Np, (E*)P.TT[0] + off_x1[b] * Np,
+                                 (E*)P.TT[1] + off_x1[b] * Np, (E*)P.WTD[0] + off_wtd[b] * Np,
+                                 (E*)P.WTD[1] + off_wtd[b] * Np);
+    k_mx_dbar<E><<<(Np * Np + 255) / 256, 256>>>(t->d.Dbar64, t->Mg, Np,
+                                                  (E*)P.DB[0] + (long long)b * NN,
+                                                  (E*)P.DB[1] + (long long)b * NN);
+    if (cudaGetLastError() != cudaSuccess) s = CC_ERR_CUDA;
+  }
+  // per-step tables
+  std::vector<long long> t5;
+  for (int b = 0; b < nb; ++b) t5.insert(t5.end(), {b * NN, (long long)b * Np, b * VOL, 1});
+  if (s == CC_OK) s = mxb_upload(m, &m->t5, t5);
+  for (int r = 0; r < m->rounds && s == CC_OK; ++r) {
+    std::vector<long long> a1, a2, a3, a4;
+    for (int b = 0; b < nb; ++b) {
+      const int s0 = r * C;
+      const int cnt = std::min(C, m->S[b] - s0);
+      if (cnt <= 0) continue;
+      for (int c = 0; c < cnt; ++c) {
+        const long long slot = (long long)b * C + c, node = s0 + c;
+        a1.insert(a1.end(), {b * NN, off_x1[b] + node * Np, slot * VOL, 1});
+        a2.insert(a2.end(), {slot * NN, off_x1[b] + node * Np, slot * 2 * VOL, 1});
+        a3.insert(a3.end(), {b * NN, off_x1[b] + node * Np, slot * 2 * VOL + VOL, 1});
+      }
+      a4.insert(a4.end(), {(long long)b * C * 2 * NN, off_wtd[b] + 2LL * s0 * Np, b * VOL,
+                           2LL * cnt});
+    }
+    long long* d[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (s == CC_OK) s = mxb_upload(m, &d[0], a1);
+    if (s == CC_OK) s = mxb_upload(m, &d[1], a2);
+    if (s == CC_OK) s = mxb_upload(m, &d[2], a3);
+    if (s == CC_OK) s = mxb_upload(m, &d[3], a4);
+    m->t123[0].push_back(d[0]);
+    m->t123[1].push_back(d[1]);
+    m->t123[2].push_back(d[2]);
+    m->t4.push_back(d[3]);
+    m->n123.push_back((int)(a1.size() / 4));
+    m->n4.push_back((int)(a4.size() / 4));
+  }
+  if (s == CC_OK) s = mxb_upload(m, &m->R_dev, Rv);
+  if (s == CC_OK) s = mxb_upload(m, &m->RF_dev, R_F);
+  if (s == CC_OK) s = mxb_upload(m, &m->pref_dev, pref);
+  if (s == CC_OK) s = mxb_upload(m, &m->eps_off_dev, eps_off);
+  if (s == CC_OK && cudaMemset(m->err, 0, sizeof(int) * 2) != cudaSuccess) s = CC_ERR_CUDA;
+  if (s == CC_OK && cudaDeviceSynchronize() != cudaSuccess) s = CC_ERR_CUDA;
+  if (s != CC_OK) {
+    mixed_batch_free(m);
+    return s;
+  }
+  *out = m;
+  return CC_OK;
+}
+
+cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
+  MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
+  if (!m) return CC_ERR_NOTSUPP;
+  constexpr int Np = 64;
+  using E = __nv_bfloat16;
+  const long long NN = (long long)Np * Np;
+  const int m_tiles = (int)(NN / kTileM);
+  MxPlanes& P = m->P;
+  k_mxb_occ<<<1216, 256, 0, st>>>(m->nbox, m->R_dev, m->RF_dev, (E*)P.O, (E*)P.OT);
+  CC_CUDA(cudaGetLastError());
+  {  // step 5: E_b = O_b x3 Dbar_b
+    TcArgs g{};
+    g.nk = 1; g.J = 1; g.a_lo = 0; g.b_lo = 1;
+    g.out_split = 0; g.beta = 0; g.out = m->E;
+    g.s_mhi = NN; g.s_mlo = Np; g.s_n = 1;
+    g.btab = m->t5; g.err = m->err;
+    CC_TRY((launch_tc<Np, E>(P.mO, P.mO, P.mDB[0], P.mDB[1], g, m_tiles, m->nbox, st)));
+  }
+  for (int r = 0; r < m->rounds; ++r) {
+    TcArgs g{};
+    g.nk = 1; g.J = 1; g.err = m->err;
+    g.a_lo = 0; g.b_lo = 1; g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
+    g.s_mhi = Np; g.s_mlo = 1; g.s_n = NN; g.btab = m->t123[0][r];
+    CC_TRY((launch_tc<Np, E>(P.mOT, P.mOT, P.mX1[0], P.mX1[1], g, m_tiles, m->n123[r], st)));
+    g.a_lo = 1; g.out = P.W[0]; g.out_lo = P.W[1];
+    g.s_mhi = NN; g.s_mlo = 1; g.s_n = Np; g.btab = m->t123[1][r];
+    CC_TRY((launch_tc<Np, E>(P.mR[0], P.mR[1], P.mTT[0], P.mTT[1], g, m_tiles, m->n123[r], st)));
+    g.a_lo = 0; g.btab = m->t123[2][r];
+    CC_TRY((launch_tc<Np, E>(P.mO, P.mO, P.mTT[0], P.mTT[1], g, m_tiles, m->n123[r], st)));
+    TcArgs g4{};
+    g4.nk = 1; g4.J = 1; g4.a_sj = NN; g4.b_sj = Np; g4.a_lo = 1; g4.b_lo = 1;
+    g4.out_split = 0; g4.beta = 1; g4.out = m->E;
+    g4.s_mhi = NN; g4.s_mlo = 1; g4.s_n = Np; g4.btab = m->t4[r]; g4.err = m->err;
+    CC_TRY((launch_tc<Np, E>(P.mW[0], P.mW[1], P.mWTD[0], P.mWTD[1], g4, m_tiles, m->n4[r], st)));
+  }
+  k_mxb_finalize<<<m->nbox, 256, 0, st>>>(m->R_dev, m->RF_dev, m->pref_dev, m->eps_off_dev, m->E,
+                                          eps, Ex);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+}  // namespace cc

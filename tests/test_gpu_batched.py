@@ -99,3 +99,33 @@ def test_batch_argument_errors():
     with pytest.raises(cc.CoulombError) as e:
         cc.Batch([{"R": 6, "L": 10.0, "R_F": 7, "S": 32}])     # R_F > R
     assert e.value.status == 2
+
+
+def test_mixed_batch_all_boxes(batch):
+    """The tensor-core (bf16x3) form of the batched engine: every box within 1e-4."""
+    import torch
+    dev, boxes, B = batch
+    eps = torch.full((int(B.offsets[-1]),), float("nan"), dtype=torch.float32, device=dev)
+    Ex = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
+    B.exchange(eps, Ex, precision="bf16x3")
+    torch.cuda.synchronize()
+    e = eps.cpu().numpy().astype(np.float64)
+    x = Ex.cpu().numpy()
+    assert not np.isnan(e).any()
+    for i, b in enumerate(boxes):
+        a, w = _nodes(b)
+        C = ox.difference_histogram(b["R_F"], "fft")
+        ref = ox.Ex_separable_periodic(b["R_F"], b["L"], a, w, C)
+        assert abs(x[i, 0] - ref) < 1e-4 * abs(ref), (i, b)
+    for i in (0, 17, 101, 255):
+        b = boxes[i]
+        a, w = _nodes(b)
+        _, vals = _box_eps(B, e, i, b["R"])
+        assert rel_err(vals, ox.eps_separable(b["R"], b["R_F"], b["L"], a, w)) < 1e-4
+    # replay through the captured graph gives the same bits
+    eps2 = torch.empty_like(eps)
+    Ex2 = torch.zeros_like(Ex)
+    B.exchange(eps2, Ex2, precision="bf16x3")
+    B.exchange(eps2, Ex2, precision="bf16x3")
+    torch.cuda.synchronize()
+    assert torch.equal(eps2, eps) and torch.equal(Ex2, Ex)
