@@ -270,12 +270,17 @@ def run_gpu(args):
                "ms_per_step": ems}
 
     peak, peak_kind = _peaks()
+    # ncu DRAM bytes of one k_col launch: 320.1 MB read + 50.2 MB written for 2e7
+    # quadruples (profiles/k_col_paper_scale.md), scaled by the quadruples of this launch
+    if args.traffic is None and lookup == "collapsed":
+        args.traffic = 370.3e6 * n / 2e7
     if lookup == "collapsed":
         algo_bytes = 20.0 * n          # 16 B quadruple in, 4 B value out
         achieved = algo_bytes / (k_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_col",
-                    "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind}
+                    "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind,
+                    "traffic_source": "ncu dram bytes of a 2e7-quadruple launch, scaled"}
     else:
         algo_bytes = 20.0 * n
         achieved = algo_bytes / (k_ms * 1e-3) / 1e9
@@ -426,23 +431,28 @@ def large_lookups(n=1_000_000_000, reps=3):
     q = torch.empty((n, 4), dtype=torch.int32, device=dev)
     ci.quads_device(63, 0, n, q)
     vals = torch.empty(n, dtype=torch.float32, device=dev)
-    out = {"quadruples": n, "S_eff": t.info["S_eff"]}
+    out = {"quadruples": n, "S_eff": t.info["S_eff"],
+           "note": "ids: every quadruple gathers 4 basis vectors from the 4.2 MB basis table "
+                   "(L2); vec: the quadruple carries its four int8x4 vectors"}
     peak, _ = _peaks()
-    for lookup in ("collapsed", "separable"):
-        cc.reconstruct_integrals(t, q, vals, lookup=lookup)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(st)
-        for _ in range(reps):
-            cc.reconstruct_integrals(t, q, vals, lookup=lookup)
-        b.record(st)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / reps
-        gbs = 20.0 * n / (ms * 1e-3) / 1e9
-        out[lookup] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3), "hbm_GBps": gbs,
-                       "hbm_frac": gbs / peak}
-    del q, vals
+    # the same quadruples in vector form (16 B each as well)
+    vecs = torch.from_numpy(cc.basis(63)).to(dev)[q.long().view(-1)].view(n, 4, 4)
+    for fmt, qq in (("ids", q), ("vec", vecs)):
+        for lookup in ("collapsed", "separable"):
+            cc.reconstruct_integrals(t, qq, vals, lookup=lookup)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            for _ in range(reps):
+                cc.reconstruct_integrals(t, qq, vals, lookup=lookup)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            gbs = 20.0 * n / (ms * 1e-3) / 1e9
+            out[f"{fmt}_{lookup}"] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3),
+                                      "hbm_GBps": gbs, "hbm_frac": gbs / peak}
+    del q, vals, vecs
     t.free()
     torch.cuda.empty_cache()
     return out
