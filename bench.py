@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 R, L, S, R_F = 13, 20.0, 64, 8
 N_QUADS = 100_000_000
+TRAFFIC_VEC_2E7 = None  # ncu DRAM bytes of a 2e7-quadruple vector-form k_col launch
 METRIC = "pair-Coulomb evals/s and integrals/s on 1 GB300, mixed vs FP32 at <=1e-4 rel err"
 UNIT = "Coulomb evals/s"
 WORKLOAD = ("paper scale: |n|<=13 (9171 planewaves), L=20 bohr, 64 nodes, R_F=8 (2109 occ); "
@@ -118,8 +119,13 @@ def run_gpu(args):
     Mocc = 2109
     n = args.quads
     # every rank owns its own slice of the quadruple stream (weak scaling, no collective)
-    q = torch.empty((n, 4), dtype=torch.int32, device=dev)
-    ci.quads_device(R, rank * n, n, q)
+    qid = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    ci.quads_device(R, rank * n, n, qid)
+    # the step consumes the quadruples in their int8x4 vector form (16 B each, the four
+    # planewave index vectors); the id form (int32 basis ids) is timed in the breakdown
+    q = torch.from_numpy(cc.basis(R)).to(dev)[qid.long().view(-1)].view(n, 4, 4)
+    if args.quad_format == "ids":
+        q = qid
     vals = torch.empty(n, dtype=torch.float32, device=dev)
     pairs = torch.empty((Nb, Nb), dtype=torch.float32, device=dev)
     eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
@@ -194,6 +200,9 @@ def run_gpu(args):
     other = "separable" if lookup == "collapsed" else "collapsed"
     parts[f"reconstruct_{other}_ms"] = time_it(
         lambda: cc.reconstruct_integrals(t, q, vals, lookup=other))
+    qo = qid if args.quad_format == "vec" else q
+    parts[f"reconstruct_{lookup}_{'ids' if args.quad_format == 'vec' else 'vec'}_ms"] = time_it(
+        lambda: cc.reconstruct_integrals(t, qo, vals, lookup=lookup))
     if args.mixed:
         parts["exchange_bf16x3_ms"] = time_it(
             lambda: cc.exchange_sums(t, R_F, eps_mx, Ex_mx, precision="bf16x3"))
@@ -204,7 +213,7 @@ def run_gpu(args):
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
-        hq = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+        hq = torch.empty(tuple(q.shape), dtype=q.dtype, pin_memory=True)
         hq.copy_(q.cpu())
         hv = torch.empty(n, dtype=torch.float32, pin_memory=True)
         hp = torch.empty((Nb, Nb), dtype=torch.float32, pin_memory=True)
@@ -270,15 +279,18 @@ def run_gpu(args):
                "ms_per_step": ems}
 
     peak, peak_kind = _peaks()
-    # ncu DRAM bytes of one k_col launch: 320.1 MB read + 50.2 MB written for 2e7
-    # quadruples (profiles/k_col_paper_scale.md), scaled by the quadruples of this launch
+    # ncu DRAM bytes of one k_col launch for 2e7 quadruples, scaled by the quadruples of
+    # this launch: id form 320.1 MB read + 50.2 MB written (profiles/k_col_paper_scale.md),
+    # vector form profiles/k_col_vec_paper_scale.md
     if args.traffic is None and lookup == "collapsed":
-        args.traffic = 370.3e6 * n / 2e7
+        args.traffic = {"ids": 370.3e6, "vec": TRAFFIC_VEC_2E7}[args.quad_format]
+        args.traffic = None if args.traffic is None else args.traffic * n / 2e7
     if lookup == "collapsed":
         algo_bytes = 20.0 * n          # 16 B quadruple in, 4 B value out
         achieved = algo_bytes / (k_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_col",
+                    "frac": achieved / peak, "traffic": args.traffic,
+                    "kernel": f"k_col ({args.quad_format} quadruples)",
                     "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind,
                     "traffic_source": "ncu dram bytes of a 2e7-quadruple launch, scaled"}
     else:
@@ -296,7 +308,8 @@ def run_gpu(args):
         "data": "synthetic (seeded SplitMix64 quadruples; shell-closed Fermi sphere)",
         "config": {"workload": WORKLOAD, "R": R, "L_bohr": L, "S": S,
                    "S_eff": t.info["S_eff"], "R_F": R_F, "Nb": Nb, "Mocc": Mocc,
-                   "quadruples": n, "pairs": Nb * Nb, "lookup": lookup,
+                   "quadruples": n, "quad_format": args.quad_format, "pairs": Nb * Nb,
+                   "lookup": lookup,
                    "evals_per_step": evals, "l2_policy": "inputs larger than L2 (1.6 GB)",
                    "parallelism": f"replicas x{world} (independent quadruple slices)"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": n_launch * args.steps,
@@ -529,6 +542,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lookup", default="collapsed", choices=["collapsed", "separable"])
     ap.add_argument("--quads", type=int, default=N_QUADS)
+    ap.add_argument("--quad-format", default="vec", choices=["vec", "ids"])
     ap.add_argument("--mixed", action="store_true")
     ap.add_argument("--mixed-launches", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")

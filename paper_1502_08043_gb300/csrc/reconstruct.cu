@@ -257,10 +257,8 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
   if ((threadIdx.x & 31) == 0) flush_counts(counters, c0, c1, c2);
 }
 
-// all-pairs, collapsed: out[r][j] = V_m[|n_j - n_{row0+r}|^2].  Each thread writes VEC
-// consecutive outputs of a row with one 16-byte store (rows start at arbitrary element
-// offsets, so the unaligned head and tail of each row are written element by element).
-template <typename T, int VEC>
+// all-pairs, collapsed: out[r][j] = V_m[|n_j - n_{row0+r}|^2]
+template <typename T>
 __global__ void __launch_bounds__(256) k_pair_col(const char4* __restrict__ gbasis, int Nb,
                                                   int64_t row0, int64_t nrows,
                                                   const T* __restrict__ gVm, int m_max,
@@ -276,36 +274,13 @@ __global__ void __launch_bounds__(256) k_pair_col(const char4* __restrict__ gbas
     basis = sb;
   }
   __syncthreads();
-  auto value = [&](char4 a, int j) {
-    const char4 b = basis[j];
-    const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-    return Vm[dx * dx + dy * dy + dz * dz];
-  };
   for (int64_t r = blockIdx.y; r < nrows; r += gridDim.y) {
     const char4 a = gbasis[row0 + r];
     T* orow = out + r * (int64_t)Nb;
-    int head = 0;
-    if (VEC > 1) {
-      const uintptr_t mis = (reinterpret_cast<uintptr_t>(orow) / sizeof(T)) % VEC;
-      head = (int)((VEC - mis) % VEC);
-      if (head > Nb) head = Nb;
-    }
-    const int nvec = (Nb - head) / VEC;
-    const int tail0 = head + nvec * VEC;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-    if (tid < head) __stcs(orow + tid, value(a, tid));
-    if (tid < Nb - tail0) __stcs(orow + tail0 + tid, value(a, tail0 + tid));
-    for (int c = tid; c < nvec; c += nthr) {
-      const int j = head + c * VEC;
-      if constexpr (VEC == 4) {
-        float4 v = make_float4(value(a, j), value(a, j + 1), value(a, j + 2), value(a, j + 3));
-        __stcs(reinterpret_cast<float4*>(orow + j), v);
-      } else if constexpr (VEC == 2) {
-        double2 v = make_double2(value(a, j), value(a, j + 1));
-        __stcs(reinterpret_cast<double2*>(orow + j), v);
-      } else {
-        __stcs(orow + j, value(a, j));
-      }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Nb; j += gridDim.x * blockDim.x) {
+      const char4 b = basis[j];
+      const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+      __stcs(orow + j, Vm[dx * dx + dy * dy + dz * dz]);
     }
   }
 }
@@ -420,12 +395,11 @@ static cc_status pairs_t(cc_tables t, int64_t row0, int64_t nrows, int lookup, T
     if (tb > kSmemCap) return CC_ERR_RANGE;
     int basis_smem = tb + (size_t)t->Nb * 4 <= 48 * 1024 ? t->Nb : 0;
     const size_t smem = tb + (size_t)basis_smem * 4;
-    constexpr int V = 16 / sizeof(T);
-    auto kern = k_pair_col<T, V>;
+    auto kern = k_pair_col<T>;
     CC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-    const int bx = (t->Nb / V + 255) / 256 < 8 ? (t->Nb / V + 255) / 256 + 1 : 8;
+    const int bx = (t->Nb + 255) / 256 < 8 ? (t->Nb + 255) / 256 : 8;
     int64_t by = ((int64_t)per_sm * num_sms() + bx - 1) / bx;
     if (by > nrows) by = nrows;
     if (by > 65535) by = 65535;
