@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 R, L, S, R_F = 13, 20.0, 64, 8
 N_QUADS = 100_000_000
-TRAFFIC_VEC_2E7 = None  # ncu DRAM bytes of a 2e7-quadruple vector-form k_col launch
+TRAFFIC_VEC_2E7 = 370.2e6  # ncu DRAM bytes of a 2e7-quadruple vector-form k_col launch
 METRIC = "pair-Coulomb evals/s and integrals/s on 1 GB300, mixed vs FP32 at <=1e-4 rel err"
 UNIT = "Coulomb evals/s"
 WORKLOAD = ("paper scale: |n|<=13 (9171 planewaves), L=20 bohr, 64 nodes, R_F=8 (2109 occ); "
@@ -106,6 +106,7 @@ def run_gpu(args):
 
     import coulomb_inputs as ci
     import paper_1502_08043_gb300 as cc
+    from paper_1502_08043_gb300 import replicas
 
     rank, world, local = _env_rank()
     if world > 1:
@@ -120,7 +121,8 @@ def run_gpu(args):
     n = args.quads
     # every rank owns its own slice of the quadruple stream (weak scaling, no collective)
     qid = torch.empty((n, 4), dtype=torch.int32, device=dev)
-    ci.quads_device(R, rank * n, n, qid)
+    first, _ = replicas.quad_slice(rank, n)
+    ci.quads_device(R, first, n, qid)
     # the step consumes the quadruples in their int8x4 vector form (16 B each, the four
     # planewave index vectors); the id form (int32 basis ids) is timed in the breakdown
     q = torch.from_numpy(cc.basis(R)).to(dev)[qid.long().view(-1)].view(n, 4, 4)
@@ -175,10 +177,7 @@ def run_gpu(args):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
     k_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    if world > 1:
-        v = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        ms = float(v.item())
+    ms = replicas.max_over_ranks(ms, dev)
 
     # per-part timing (outside the timed region; for the breakdown only)
     def time_it(fn, reps=5):
@@ -208,7 +207,7 @@ def run_gpu(args):
             lambda: cc.exchange_sums(t, R_F, eps_mx, Ex_mx, precision="bf16x3"))
 
     evals = n + Nb * Nb + Nb * Mocc
-    value = world * evals / (ms * 1e-3)
+    value = replicas.job_throughput(evals, world, ms)
 
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -269,11 +268,8 @@ def run_gpu(args):
         b.record(st)
         torch.cuda.synchronize()
         ems = a.elapsed_time(b) / ks
-        if world > 1:
-            v = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(v, op=dist.ReduceOp.MAX)
-            ems = float(v.item())
-        e2e = {"value": world * evals / (ems * 1e-3), "unit": UNIT,
+        ems = replicas.max_over_ranks(ems, dev)
+        e2e = {"value": replicas.job_throughput(evals, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(n * 16),
                "d2h_bytes_per_step": int(n * 4 + Nb * Nb * 4 + Mg ** 3 * 4 + 16),
                "ms_per_step": ems}

@@ -206,11 +206,20 @@ cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, d
 cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_dev, double* Ex_dev,
                                    void* stream);
 
-/* Error word of the tensor-core (mixed precision) exchange path: 0 = fine; 1, 2, 3 = a
- * bounded wait inside the kernel ran out (TMA producer, MMA issuer, epilogue) and the
- * kernel returned without finishing (outputs invalid).  Synchronises; clear != 0 resets
+/* Error word of the tensor-core (mixed precision) exchange path: 0 = fine; 1, 2, 3, 4 = a
+ * bounded wait inside the kernel ran out (TMA producer, MMA issuer on its operands,
+ * epilogue, MMA issuer on a free accumulator), 5 = the stall of cc_test_stall_next_mixed;
+ * the kernel returned without finishing (outputs invalid).  Synchronises; clear != 0 resets
  * it.  Returns CC_ERR_TIMEOUT when the word is nonzero. */
 cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
+
+/* Test hook for the bounded waits (no counterpart in the paper): the next tensor-core
+ * GEMM launch of this process makes its MMA warp wait on a barrier that nothing arrives
+ * at; after 20 ms the wait gives up, the kernel writes error code 5 to the mixed-path
+ * error word (see cc_mixed_status), every role of the CTA stops, TMEM is freed and the
+ * kernel returns.  The results of that exchange call are invalid; the context and
+ * later calls are not affected. */
+cc_status cc_test_stall_next_mixed(void);
 
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
  * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the

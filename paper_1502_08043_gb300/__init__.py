@@ -78,6 +78,7 @@ SIGNATURES = {
     "cc_set_gemm_tiles": (_I, [_I, _I, _I, _I]),
     "cc_mixed_status": (_I, [_P, _P, _I]),
     "cc_exchange_sums_noalloc": (_I, [_P, _I, _P, _P, _P]),
+    "cc_test_stall_next_mixed": (_I, []),
     "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
     "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),
     "cc_batch_exchange": (_I, [_P, _I, _P, _P, _P]),

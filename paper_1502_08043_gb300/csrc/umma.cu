@@ -33,7 +33,8 @@
 //                    columns, scale, store FP32 (accumulation by reductions) or split into
 //                    hi / lo planes, then release the accumulator.
 // Every mbarrier wait is bounded by the global timer (about 2 s); on expiry the kernel
-// sets an error word, stops issuing work, and returns through the normal teardown.
+// sets an error word, the other roles of the CTA stop waiting, and the CTA returns through
+// the normal teardown (TMEM freed), leaving the context usable.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -78,16 +79,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: gives up after ~2 s of wall time and reports through *err
+// bounded wait: gives up after ~2 s of wall time and reports through *err, or returns
+// early (without an error code of its own) once another role of the CTA has aborted
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                          const volatile int* abort_flag = nullptr,
+                                          uint64_t limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     for (int i = 0; i < 256; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) {
+    if (abort_flag && *abort_flag) return false;
+    if (global_ns() - t0 > limit_ns) {
       atomicCAS(err, 0, code);
       return false;
     }
@@ -180,6 +185,7 @@ struct TcArgs {
   // btab[4b] = A row base, btab[4b+1] = B row base, btab[4b+2] = output element offset,
   // btab[4b+3] = number of stacked products J_b
   const long long* btab;
+  int stall_test;  // test hook: the MMA warp first waits on a barrier nothing arrives at
   int* err;
 };
 
@@ -232,9 +238,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
   auto tfull = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
   auto tempty = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
+  const uint32_t never = bar0 + 8u * (2 * kStages + 4);
   uint32_t* tmem_slot =
-      reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 4));
-  __shared__ int s_abort;
+      reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 5));
+  __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = g.m_tiles * g.batches;
@@ -248,6 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(tfull(a), 1);
       mbar_init(tempty(a), 4);  // one arrival per epilogue warp
     }
+    mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int it = 0; it < iters; ++it, ++n) {
           const int s = (int)(n % kStages);
           const uint32_t ph = (n / kStages) & 1u;
-          if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1)) {
+          if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1, &s_abort)) {
             s_abort = 1;
             break;
           }
@@ -298,9 +306,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
                                  ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
       uint32_t n = 0, lt = 0;
+      if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
       for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x, ++lt) {
         const uint32_t acc = lt & 1u, use = lt >> 1;
-        if (!mbar_wait(tempty(acc), (use & 1u) ^ 1u, g.err, 4)) {
+        if (!mbar_wait(tempty(acc), (use & 1u) ^ 1u, g.err, 4, &s_abort)) {
           s_abort = 1;
           break;
         }
@@ -311,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int it = 0; it < iters; ++it, ++n) {
           const int s = (int)(n % kStages);
           const uint32_t ph = (n / kStages) & 1u;
-          if (!mbar_wait(full(s), ph, g.err, 2)) {
+          if (!mbar_wait(full(s), ph, g.err, 2, &s_abort)) {
             ok = false;
             break;
           }
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t lt = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u, use = lt >> 1;
-      const bool have = mbar_wait(tfull(acc), use & 1u, g.err, 3);
+      const bool have = mbar_wait(tfull(acc), use & 1u, g.err, 3, &s_abort);
       tc_fence_after();
       if (!have || s_abort) break;
       const int b = t / g.m_tiles;
@@ -676,10 +685,13 @@ static int tc_sm_count() {
   return n;
 }
 
+static int g_stall_next = 0;
+
 template <int NP, typename E>
 static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const CUtensorMap& B,
                            const CUtensorMap& Blo, TcArgs g, int m_tiles, int batches,
                            cudaStream_t st) {
+  g.stall_test = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
   auto kern = k_tc_gemm<NP, E>;
   const int smem = TcSmem<NP>::kBytes;
   static bool attr = false;
@@ -1057,3 +1069,11 @@ cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
 }
 
 }  // namespace cc
+
+// Test hook (no counterpart in the paper): the next tensor-core GEMM launch makes its MMA
+// warp wait on a barrier that nothing arrives at; the 20 ms bound runs out, the kernel
+// records error code 5 and returns through its normal teardown.
+extern "C" cc_status cc_test_stall_next_mixed(void) {
+  __atomic_store_n(&cc::g_stall_next, 1, __ATOMIC_RELEASE);
+  return CC_OK;
+}

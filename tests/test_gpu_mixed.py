@@ -109,3 +109,25 @@ def test_fp16x3_with_exponent_scaling(dev, cfg):
     ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
     assert abs(Ex[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
     t.free()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(dev):
+    """Failure detection without a fault: the test hook makes one tensor-core launch wait on
+    a barrier nothing arrives at; the bounded wait runs out, the error word reads 5, and
+    the next exchange on the same handle is correct again."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = CFG2["R"], CFG2["L"], CFG2["R_F"]
+    t = cc.build_tables("periodic", R=R, L=L, S=CFG2["S"])
+    Mg = t.info["Mg"]
+    eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+    Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+    assert cc.lib().cc_test_stall_next_mixed() == 0
+    cc.exchange_sums(t, R_F, eps, Ex, precision="bf16x3")
+    torch.cuda.synchronize()
+    assert cc.mixed_status(t) == 5
+    assert cc.mixed_status(t) == 0          # cleared by the read
+    grid, Ex2 = _run(t, R_F, "bf16x3", dev)
+    a, w = oracle_nodes(R, CFG2["S"])
+    assert rel_err(_basis_values(R, grid), ox.eps_separable(R, R_F, L, a, w)) < TOL_MIXED
+    t.free()
