@@ -186,6 +186,10 @@ struct TcArgs {
   // btab[4b+3] = number of stacked products J_b
   const long long* btab;
   int stall_test;  // test hook: the MMA warp first waits on a barrier nothing arrives at
+  // tile_b (Np = 128 only): the tile index walks the rows of B (N side) instead of A;
+  // output element (m, n) of tile `tile` goes to obase + tile*s_tile + m*s_mlo + n*s_n
+  int tile_b;
+  long long s_tile;
   int* err;
 };
 
@@ -288,8 +292,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           const int j = it / g.nk, kb = it % g.nk;
-          const int arow = (int)(bt.abase + j * g.a_sj + m0);
-          const int brow = (int)(bt.bbase + j * g.b_sj);
+          const int arow = (int)(bt.abase + j * g.a_sj + (g.tile_b ? 0 : m0));
+          const int brow = (int)(bt.bbase + j * g.b_sj + (g.tile_b ? m0 : 0));
           const uint32_t st = base + s * L::kStage;
           mbar_expect_tx(full(s), bytes);
           tma_load_2d(st, &mA, kb * kKB, arow, full(s));
@@ -353,9 +357,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       if (!have || s_abort) break;
       const int b = t / g.m_tiles;
-      const long long m = (long long)(t % g.m_tiles) * kTileM + warp * 32 + lane;
+      const int tile = t % g.m_tiles;
+      const long long m = g.tile_b ? (long long)(warp * 32 + lane)
+                                   : (long long)tile * kTileM + warp * 32 + lane;
       const long long mh = m / NP, ml = m % NP;
-      const long long row_off = tc_batch(g, b).obase + mh * g.s_mhi + ml * g.s_mlo;
+      const long long row_off = tc_batch(g, b).obase + (g.tile_b ? tile * g.s_tile : 0) +
+                                mh * g.s_mhi + ml * g.s_mlo;
       const float sc = g.scale ? g.scale[b] : 1.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < NP; c0 += 32) {
@@ -732,6 +739,43 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
   }
   for (int s0 = 0; s0 < S; s0 += C) {
     const int cs = S - s0 < C ? S - s0 : C;
+    if (NP == kTileM) {
+      // Np = 128: the Toeplitz operand is the 128-row M side and the tiles walk the slab
+      // stack on the N side, so every output row is contiguous (vector stores)
+      TcArgs g{};
+      g.nk = NP / kKB; g.J = 1; g.tile_b = 1; g.err = w->err;
+      g.scale = nullptr;
+      // step 1: R_s[x][(y,z)] = sum_x' X1_s[x][x'] OT[(y,z)][x']
+      g.a_base = (long long)s0 * NP; g.a_sb = NP; g.a_lo = 1;
+      g.b_base = 0; g.b_sb = 0; g.b_lo = 0;
+      g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
+      g.o_base = 0; g.o_sb = VOL; g.s_tile = kTileM; g.s_mhi = 0; g.s_mlo = NN; g.s_n = 1;
+      CC_TRY((launch_tc<NP, E>(P.mX1[0], P.mX1[1], P.mOT, P.mOT, g, m_tiles, cs, st)));
+      // step 2: W1_s[x][z'][y] = sum_z T_s[z'][z] R_s[(x,y)][z]
+      g.a_base = (long long)s0 * NP; g.a_sb = NP; g.a_lo = 1;
+      g.b_base = 0; g.b_sb = NN; g.b_lo = 1;
+      g.out = P.W[0]; g.out_lo = P.W[1];
+      g.o_base = 0; g.o_sb = 2 * VOL; g.s_tile = NN; g.s_mlo = NP; g.s_n = 1;
+      g.scale = P.cs ? P.cs + s0 : nullptr;
+      CC_TRY((launch_tc<NP, E>(P.mTT[0], P.mTT[1], P.mR[0], P.mR[1], g, m_tiles, cs, st)));
+      if (periodic) {
+        // step 3: W2_s[x][z'][y] = sum_z T_s[z'][z] O[(x,y)][z]
+        g.b_base = 0; g.b_sb = 0; g.b_lo = 0;
+        g.o_base = VOL;
+        CC_TRY((launch_tc<NP, E>(P.mTT[0], P.mTT[1], P.mO, P.mO, g, m_tiles, cs, st)));
+      }
+      // step 4: E[x][y'][z'] += sum_j sum_y WTD_j[y'][y] W_j[(x,z')][y]
+      TcArgs g4{};
+      g4.nk = NP / kKB; g4.tile_b = 1; g4.err = w->err;
+      g4.J = periodic ? 2 * cs : cs;
+      g4.a_base = (long long)s0 * 2 * NP; g4.a_sb = 0; g4.a_sj = periodic ? NP : 2 * NP; g4.a_lo = 1;
+      g4.b_base = 0; g4.b_sb = 0; g4.b_sj = periodic ? NN : 2 * NN; g4.b_lo = 1;
+      g4.out_split = 0; g4.beta = first ? 0 : 1; g4.out = w->E;
+      g4.o_base = 0; g4.o_sb = 0; g4.s_tile = NN; g4.s_mhi = 0; g4.s_mlo = NP; g4.s_n = 1;
+      CC_TRY((launch_tc<NP, E>(P.mWTD[0], P.mWTD[1], P.mW[0], P.mW[1], g4, m_tiles, 1, st)));
+      first = false;
+      continue;
+    }
     // step 1: R_s[x][(y,z)] = sum_x' X1_s[x][x'] OT[(y,z)][x']   (stored transposed)
     {
       TcArgs g{};

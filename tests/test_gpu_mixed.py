@@ -93,7 +93,7 @@ def test_mixed_repeatable(dev):
     t.free()
 
 
-@pytest.mark.parametrize("cfg", [CFG2, CFG3], ids=["R13", "R31"])
+@pytest.mark.parametrize("cfg", [CFG2, CFG3, CFG5], ids=["R13", "R31", "R63"])
 def test_fp16x3_with_exponent_scaling(dev, cfg):
     """fp16 hi+lo with per-node power-of-two scaling of the y-mode operands."""
     import paper_1502_08043_gb300 as cc
