@@ -190,6 +190,10 @@ struct TcArgs {
   // output element (m, n) of tile `tile` goes to obase + tile*s_tile + m*s_mlo + n*s_n
   int tile_b;
   long long s_tile;
+  // resident (J = 1, not tile_b): a CTA takes a contiguous run of tiles; the fixed N-side
+  // operand of a batch (all K blocks, hi and lo) is loaded once and stays in shared
+  // memory while only the M-side tiles stream through a ring of A slots
+  int resident;
   int* err;
 };
 
@@ -238,23 +242,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t bar0 = base + kStages * L::kStage;
+  constexpr int kRing = 4;  // barrier slots (3 used by the normal ring, 4 by the resident one)
   auto full = [&](int s) { return bar0 + 8u * s; };
-  auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
-  auto tfull = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
-  auto tempty = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
-  const uint32_t never = bar0 + 8u * (2 * kStages + 4);
+  auto empty = [&](int s) { return bar0 + 8u * (kRing + s); };
+  auto tfull = [&](int a) { return bar0 + 8u * (2 * kRing + a); };
+  auto tempty = [&](int a) { return bar0 + 8u * (2 * kRing + 2 + a); };
+  const uint32_t never = bar0 + 8u * (2 * kRing + 4);
+  const uint32_t a_full = bar0 + 8u * (2 * kRing + 5);
+  const uint32_t a_empty = bar0 + 8u * (2 * kRing + 6);
   uint32_t* tmem_slot =
-      reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kStages + 5));
+      reinterpret_cast<uint32_t*>(gbase + kStages * L::kStage + 8 * (2 * kRing + 7));
+  // resident mode: the N-side operand at base (nk x (hi, lo) of kB), ring of A slots after it
+  const uint32_t rb = base;
+  constexpr int kResBytes = 2 * 2 * L::kB;  // up to two K blocks of hi + lo
+  const uint32_t ring0 = base + (uint32_t)kResBytes;
+  constexpr int kResSlots0 = (kStages * L::kStage - kResBytes) / (2 * L::kA);
+  constexpr int kResSlots = kResSlots0 < kRing ? kResSlots0 : kRing;
+  static_assert(kResSlots >= 2, "resident ring");
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = g.m_tiles * g.batches;
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kRing; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
+    mbar_init(a_full, 1);
+    mbar_init(a_empty, 1);
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull(a), 1);
       mbar_init(tempty(a), 4);  // one arrival per epilogue warp
@@ -273,13 +289,57 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // tiles of this CTA: strided, or a contiguous run in resident mode
+  int t_first = blockIdx.x, t_step = gridDim.x, t_end = total;
+  if (g.resident) {
+    const int per = (total + gridDim.x - 1) / gridDim.x;
+    t_first = blockIdx.x * per;
+    t_step = 1;
+    t_end = min(total, t_first + per);
+  }
 
   if (warp == 4) {
     if (lane == 0) {
       // ---------------- TMA producer
       const uint32_t bytes = (uint32_t)(L::kA * (g.a_lo ? 2 : 1) + L::kB * (g.b_lo ? 2 : 1));
       uint32_t n = 0;
-      for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+      if (g.resident) {
+        const uint32_t rbytes = (uint32_t)(g.nk * L::kB * (g.b_lo ? 2 : 1));
+        const uint32_t abytes = (uint32_t)(L::kA * (g.a_lo ? 2 : 1));
+        uint32_t loads = 0;
+        int cur = -1;
+        for (int t = t_first; t < t_end && !s_abort; t += t_step) {
+          const int b = t / g.m_tiles;
+          const TcBatch bt = tc_batch(g, b);
+          const long long m0 = (long long)(t % g.m_tiles) * kTileM;
+          if (b != cur) {
+            if (!mbar_wait(a_empty, (loads & 1u) ^ 1u, g.err, 6, &s_abort)) {
+              s_abort = 1;
+              break;
+            }
+            mbar_expect_tx(a_full, rbytes);
+            for (int kb = 0; kb < g.nk; ++kb) {
+              tma_load_2d(rb + kb * 2 * L::kB, &mB, kb * kKB, (int)bt.bbase, a_full);
+              if (g.b_lo) tma_load_2d(rb + kb * 2 * L::kB + L::kB, &mBlo, kb * kKB, (int)bt.bbase, a_full);
+            }
+            cur = b;
+            ++loads;
+          }
+          for (int kb = 0; kb < g.nk; ++kb, ++n) {
+            const int s = (int)(n % kResSlots);
+            const uint32_t ph = (n / kResSlots) & 1u;
+            if (!mbar_wait(empty(s), ph ^ 1u, g.err, 1, &s_abort)) {
+              s_abort = 1;
+              break;
+            }
+            const uint32_t st = ring0 + s * 2 * L::kA;
+            mbar_expect_tx(full(s), abytes);
+            tma_load_2d(st, &mA, kb * kKB, (int)(bt.abase + m0), full(s));
+            if (g.a_lo) tma_load_2d(st + L::kA, &mAlo, kb * kKB, (int)(bt.abase + m0), full(s));
+          }
+        }
+      }
+      for (int t = blockIdx.x; t < total && !s_abort && !g.resident; t += gridDim.x) {
         const int b = t / g.m_tiles;
         const TcBatch bt = tc_batch(g, b);
         const int iters = bt.J * g.nk;
@@ -311,7 +371,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                  ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
       uint32_t n = 0, lt = 0;
       if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
-      for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x, ++lt) {
+      if (g.resident) {
+        uint32_t loads = 0;
+        int cur = -1;
+        for (int t = t_first; t < t_end && !s_abort; t += t_step, ++lt) {
+          const int b = t / g.m_tiles;
+          if (b != cur) {
+            if (cur >= 0) mma_commit(a_empty);  // frees the old operand once its MMAs finish
+            if (!mbar_wait(a_full, loads & 1u, g.err, 7, &s_abort)) {
+              s_abort = 1;
+              break;
+            }
+            ++loads;
+            cur = b;
+          }
+          const uint32_t acc = lt & 1u, use = lt >> 1;
+          if (!mbar_wait(tempty(acc), (use & 1u) ^ 1u, g.err, 4, &s_abort)) {
+            s_abort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + acc * (uint32_t)NP;
+          bool ok = true;
+          for (int kb = 0; kb < g.nk; ++kb, ++n) {
+            const int s = (int)(n % kResSlots);
+            const uint32_t ph = (n / kResSlots) & 1u;
+            if (!mbar_wait(full(s), ph, g.err, 2, &s_abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = ring0 + s * 2 * L::kA;
+            const uint64_t dA = sdesc(st), dAl = sdesc(st + L::kA);
+            const uint64_t dB = sdesc(rb + kb * 2 * L::kB), dBl = sdesc(rb + kb * 2 * L::kB + L::kB);
+#pragma unroll
+            for (int k = 0; k < kKB / 16; ++k) {
+              const uint64_t adv = (uint64_t)((k * 32) >> 4);
+              mma_f16(d, dA + adv, dB + adv, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+              if (g.b_lo) mma_f16(d, dA + adv, dBl + adv, idesc, 1u);
+              if (g.a_lo) mma_f16(d, dAl + adv, dB + adv, idesc, 1u);
+            }
+            mma_commit(empty(s));
+          }
+          if (!ok) {
+            s_abort = 1;
+            break;
+          }
+          mma_commit(tfull(acc));
+        }
+      }
+      for (int t = blockIdx.x; t < total && !s_abort && !g.resident; t += gridDim.x, ++lt) {
         const uint32_t acc = lt & 1u, use = lt >> 1;
         if (!mbar_wait(tempty(acc), (use & 1u) ^ 1u, g.err, 4, &s_abort)) {
           s_abort = 1;
@@ -351,7 +460,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     // ---------------- epilogue (warps 0-3; warp w owns TMEM lanes 32w .. 32w + 31)
     uint32_t lt = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+    for (int t = t_first; t < t_end; t += t_step, ++lt) {
       const uint32_t acc = lt & 1u, use = lt >> 1;
       const bool have = mbar_wait(tfull(acc), use & 1u, g.err, 3, &s_abort);
       tc_fence_after();
@@ -729,7 +838,7 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
   if (periodic) {
     // step 5: E[x][y][z'] = sum_z O[(x,y)][z] Dbar[z'][z]
     TcArgs g{};
-    g.nk = NP / kKB; g.J = 1;
+    g.nk = NP / kKB; g.J = 1; g.resident = 1;
     g.a_base = 0; g.a_lo = 0; g.b_base = 0; g.b_lo = 1;
     g.out_split = 0; g.beta = 0; g.out = w->E;
     g.o_base = 0; g.o_sb = 0; g.s_mhi = nat_mhi; g.s_mlo = nat_mlo; g.s_n = 1;
@@ -739,47 +848,10 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
   }
   for (int s0 = 0; s0 < S; s0 += C) {
     const int cs = S - s0 < C ? S - s0 : C;
-    if (NP == kTileM) {
-      // Np = 128: the Toeplitz operand is the 128-row M side and the tiles walk the slab
-      // stack on the N side, so every output row is contiguous (vector stores)
-      TcArgs g{};
-      g.nk = NP / kKB; g.J = 1; g.tile_b = 1; g.err = w->err;
-      g.scale = nullptr;
-      // step 1: R_s[x][(y,z)] = sum_x' X1_s[x][x'] OT[(y,z)][x']
-      g.a_base = (long long)s0 * NP; g.a_sb = NP; g.a_lo = 1;
-      g.b_base = 0; g.b_sb = 0; g.b_lo = 0;
-      g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
-      g.o_base = 0; g.o_sb = VOL; g.s_tile = kTileM; g.s_mhi = 0; g.s_mlo = NN; g.s_n = 1;
-      CC_TRY((launch_tc<NP, E>(P.mX1[0], P.mX1[1], P.mOT, P.mOT, g, m_tiles, cs, st)));
-      // step 2: W1_s[x][z'][y] = sum_z T_s[z'][z] R_s[(x,y)][z]
-      g.a_base = (long long)s0 * NP; g.a_sb = NP; g.a_lo = 1;
-      g.b_base = 0; g.b_sb = NN; g.b_lo = 1;
-      g.out = P.W[0]; g.out_lo = P.W[1];
-      g.o_base = 0; g.o_sb = 2 * VOL; g.s_tile = NN; g.s_mlo = NP; g.s_n = 1;
-      g.scale = P.cs ? P.cs + s0 : nullptr;
-      CC_TRY((launch_tc<NP, E>(P.mTT[0], P.mTT[1], P.mR[0], P.mR[1], g, m_tiles, cs, st)));
-      if (periodic) {
-        // step 3: W2_s[x][z'][y] = sum_z T_s[z'][z] O[(x,y)][z]
-        g.b_base = 0; g.b_sb = 0; g.b_lo = 0;
-        g.o_base = VOL;
-        CC_TRY((launch_tc<NP, E>(P.mTT[0], P.mTT[1], P.mO, P.mO, g, m_tiles, cs, st)));
-      }
-      // step 4: E[x][y'][z'] += sum_j sum_y WTD_j[y'][y] W_j[(x,z')][y]
-      TcArgs g4{};
-      g4.nk = NP / kKB; g4.tile_b = 1; g4.err = w->err;
-      g4.J = periodic ? 2 * cs : cs;
-      g4.a_base = (long long)s0 * 2 * NP; g4.a_sb = 0; g4.a_sj = periodic ? NP : 2 * NP; g4.a_lo = 1;
-      g4.b_base = 0; g4.b_sb = 0; g4.b_sj = periodic ? NN : 2 * NN; g4.b_lo = 1;
-      g4.out_split = 0; g4.beta = first ? 0 : 1; g4.out = w->E;
-      g4.o_base = 0; g4.o_sb = 0; g4.s_tile = NN; g4.s_mhi = 0; g4.s_mlo = NP; g4.s_n = 1;
-      CC_TRY((launch_tc<NP, E>(P.mWTD[0], P.mWTD[1], P.mW[0], P.mW[1], g4, m_tiles, 1, st)));
-      first = false;
-      continue;
-    }
     // step 1: R_s[x][(y,z)] = sum_x' X1_s[x][x'] OT[(y,z)][x']   (stored transposed)
     {
       TcArgs g{};
-      g.nk = NP / kKB; g.J = 1;
+      g.nk = NP / kKB; g.J = 1; g.resident = 1;
       g.a_base = 0; g.a_sb = 0; g.a_lo = 0;
       g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
       g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
@@ -790,7 +862,7 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
     // step 2: W1_s[x][z'][y] = sum_z T_s[z'][z] R_s[(x,y)][z]      (slab transposed)
     {
       TcArgs g{};
-      g.nk = NP / kKB; g.J = 1;
+      g.nk = NP / kKB; g.J = 1; g.resident = 1;
       g.a_base = 0; g.a_sb = NN; g.a_lo = 1;
       g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
       g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
@@ -802,7 +874,7 @@ static cc_status run_mixed(cc_tables t, MxWorkspace* w, MxPlanes& P, int R_F, fl
     if (periodic) {
       // step 3: W2_s[x][z'][y] = sum_z T_s[z'][z] O[(x,y)][z]
       TcArgs g{};
-      g.nk = NP / kKB; g.J = 1;
+      g.nk = NP / kKB; g.J = 1; g.resident = 1;
       g.a_base = 0; g.a_sb = 0; g.a_lo = 0;
       g.b_base = (long long)s0 * NP; g.b_sb = NP; g.b_lo = 1;
       g.out_split = 1; g.out = P.W[0]; g.out_lo = P.W[1];
@@ -1083,7 +1155,7 @@ cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   CC_CUDA(cudaGetLastError());
   {  // step 5: E_b = O_b x3 Dbar_b
     TcArgs g{};
-    g.nk = 1; g.J = 1; g.a_lo = 0; g.b_lo = 1;
+    g.nk = 1; g.J = 1; g.resident = 1; g.a_lo = 0; g.b_lo = 1;
     g.out_split = 0; g.beta = 0; g.out = m->E;
     g.s_mhi = NN; g.s_mlo = Np; g.s_n = 1;
     g.btab = m->t5; g.err = m->err;
@@ -1091,7 +1163,7 @@ cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   }
   for (int r = 0; r < m->rounds; ++r) {
     TcArgs g{};
-    g.nk = 1; g.J = 1; g.err = m->err;
+    g.nk = 1; g.J = 1; g.resident = 1; g.err = m->err;
     g.a_lo = 0; g.b_lo = 1; g.out_split = 1; g.out = P.R[0]; g.out_lo = P.R[1];
     g.s_mhi = Np; g.s_mlo = 1; g.s_n = NN; g.btab = m->t123[0][r];
     CC_TRY((launch_tc<Np, E>(P.mOT, P.mOT, P.mX1[0], P.mX1[1], g, m_tiles, m->n123[r], st)));
