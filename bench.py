@@ -3,13 +3,15 @@
 Workload (the paper's 9171-planewave scale): cutoff |n| <= 13 (Nb = 9171 planewaves),
 L = 20 bohr, 64 quadrature nodes (58 kept), Fermi radius 8 (Mocc = 2109).  One step is
 one pass of the whole hot path over one batch of synthetic input:
-  1. reconstruct 1e8 seeded momentum-conserving quadruples (IJ|KL)  (16 B in, 4 B out each)
+  1. reconstruct 1e8 seeded momentum-conserving quadruples (IJ|KL)  (8 B of uint16 basis
+     ids in, 4 B out each; the int32-id and int8x4-vector forms, 16 B each, are timed in
+     the breakdown)
   2. all Nb^2 = 8.41e7 exchange-type pair integrals V(k_i - k_j)
   3. exchange sums eps(k) on the (2R+1)^3 grid and E_x by Toeplitz mode products
      (plain FP32 path; mixed bf16x3 path as well when --mixed), FP64 E_x reduction.
 metric value = Coulomb evaluations per second = (1e8 + Nb^2 + Nb * Mocc) / step time,
 the exchange counted as the Nb * Mocc pair evaluations its sums replace.
-Inputs (1.6 GB of quadruples) are larger than L2 (129 MB), so no flush is needed.
+Inputs (0.8 GB of uint16-id quadruples) are larger than L2 (129 MB), so no flush is needed.
 
 --impl reference times the FP64 CPU oracle (the slow, plainly correct restatement of the
 paper) on a bounded sample of the same workload per step.
@@ -30,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 R, L, S, R_F = 13, 20.0, 64, 8
 N_QUADS = 100_000_000
-TRAFFIC_VEC_2E7 = 370.2e6  # ncu DRAM bytes of a 2e7-quadruple vector-form k_col launch
+# ncu DRAM bytes of a 2e7-quadruple k_col launch, per quadruple encoding
+TRAFFIC_2E7 = {"ids": 370.3e6, "vec": 370.2e6, "ids16": None}
 METRIC = "pair-Coulomb evals/s and integrals/s on 1 GB300, mixed vs FP32 at <=1e-4 rel err"
 UNIT = "Coulomb evals/s"
 WORKLOAD = ("paper scale: |n|<=13 (9171 planewaves), L=20 bohr, 64 nodes, R_F=8 (2109 occ); "
@@ -123,11 +126,15 @@ def run_gpu(args):
     qid = torch.empty((n, 4), dtype=torch.int32, device=dev)
     first, _ = replicas.quad_slice(rank, n)
     ci.quads_device(R, first, n, qid)
-    # the step consumes the quadruples in their int8x4 vector form (16 B each, the four
-    # planewave index vectors); the id form (int32 basis ids) is timed in the breakdown
-    q = torch.from_numpy(cc.basis(R)).to(dev)[qid.long().view(-1)].view(n, 4, 4)
-    if args.quad_format == "ids":
-        q = qid
+    # three encodings of the same quadruples: uint16 basis ids (8 B, needs Nb <= 65536),
+    # int32 ids (16 B) and the int8x4 vectors (16 B); the step reads --quad-format, the
+    # other two are timed in the breakdown
+    forms = {"ids": qid,
+             "vec": torch.from_numpy(cc.basis(R)).to(dev)[qid.long().view(-1)].view(n, 4, 4)}
+    if Nb <= 65536:
+        forms["ids16"] = torch.where(qid >= 32768, qid - 65536, qid).to(torch.int16)
+    q = forms[args.quad_format]
+    qbytes = q.element_size() * q[0].numel()   # bytes per quadruple
     vals = torch.empty(n, dtype=torch.float32, device=dev)
     pairs = torch.empty((Nb, Nb), dtype=torch.float32, device=dev)
     eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
@@ -199,9 +206,10 @@ def run_gpu(args):
     other = "separable" if lookup == "collapsed" else "collapsed"
     parts[f"reconstruct_{other}_ms"] = time_it(
         lambda: cc.reconstruct_integrals(t, q, vals, lookup=other))
-    qo = qid if args.quad_format == "vec" else q
-    parts[f"reconstruct_{lookup}_{'ids' if args.quad_format == 'vec' else 'vec'}_ms"] = time_it(
-        lambda: cc.reconstruct_integrals(t, qo, vals, lookup=lookup))
+    for fname, qo in forms.items():
+        if fname != args.quad_format:
+            parts[f"reconstruct_{lookup}_{fname}_ms"] = time_it(
+                lambda qo=qo: cc.reconstruct_integrals(t, qo, vals, lookup=lookup))
     if args.mixed:
         parts["exchange_bf16x3_ms"] = time_it(
             lambda: cc.exchange_sums(t, R_F, eps_mx, Ex_mx, precision="bf16x3"))
@@ -219,23 +227,35 @@ def run_gpu(args):
         he = torch.empty(Mg ** 3, dtype=torch.float32, pin_memory=True)
         hx = torch.empty(2, dtype=torch.float64, pin_memory=True)
 
-        # the step through the public API with host buffers: the quadruples go up in
-        # chunks on a copy stream while earlier chunks are reconstructed, and results
-        # come back on a second copy stream (H2D, compute and D2H overlap)
+        # the step through the public API with host buffers: the pair matrix and the
+        # exchange sums (which need no quadruples) are computed first and go down on one
+        # copy stream while the quadruples come up in chunks on another; each chunk is
+        # reconstructed as soon as it has landed and its values follow the pairs down
+        # (H2D, compute and D2H overlap; the link carries both directions at once)
         nchunk = 8
         bounds = [n * c // nchunk for c in range(nchunk + 1)]
         up = torch.cuda.Stream(dev)
         down = torch.cuda.Stream(dev)
         loaded = [torch.cuda.Event() for _ in range(nchunk)]
         done = [torch.cuda.Event() for _ in range(nchunk)]
+        ev_head = torch.cuda.Event()
 
         def e2e_step():
+            up.wait_stream(st)      # the previous step has finished with q
+            down.wait_stream(st)    # ... and with the host result buffers
             with torch.cuda.stream(up):
-                up.wait_stream(st)
                 for c in range(nchunk):
                     a, b = bounds[c], bounds[c + 1]
                     q[a:b].copy_(hq[a:b], non_blocking=True)
                     loaded[c].record(up)
+            cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup, stream=st)
+            cc.exchange_sums(t, R_F, eps, Ex, precision="fp32", stream=st)
+            ev_head.record(st)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_head)
+                hp.copy_(pairs, non_blocking=True)
+                he.copy_(eps, non_blocking=True)
+                hx.copy_(Ex, non_blocking=True)
             for c in range(nchunk):
                 a, b = bounds[c], bounds[c + 1]
                 st.wait_event(loaded[c])
@@ -244,15 +264,6 @@ def run_gpu(args):
                 with torch.cuda.stream(down):
                     down.wait_event(done[c])
                     hv[a:b].copy_(vals[a:b], non_blocking=True)
-            cc.pair_matrix(t, 0, Nb, pairs, lookup=lookup)
-            cc.exchange_sums(t, R_F, eps, Ex, precision="fp32")
-            ev_tail = torch.cuda.Event()
-            ev_tail.record(st)
-            with torch.cuda.stream(down):
-                down.wait_event(ev_tail)
-                hp.copy_(pairs, non_blocking=True)
-                he.copy_(eps, non_blocking=True)
-                hx.copy_(Ex, non_blocking=True)
             st.wait_stream(down)
             st.wait_stream(up)
 
@@ -270,19 +281,20 @@ def run_gpu(args):
         ems = a.elapsed_time(b) / ks
         ems = replicas.max_over_ranks(ems, dev)
         e2e = {"value": replicas.job_throughput(evals, world, ems), "unit": UNIT,
-               "h2d_bytes_per_step": int(n * 16),
+               "h2d_bytes_per_step": int(n * qbytes),
                "d2h_bytes_per_step": int(n * 4 + Nb * Nb * 4 + Mg ** 3 * 4 + 16),
                "ms_per_step": ems}
 
     peak, peak_kind = _peaks()
     # ncu DRAM bytes of one k_col launch for 2e7 quadruples, scaled by the quadruples of
     # this launch: id form 320.1 MB read + 50.2 MB written (profiles/k_col_paper_scale.md),
-    # vector form profiles/k_col_vec_paper_scale.md
+    # vector form profiles/k_col_vec_paper_scale.md, uint16 form
+    # profiles/k_col_ids16_paper_scale.md
     if args.traffic is None and lookup == "collapsed":
-        args.traffic = {"ids": 370.3e6, "vec": TRAFFIC_VEC_2E7}[args.quad_format]
+        args.traffic = TRAFFIC_2E7.get(args.quad_format)
         args.traffic = None if args.traffic is None else args.traffic * n / 2e7
+    algo_bytes = float(qbytes + 4) * n    # the quadruple in, one FP32 value out
     if lookup == "collapsed":
-        algo_bytes = 20.0 * n          # 16 B quadruple in, 4 B value out
         achieved = algo_bytes / (k_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": args.traffic,
@@ -290,7 +302,6 @@ def run_gpu(args):
                     "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind,
                     "traffic_source": "ncu dram bytes of a 2e7-quadruple launch, scaled"}
     else:
-        algo_bytes = 20.0 * n
         achieved = algo_bytes / (k_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": args.traffic, "kernel": "k_sep",
@@ -306,7 +317,7 @@ def run_gpu(args):
                    "S_eff": t.info["S_eff"], "R_F": R_F, "Nb": Nb, "Mocc": Mocc,
                    "quadruples": n, "quad_format": args.quad_format, "pairs": Nb * Nb,
                    "lookup": lookup,
-                   "evals_per_step": evals, "l2_policy": "inputs larger than L2 (1.6 GB)",
+                   "evals_per_step": evals, "l2_policy": f"inputs larger than L2 ({n * qbytes / 1e9:.1f} GB of quadruples)",
                    "parallelism": f"replicas x{world} (independent quadruple slices)"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": n_launch * args.steps,
         "clocks": clk, "breakdown": parts,
@@ -538,7 +549,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lookup", default="collapsed", choices=["collapsed", "separable"])
     ap.add_argument("--quads", type=int, default=N_QUADS)
-    ap.add_argument("--quad-format", default="vec", choices=["vec", "ids"])
+    ap.add_argument("--quad-format", default="ids16", choices=["ids16", "vec", "ids"])
     ap.add_argument("--mixed", action="store_true")
     ap.add_argument("--mixed-launches", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")

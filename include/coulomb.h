@@ -67,8 +67,9 @@ typedef enum {
 } cc_lookup;
 
 typedef enum {
-  CC_QUAD_IDS_I32 = 0, /* int32[n][4] basis ids (I, J, K, L) */
-  CC_QUAD_VEC_I8X4 = 1 /* int8[n][4][4]: the four vectors (n_x, n_y, n_z, unused) */
+  CC_QUAD_IDS_I32 = 0, /* int32[n][4] basis ids (I, J, K, L), 16 B per quadruple */
+  CC_QUAD_VEC_I8X4 = 1, /* int8[n][4][4]: the four vectors (n_x, n_y, n_z, unused), 16 B */
+  CC_QUAD_IDS_U16 = 2  /* uint16[n][4] basis ids, 8 B per quadruple; basis <= 65536 */
 } cc_quad_format;
 
 /* Quadrature and table parameters (Sec. II Eqs. 11-14 and the Table I meshes).
@@ -155,7 +156,9 @@ cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail);
 cc_status cc_basis(int R, int* Nb, int8_t* vec_host);
 
 /* Reconstruct (IJ|KL) for n quadruples (Sec. II Eq. 14; momentum conservation Sec. III).
- *   quads_dev     n quadruples in `format`, 16 bytes each, 16-byte aligned.
+ *   quads_dev     n quadruples in `format` (16 bytes each and 16-byte aligned; 8 bytes and
+ *                 8-byte aligned for CC_QUAD_IDS_U16, which needs Nb <= 65536, else
+ *                 CC_ERR_RANGE).
  *   lookup        CC_LOOKUP_SEPARABLE (any kernel) or CC_LOOKUP_COLLAPSED (PERIODIC).
  *   precision     CC_PREC_FP32 (out float[n]) or CC_PREC_FP64 (out double[n]).
  *   counters_dev  NULL or unsigned long long[3], ADDED to (not cleared):
@@ -220,6 +223,14 @@ cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
  * kernel returns.  The results of that exchange call are invalid; the context and
  * later calls are not affected. */
 cc_status cc_test_stall_next_mixed(void);
+
+/* Which bf16x3 form the tensor-core exchange takes (not part of the paper; a diagnostic and
+ * tuning switch of this implementation, process-wide): 0 = automatic, 1 = the step chain of
+ * five batched GEMM launches (any grid side <= 128), 2 = the fused slab kernel (grid side
+ * 65 .. 127 only; smaller grids then return CC_ERR_NOTSUPP).  Automatic takes the fused
+ * slab kernel wherever it applies.  The fp16x3 precision always takes the step chain.
+ * CC_ERR_ARG for any other value. */
+cc_status cc_set_mixed_variant(int variant);
 
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
  * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libcoulomb.so")
 KERNELS = {"periodic": 0, "box": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp16x3": 3}
 LOOKUPS = {"separable": 0, "collapsed": 1}
-FORMATS = {"ids": 0, "vec": 1}
+FORMATS = {"ids": 0, "vec": 1, "ids16": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "size beyond limit", 3: "CUDA error",
           4: "allocation failed", 5: "device wait timed out", 6: "not supported",
           7: "I/O or format error"}
@@ -79,6 +79,7 @@ SIGNATURES = {
     "cc_mixed_status": (_I, [_P, _P, _I]),
     "cc_exchange_sums_noalloc": (_I, [_P, _I, _P, _P, _P]),
     "cc_test_stall_next_mixed": (_I, []),
+    "cc_set_mixed_variant": (_I, [_I]),
     "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
     "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),
     "cc_batch_exchange": (_I, [_P, _I, _P, _P, _P]),
@@ -239,15 +240,21 @@ def _prec_of(t):
 
 def reconstruct_integrals(tables: Tables, quads, out, lookup="separable", counters=None,
                           stream=None):
-    """cc_reconstruct_integrals.  quads: int32[n, 4] ids or int8[n, 4, 4] vectors;
+    """cc_reconstruct_integrals.  quads: int32[n, 4] ids, int16[n, 4] ids (bit patterns of
+    uint16, basis <= 65536) or int8[n, 4, 4] vectors;
     out: float32 / float64 [n]; counters: None or int64[3] (added to)."""
     import torch
     if quads.dtype == torch.int32:
         fmt, n = FORMATS["ids"], quads.shape[0]
     elif quads.dtype == torch.int8:
         fmt, n = FORMATS["vec"], quads.shape[0]
+    elif quads.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        fmt, n = FORMATS["ids16"], quads.shape[0]   # the 16 bits of each id, unsigned
     else:
-        raise TypeError("quads must be int32 ids or int8 vectors")
+        raise TypeError("quads must be int32 ids, int16/uint16 ids or int8 vectors")
+    if n and (not quads.is_contiguous() or quads[0].numel() * quads.element_size() !=
+              (8 if fmt == FORMATS["ids16"] else 16)):
+        raise ValueError("quads must be contiguous rows of four ids (or four int8x4 vectors)")
     if out.numel() < n:
         raise ValueError("output too small")
     if counters is not None and (counters.dtype != torch.int64 or counters.numel() < 3):

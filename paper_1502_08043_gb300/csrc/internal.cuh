@@ -112,4 +112,10 @@ cc_status mixed_workspace_alloc(cc_tables t);
 void mixed_workspace_free(cc_tables t);
 cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
                          cudaStream_t st);
+// tcslab.cu (fused tensor-core exchange, grid side 65 .. 127, bf16x3)
+bool tc_slab_supported(cc_tables t);
+cc_status tc_slab_alloc(cc_tables t, void** out);
+void tc_slab_free(void* ws);
+cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
+                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st);
 }  // namespace cc

@@ -21,32 +21,28 @@ namespace cc {
 constexpr unsigned kFull = 0xffffffffu;
 enum : int { kNonCons = 1, kQZero = 2, kRange = 4, kInvalid = 8 };
 
-__device__ __forceinline__ char4 as_c4(int v) {
-  char4 c;
-  c.x = (signed char)(v & 0xff);
-  c.y = (signed char)((v >> 8) & 0xff);
-  c.z = (signed char)((v >> 16) & 0xff);
-  c.w = (signed char)((v >> 24) & 0xff);
-  return c;
-}
-
 __device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
 
-// q = n_J - n_I; conservation n_J - n_I + n_L - n_K == 0; flags; |q| per axis
+// A planewave index vector is one 32-bit word of signed bytes (n_x, n_y, n_z, -), both in
+// the basis table and in the int8x4 quadruple form, and the bookkeeping runs on the packed
+// words with byte-wise SIMD arithmetic (|n_i| <= 63, so every sum and difference below
+// stays inside a signed byte, and the conservation residual inside (-256, 256)).
+constexpr uint32_t kXYZ = 0x00ffffffu;
+
+__device__ __forceinline__ uint32_t ld_word(const char4* b, int i) {
+  return *reinterpret_cast<const uint32_t*>(b + i);  // one 32-bit load per gather
+}
+
+// q = n_J - n_I; conservation n_J - n_I + n_L - n_K == 0; flags; qa = (|q_x|, |q_y|, |q_z|)
+// as unsigned bytes
 template <bool kPeriodic>
-__device__ __forceinline__ int classify(char4 a, char4 b, char4 c, char4 d, int& qx, int& qy,
-                                        int& qz) {
-  qx = (int)b.x - (int)a.x;
-  qy = (int)b.y - (int)a.y;
-  qz = (int)b.z - (int)a.z;
-  const bool cons = (qx + (int)d.x - (int)c.x) == 0 && (qy + (int)d.y - (int)c.y) == 0 &&
-                    (qz + (int)d.z - (int)c.z) == 0;
+__device__ __forceinline__ int classify(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                        uint32_t& qa) {
+  const uint32_t resid = __vsub4(__vadd4(b, d), __vadd4(a, c)) & kXYZ;
+  qa = __vabsdiffs4(b, a) & kXYZ;
   int f = 0;
-  if (!cons) f = kNonCons;
-  else if (kPeriodic && (qx | qy | qz) == 0) f = kQZero;
-  qx = abs(qx);
-  qy = abs(qy);
-  qz = abs(qz);
+  if (resid != 0) f = kNonCons;
+  else if (kPeriodic && qa == 0) f = kQZero;
   return f;
 }
 
@@ -56,17 +52,43 @@ struct IdsSrc {
   int Nb;
   __device__ __forceinline__ int4 raw(int64_t i) const { return ld_stream(q + i); }
   template <bool kPeriodic>
-  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
-    return classify_raw<kPeriodic>(raw(i), qx, qy, qz);
+  __device__ __forceinline__ int decode(int64_t i, uint32_t& qa) const {
+    return classify_raw<kPeriodic>(raw(i), qa);
   }
   template <bool kPeriodic>
-  __device__ __forceinline__ int classify_raw(const int4 v, int& qx, int& qy, int& qz) const {
+  __device__ __forceinline__ int classify_raw(const int4 v, uint32_t& qa) const {
     if ((unsigned)v.x >= (unsigned)Nb || (unsigned)v.y >= (unsigned)Nb ||
         (unsigned)v.z >= (unsigned)Nb || (unsigned)v.w >= (unsigned)Nb) {
-      qx = qy = qz = 0;
+      qa = 0;
       return kRange;
     }
-    return classify<kPeriodic>(basis[v.x], basis[v.y], basis[v.z], basis[v.w], qx, qy, qz);
+    return classify<kPeriodic>(ld_word(basis, v.x), ld_word(basis, v.y), ld_word(basis, v.z),
+                               ld_word(basis, v.w), qa);
+  }
+};
+
+// uint16 ids: 8 bytes per quadruple (basis of at most 65536 functions)
+struct Ids16Src {
+  const uint2* q;
+  const char4* basis;
+  int Nb;
+  __device__ __forceinline__ int4 raw(int64_t i) const {
+    const uint2 v = __ldcs(q + i);
+    return make_int4((int)(v.x & 0xffffu), (int)(v.x >> 16), (int)(v.y & 0xffffu),
+                     (int)(v.y >> 16));
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int decode(int64_t i, uint32_t& qa) const {
+    return classify_raw<kPeriodic>(raw(i), qa);
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_raw(const int4 v, uint32_t& qa) const {
+    if (v.x >= Nb || v.y >= Nb || v.z >= Nb || v.w >= Nb) {
+      qa = 0;
+      return kRange;
+    }
+    return classify<kPeriodic>(ld_word(basis, v.x), ld_word(basis, v.y), ld_word(basis, v.z),
+                               ld_word(basis, v.w), qa);
   }
 };
 
@@ -74,22 +96,23 @@ struct VecSrc {
   const int4* q;
   const char4* basis;  // unused
   int R2;
-  __device__ __forceinline__ static bool in_sphere(char4 a, int R2) {
-    return (int)a.x * a.x + (int)a.y * a.y + (int)a.z * a.z <= R2;
+  __device__ __forceinline__ bool in_sphere(uint32_t a) const {
+    const int v = (int)(a & kXYZ);
+    return __dp4a(v, v, 0) <= R2;
   }
   __device__ __forceinline__ int4 raw(int64_t i) const { return ld_stream(q + i); }
   template <bool kPeriodic>
-  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
-    return classify_raw<kPeriodic>(raw(i), qx, qy, qz);
+  __device__ __forceinline__ int decode(int64_t i, uint32_t& qa) const {
+    return classify_raw<kPeriodic>(raw(i), qa);
   }
   template <bool kPeriodic>
-  __device__ __forceinline__ int classify_raw(const int4 v, int& qx, int& qy, int& qz) const {
-    const char4 a = as_c4(v.x), b = as_c4(v.y), c = as_c4(v.z), d = as_c4(v.w);
-    if (!in_sphere(a, R2) || !in_sphere(b, R2) || !in_sphere(c, R2) || !in_sphere(d, R2)) {
-      qx = qy = qz = 0;
+  __device__ __forceinline__ int classify_raw(const int4 v, uint32_t& qa) const {
+    const uint32_t a = (uint32_t)v.x, b = (uint32_t)v.y, c = (uint32_t)v.z, d = (uint32_t)v.w;
+    if (!in_sphere(a) || !in_sphere(b) || !in_sphere(c) || !in_sphere(d)) {
+      qa = 0;
       return kRange;
     }
-    return classify<kPeriodic>(a, b, c, d, qx, qy, qz);
+    return classify<kPeriodic>(a, b, c, d, qa);
   }
 };
 
@@ -100,11 +123,11 @@ struct PairSrc {
   int Nb;
   int64_t row0;
   template <bool kPeriodic>
-  __device__ __forceinline__ int decode(int64_t i, int& qx, int& qy, int& qz) const {
+  __device__ __forceinline__ int decode(int64_t i, uint32_t& qa) const {
     const int64_t r = row0 + i / Nb;
     const int c = (int)(i % Nb);
-    const char4 a = basis[r], b = basis[c];
-    return classify<kPeriodic>(a, b, b, a, qx, qy, qz);
+    const uint32_t a = ld_word(basis, (int)r), b = ld_word(basis, c);
+    return classify<kPeriodic>(a, b, b, a, qa);
   }
 };
 
@@ -172,10 +195,10 @@ __global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __rest
   for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * 32; base < n;
        base += (int64_t)gridDim.x * nw * 32) {
     const int64_t i = base + lane;
-    int qx = 0, qy = 0, qz = 0, flag = kInvalid;
-    if (i < n) flag = src.template decode<kPeriodic>(i, qx, qy, qz);
-    if (flag) qx = qy = qz = 0;
-    const unsigned pk = (unsigned)qx | ((unsigned)qy << 8) | ((unsigned)qz << 16);
+    uint32_t qa = 0;
+    int flag = kInvalid;
+    if (i < n) flag = src.template decode<kPeriodic>(i, qa);
+    const unsigned pk = flag ? 0u : qa;  // (|q_x|, |q_y|, |q_z|) bytes
     c0 += __popc(__ballot_sync(kFull, flag == kNonCons));
     c1 += __popc(__ballot_sync(kFull, flag == kQZero));
     c2 += __popc(__ballot_sync(kFull, flag == kRange));
@@ -228,12 +251,13 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
     int4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = src.raw(i + u * stride);
-    int f[U], m[U];
+    int f[U];
+    uint32_t m[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      int qx, qy, qz;
-      f[u] = src.template classify_raw<true>(v[u], qx, qy, qz);
-      m[u] = qx * qx + qy * qy + qz * qz;
+      uint32_t qa;
+      f[u] = src.template classify_raw<true>(v[u], qa);
+      m[u] = __dp4a(qa, qa, 0u);  // |q|^2
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -244,12 +268,12 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
     }
   }
   for (; i < n; i += stride) {
-    int qx, qy, qz;
-    const int f = src.template decode<true>(i, qx, qy, qz);
+    uint32_t qa;
+    const int f = src.template decode<true>(i, qa);
     c0 += f == kNonCons;
     c1 += f == kQZero;
     c2 += f == kRange;
-    __stcs(out + i, f ? T(0) : Vm[qx * qx + qy * qy + qz * qz]);
+    __stcs(out + i, f ? T(0) : Vm[__dp4a(qa, qa, 0u)]);
   }
   c0 = __reduce_add_sync(kFull, c0);
   c1 = __reduce_add_sync(kFull, c1);
@@ -275,12 +299,11 @@ __global__ void __launch_bounds__(256) k_pair_col(const char4* __restrict__ gbas
   }
   __syncthreads();
   for (int64_t r = blockIdx.y; r < nrows; r += gridDim.y) {
-    const char4 a = gbasis[row0 + r];
+    const uint32_t a = ld_word(gbasis, (int)(row0 + r));
     T* orow = out + r * (int64_t)Nb;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Nb; j += gridDim.x * blockDim.x) {
-      const char4 b = basis[j];
-      const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-      __stcs(orow + j, Vm[dx * dx + dy * dy + dz * dz]);
+      const uint32_t qa = __vabsdiffs4(ld_word(basis, j), a) & kXYZ;
+      __stcs(orow + j, Vm[__dp4a(qa, qa, 0u)]);
     }
   }
 }
@@ -370,6 +393,13 @@ static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int fo
   const bool periodic = t->p.kernel == CC_KERNEL_PERIODIC;
   const char4* basis = reinterpret_cast<const char4*>(t->d.basis);
   const int4* q = reinterpret_cast<const int4*>(quads);
+  const uint2* q16 = reinterpret_cast<const uint2*>(quads);
+  if (format == CC_QUAD_IDS_U16) {
+    if (lookup == CC_LOOKUP_COLLAPSED)
+      return launch_col<T>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st, true);
+    if (periodic) return launch_sep<T, Ids16Src, true>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
+    return launch_sep<T, Ids16Src, false>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
+  }
   if (lookup == CC_LOOKUP_COLLAPSED) {
     if (format == CC_QUAD_IDS_I32) return launch_col<T>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st, true);
     return launch_col<T>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st, false);
@@ -424,13 +454,15 @@ extern "C" cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev
                                               void* out_dev, unsigned long long* counters_dev,
                                               void* stream) {
   if (!t || n < 0) return CC_ERR_ARG;
-  if (format != CC_QUAD_IDS_I32 && format != CC_QUAD_VEC_I8X4) return CC_ERR_ARG;
+  if (format != CC_QUAD_IDS_I32 && format != CC_QUAD_VEC_I8X4 && format != CC_QUAD_IDS_U16)
+    return CC_ERR_ARG;
+  if (format == CC_QUAD_IDS_U16 && t->Nb > 65536) return CC_ERR_RANGE;
   if (lookup != CC_LOOKUP_SEPARABLE && lookup != CC_LOOKUP_COLLAPSED) return CC_ERR_ARG;
   if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
   if (lookup == CC_LOOKUP_COLLAPSED && t->p.kernel != CC_KERNEL_PERIODIC) return CC_ERR_NOTSUPP;
   if (n == 0) return CC_OK;
   if (!quads_dev || !out_dev) return CC_ERR_ARG;
-  if (((uintptr_t)quads_dev & 15) != 0) return CC_ERR_ARG;
+  if (((uintptr_t)quads_dev & (format == CC_QUAD_IDS_U16 ? 7 : 15)) != 0) return CC_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   if (precision == CC_PREC_FP32)
     return reconstruct_t<float>(t, quads_dev, n, format, lookup, (float*)out_dev, counters_dev, st);

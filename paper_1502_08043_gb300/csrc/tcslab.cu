@@ -1,0 +1,611 @@
+// Fused tensor-core exchange sums for grid sides 65 .. 127 (Np = 128), bf16 hi + lo.
+//
+// Sec. III exchange of the uniform electron gas with the node sum of Sec. II Eq. 14; the
+// periodic kernel uses the D_s = T_s - I split, so with the Fermi-sphere occupation O
+//   E[x] = sum_s w_s (T_s R_{s,x} + A_{s,x}) T_s  +  (I x I x Dbar term),
+// where, for the slab x (all matrices Mg x Mg, indices y, z):
+//   R_{s,x}[y][z] = F_s[x][h(y, z)]     the first mode product of O (line along x),
+//   A_{s,x}[y][z] = F_s[y][h(x, z)]     O x2 D_s restricted to the slab (line along y),
+//   F_s[a][h]     = sum_{k = R-h}^{R+h} D_s[a][k]   (window sums, FP64, 0 for h < 0),
+//   h(u, v)       = floor(sqrt(R_F^2 - (u-R)^2 - (v-R)^2)), -1 outside the sphere.
+// The box kernel has F_s from T_s, no A term and no Dbar term.
+//
+// One CTA per SM walks a contiguous run of work units (slab pair, node).  For every unit:
+//   MMA1  U_j = T_s R_{s,x_j}                 (A = T_s, B = R from shared memory)
+//   epi   U_j <- w_s U_j + w_s A_{s,x_j}, split into bf16 hi + lo, written back into the
+//         same tensor-memory columns (each 32-column chunk becomes 16 hi + 16 lo columns)
+//   MMA2  E_j += U_j T_s                      (A = U_j from tensor memory, B = T_s)
+// for the two slabs x_0 = 2p, x_1 = 2p + 1 of the pair, issued in the order
+//   MMA1(i, 0), MMA2(i-1, 1), MMA1(i, 1), MMA2(i, 0)
+// so that the epilogue of one slab always overlaps two GEMMs of the other, the single
+// R operand buffer has one GEMM of slack for its rebuild, and T_s (two buffers) is
+// loaded by TMA two GEMMs ahead.  E_0, E_1 stay in tensor memory (FP32) for the whole run
+// of nodes of the pair on this CTA and leave once, as a partial; a second kernel adds
+// the partials of each pair in a fixed order (deterministic), adds the Dbar term and
+// forms eps and E_x.  Each product is bf16x3: hi*hi + hi*lo + lo*hi, FP32 accumulate.
+//
+// Tensor memory (512 columns): [0,128) U_0, [128,256) U_1, [256,384) E_0, [384,512) E_1.
+// Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..), 8-13 build R,
+// 14 TMA producer, 15 MMA issuer.  Every wait is bounded (global timer); on expiry the
+// error word is set, all roles stop, the MMA issuer drains its MMAs and tensor memory is
+// freed before the CTA returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "tc_prims.cuh"
+
+namespace cc {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kEpiWarps = 8;
+constexpr int kBldWarps = 6;
+constexpr int kBldThreads = 32 * kBldWarps;
+constexpr int kProdWarp = 14;
+constexpr int kMmaWarp = 15;
+constexpr int kN = 128;                 // padded grid side
+constexpr int kHMax = 64;               // window half-lengths h = 0 .. R_F <= 63
+constexpr uint32_t kPlane = 128 * 64 * 2;   // one 64-wide K block of one plane: 16 KB
+constexpr uint32_t kOp = 4 * kPlane;        // 128 x 128 operand, hi + lo: 64 KB
+constexpr uint32_t kOffT = 0;               // two T_s buffers
+constexpr uint32_t kOffR = 2 * kOp;         // the R operand
+constexpr uint32_t kOffIsq = 3 * kOp;       // floor(sqrt(v)), v < 4096
+constexpr uint32_t kOffBar = kOffIsq + 4096;
+constexpr int kNumBars = 16;
+constexpr uint32_t kSmemBytes = kOffBar + 8 * kNumBars + 16 + 1024;
+
+struct Args {
+  int R, R_F, Mg, S, periodic;
+  int units, maxseg;
+  const uint32_t* FR;  // [S][128][64] F_s[x][h] as bf16 hi (low half) | lo (high half)
+  const float* FW;     // [S][64][128] w_s F_s[y][h], h-major (periodic)
+  const float* w;      // [S]
+  float* part;         // [pairs * maxseg][2][128][128] partial E of a slab pair
+  int* err;
+  int stall_test;
+};
+
+// CTA c owns work units [c U / G, (c + 1) U / G); the CTA that owns unit u
+__host__ __device__ inline int owner_cta(long long u, int units, int grid) {
+  int c = (int)((u * grid) / units);
+  while (c + 1 < grid && (long long)(c + 1) * units / grid <= u) ++c;
+  while (c > 0 && (long long)c * units / grid > u) --c;
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_slab(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
+              Args g) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gb = smem_raw + (base - raw);
+  const uint8_t* isq = gb + kOffIsq;
+  const uint32_t bar = base + kOffBar;
+  auto tfull = [&](int k) { return bar + 8u * k; };          // 0, 1
+  auto tfree = [&](int k) { return bar + 8u * (2 + k); };    // 2, 3
+  const uint32_t rfull = bar + 8u * 4, rfree = bar + 8u * 5;
+  auto d1full = [&](int j) { return bar + 8u * (6 + j); };   // 6, 7
+  auto a2full = [&](int j) { return bar + 8u * (8 + j); };   // 8, 9
+  const uint32_t efull = bar + 8u * 10, edone = bar + 8u * 11;
+  const uint32_t never = bar + 8u * 12, drain = bar + 8u * 13;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int R = g.R, RF = g.R_F, S = g.S;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(tfull(k), 1);
+      mbar_init(tfree(k), 1);
+      mbar_init(d1full(k), 1);
+      mbar_init(a2full(k), kEpiWarps);
+    }
+    mbar_init(rfull, kBldWarps);
+    mbar_init(rfree, 1);
+    mbar_init(efull, 1);
+    mbar_init(edone, kEpiWarps);
+    mbar_init(never, 1);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // isqrt table and a zero R operand (the builders only ever write the square
+  // |y - R|, |z - R| <= R_F; the rest of the operand stays zero)
+  for (int v = tid; v < 4096; v += kThreads) {
+    int h = (int)sqrtf((float)v);
+    while (h * h > v) --h;
+    while ((h + 1) * (h + 1) <= v) ++h;
+    gb[kOffIsq + v] = (uint8_t)h;
+  }
+  for (uint32_t o = 16u * tid; o < kOp; o += 16u * kThreads)
+    *reinterpret_cast<uint4*>(gb + kOffR + o) = make_uint4(0u, 0u, 0u, 0u);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const long long u0 = (long long)blockIdx.x * g.units / gridDim.x;
+  const long long u1 = (long long)(blockIdx.x + 1) * g.units / gridDim.x;
+
+  if (warp == kProdWarp) {
+    if (lane == 0) {
+      // ---------------- TMA producer: T_s hi + lo, both K blocks, into buffer (unit & 1)
+      uint32_t n = 0;
+      for (long long u = u0; u < u1 && !s_abort; ++u, ++n) {
+        const int s = (int)(u % S), k = (int)(n & 1u);
+        if (!mbar_wait(tfree(k), ((n >> 1) & 1u) ^ 1u, g.err, 11, &s_abort)) {
+          s_abort = 1;
+          break;
+        }
+        const uint32_t dst = base + kOffT + k * kOp;
+        mbar_expect_tx(tfull(k), kOp);
+        for (int kb = 0; kb < 2; ++kb) {
+          tma_load_2d(dst + kb * 2 * kPlane, &mTh, kb * 64, s * kN, tfull(k));
+          tma_load_2d(dst + kb * 2 * kPlane + kPlane, &mTl, kb * 64, s * kN, tfull(k));
+        }
+      }
+      // copies still in flight land before the CTA leaves
+      for (uint32_t m = n > 2 ? n - 2 : 0; m < n; ++m)
+        mbar_wait(tfull(m & 1u), (m >> 1) & 1u, g.err, 12, nullptr, 100000000ull);
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                 ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
+      uint32_t n = 0, r = 0, segc = 0;
+      auto mma1 = [&](uint32_t tb, int j) {
+        const uint32_t d = tmem + (uint32_t)(j * 128);
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+          const uint64_t dA = sdesc(tb + kb * 2 * kPlane), dAl = sdesc(tb + kb * 2 * kPlane + kPlane);
+          const uint64_t dB = sdesc(base + kOffR + kb * 2 * kPlane);
+          const uint64_t dBl = sdesc(base + kOffR + kb * 2 * kPlane + kPlane);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t adv = (uint64_t)(2 * k);  // 32 bytes per K = 16 step
+            mma_f16(d, dA + adv, dB + adv, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            mma_f16(d, dA + adv, dBl + adv, idesc, 1u);
+            mma_f16(d, dAl + adv, dB + adv, idesc, 1u);
+          }
+        }
+      };
+      auto mma2 = [&](uint32_t tb, int j, bool first) {
+        const uint32_t d = tmem + 256u + (uint32_t)(j * 128);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {  // K step m covers z = 16 m .. 16 m + 15
+          const int kb = m >> 2, k = m & 3;
+          const uint32_t aH = tmem + (uint32_t)(j * 128 + 32 * (m >> 1) + 8 * (m & 1));
+          const uint64_t dB = sdesc(tb + kb * 2 * kPlane) + (uint64_t)(2 * k);
+          const uint64_t dBl = sdesc(tb + kb * 2 * kPlane + kPlane) + (uint64_t)(2 * k);
+          mma_f16_ts(d, aH, dB, idesc, (first && m == 0) ? 0u : 1u);
+          mma_f16_ts(d, aH, dBl, idesc, 1u);
+          mma_f16_ts(d, aH + 16u, dB, idesc, 1u);
+        }
+      };
+      bool ok = !s_abort;
+      for (long long u = u0; u < u1 && ok;) {
+        const long long p = u / S;
+        const long long ue = u1 < (p + 1) * S ? u1 : (p + 1) * S;
+        const int U = (int)(ue - u);
+        for (int i = 0; i < U && ok; ++i, ++n) {
+          const uint32_t k = n & 1u, tb = base + kOffT + k * kOp;
+          const uint32_t tbp = base + kOffT + (k ^ 1u) * kOp;
+          // MMA1(i, 0)
+          ok = mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
+               mbar_wait(rfull, r & 1u, g.err, 15, &s_abort);
+          if (!ok) break;
+          tc_fence_after();
+          mma1(tb, 0);
+          mma_commit(rfree);
+          mma_commit(d1full(0));
+          ++r;
+          // MMA2(i - 1, 1)
+          if (i > 0) {
+            ok = mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort);
+            if (!ok) break;
+            tc_fence_after();
+            mma2(tbp, 1, i - 1 == 0);
+            mma_commit(tfree(k ^ 1u));
+          }
+          // MMA1(i, 1)
+          ok = mbar_wait(rfull, r & 1u, g.err, 15, &s_abort);
+          if (!ok) break;
+          tc_fence_after();
+          mma1(tb, 1);
+          mma_commit(rfree);
+          mma_commit(d1full(1));
+          ++r;
+          // MMA2(i, 0); the first one of a pair also waits until the previous pair's E
+          // has left tensor memory
+          ok = mbar_wait(a2full(0), n & 1u, g.err, 16, &s_abort) &&
+               (i > 0 || segc == 0 || mbar_wait(edone, (segc - 1) & 1u, g.err, 13, &s_abort));
+          if (!ok) break;
+          tc_fence_after();
+          mma2(tb, 0, i == 0);
+        }
+        if (!ok) break;
+        // MMA2(U - 1, 1), then E of the pair is complete
+        const uint32_t kl = (n - 1) & 1u;
+        ok = mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort);
+        if (!ok) break;
+        tc_fence_after();
+        mma2(base + kOffT + kl * kOp, 1, U == 1);
+        mma_commit(tfree(kl));
+        mma_commit(efull);
+        ++segc;
+        u = ue;
+      }
+      if (!ok) s_abort = 1;
+      // every MMA issued has finished before tensor memory is released
+      mma_commit(drain);
+      mbar_wait(drain, 0, g.err, 17, nullptr, 100000000ull);
+    }
+  } else if (warp >= kEpiWarps) {
+    // ---------------- R operand builders (warps 8-13)
+    const int bt = tid - 32 * kEpiWarps;
+    const int zlo = R - RF, nz = 2 * RF + 1;
+    const int clo = (R - RF) >> 3, nc = ((R + RF) >> 3) - clo + 1;
+    const int tasks = nz * nc;
+    uint32_t r = 0;
+    bool ok = true;
+    for (long long u = u0; u < u1 && ok; ++u) {
+      const long long p = u / S;
+      const int s = (int)(u % S);
+      for (int j = 0; j < 2 && ok; ++j, ++r) {
+        ok = mbar_wait(rfree, (r & 1u) ^ 1u, g.err, 21, &s_abort);
+        if (!ok) break;
+        // R_{s,x}[y][z] = F_s[x][h(y, z)]: the x line of the sphere at (y, z) does not
+        // depend on x, only the row of F_s does
+        const int x = (int)(2 * p + j);
+        const int Q = RF * RF;
+        const uint32_t* Fx = g.FR + ((long long)s * kN + x) * kHMax;
+        for (int t = bt; t < tasks; t += kBldThreads) {
+          const int z = zlo + t / nc, c = clo + t % nc;
+          const int dz = z - R, q2 = Q - dz * dz;
+          uint32_t v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int dy = 8 * c + e - R;
+            const int q = q2 - dy * dy;
+            v[e] = q >= 0 ? __ldg(Fx + isq[q]) : 0u;
+          }
+          uint4 hi, lo;
+          hi.x = __byte_perm(v[0], v[1], 0x5410);
+          hi.y = __byte_perm(v[2], v[3], 0x5410);
+          hi.z = __byte_perm(v[4], v[5], 0x5410);
+          hi.w = __byte_perm(v[6], v[7], 0x5410);
+          lo.x = __byte_perm(v[0], v[1], 0x7632);
+          lo.y = __byte_perm(v[2], v[3], 0x7632);
+          lo.z = __byte_perm(v[4], v[5], 0x7632);
+          lo.w = __byte_perm(v[6], v[7], 0x7632);
+          const uint32_t off = kOffR + (uint32_t)(c >> 3) * 2 * kPlane + (uint32_t)z * 128u +
+                               ((uint32_t)((c & 7) ^ (z & 7)) << 4);
+          *reinterpret_cast<uint4*>(gb + off) = hi;
+          *reinterpret_cast<uint4*>(gb + off + kPlane) = lo;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rfull);
+      }
+    }
+    if (!ok) s_abort = 1;
+  } else {
+    // ---------------- epilogue warps 0-7
+    const int quad = warp & 3, half = warp >> 2;
+    const int yrow = 32 * quad + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    uint32_t n = 0, segc = 0;
+    bool ok = true;
+    for (long long u = u0; u < u1 && ok;) {
+      const long long p = u / S;
+      const long long ue = u1 < (p + 1) * S ? u1 : (p + 1) * S;
+      for (; u < ue && ok; ++u, ++n) {
+        const int s = (int)(u % S);
+        const float ws = g.w[s];
+        const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
+        for (int j = 0; j < 2; ++j) {
+          ok = mbar_wait(d1full(j), n & 1u, g.err, 31, &s_abort);
+          if (!ok) break;
+          tc_fence_after();
+          const int dx = (int)(2 * p + j) - R;
+          const int Q = RF * RF - dx * dx;
+#pragma unroll 1
+          for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
+            const uint32_t ta = tmem + lane_off + (uint32_t)(j * 128 + 32 * cc);
+            uint32_t v[32];
+            tmem_ld32(ta, v);
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int e = 0; e < 32; e += 2) {
+              float a0 = 0.0f, a1 = 0.0f;
+              if (g.periodic) {
+                const int dz0 = 32 * cc + e - R, dz1 = dz0 + 1;
+                const int q0 = Q - dz0 * dz0, q1 = Q - dz1 * dz1;
+                if (q0 >= 0) a0 = __ldg(FWs + (int)isq[q0] * kN);
+                if (q1 >= 0) a1 = __ldg(FWs + (int)isq[q1] * kN);
+              }
+              const float x0 = fmaf(__uint_as_float(v[e]), ws, a0);
+              const float x1 = fmaf(__uint_as_float(v[e + 1]), ws, a1);
+              const uint32_t h = pack_bf16x2(x0, x1);
+              hi[e >> 1] = h;
+              lo[e >> 1] = pack_bf16x2(x0 - bf16_lo_f(h), x1 - bf16_hi_f(h));
+            }
+            tmem_st16(ta, hi);
+            tmem_st16(ta + 16u, lo);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(a2full(j));
+        }
+      }
+      if (!ok) break;
+      // the pair's E leaves tensor memory once, as a partial of this CTA
+      ok = mbar_wait(efull, segc & 1u, g.err, 32, &s_abort);
+      if (!ok) break;
+      tc_fence_after();
+      const int kseg = (int)blockIdx.x - owner_cta(p * S, g.units, gridDim.x);
+      float* P = g.part + ((p * g.maxseg + kseg) * 2) * (long long)(kN * kN);
+      for (int j = 0; j < 2; ++j) {
+#pragma unroll 1
+        for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
+          uint32_t v[32];
+          tmem_ld32(tmem + lane_off + (uint32_t)(256 + j * 128 + 32 * cc), v);
+          float4* o = reinterpret_cast<float4*>(P + (long long)j * kN * kN + yrow * kN + 32 * cc);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                               __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(edone);
+      ++segc;
+    }
+    if (!ok) s_abort = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+}
+
+// F_s window sums (FP64) of every row a < Mg: the bf16 hi | lo pairs for the R operand and,
+// periodic, w_s F_s transposed for the A term.  One thread per (s, a).
+__global__ void k_tc_slab_prep(const double* Tm, const double* w, int S, int Mg, int R, int RF,
+                               int periodic, uint32_t* FR, float* FW) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S * kN) return;
+  const int s = i / kN, a = i % kN;
+  const double* row = Tm + ((long long)s * Mg + (a < Mg ? a : 0)) * Mg;
+  auto X = [&](int k) { return (periodic && k == a) ? 0.0 : row[k]; };
+  double acc = 0.0;
+  for (int h = 0; h < kHMax; ++h) {
+    double f = 0.0;
+    if (a < Mg && h <= RF) {
+      acc += h == 0 ? X(R) : X(R - h) + X(R + h);
+      f = acc;
+    }
+    const __nv_bfloat16 hb = __double2bfloat16(f);
+    const __nv_bfloat16 lb = __double2bfloat16(f - (double)__bfloat162float(hb));
+    FR[(long long)i * kHMax + h] = (uint32_t)__bfloat16_as_ushort(hb) |
+                                   ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+    if (periodic) FW[((long long)s * kHMax + h) * kN + a] = (float)(w[s] * f);
+  }
+}
+
+// window sums of Dbar (I x I x Dbar term), FB[h][z'] = sum_{k=R-h}^{R+h} Dbar[z'][k]
+__global__ void k_tc_slab_dbar(const double* Dbar, int Mg, int R, int RF, float* FB) {
+  const int a = threadIdx.x;
+  double acc = 0.0;
+  for (int h = 0; h < kHMax; ++h) {
+    double f = 0.0;
+    if (a < Mg && h <= RF) {
+      acc += h == 0 ? Dbar[a * Mg + R] : Dbar[a * Mg + R - h] + Dbar[a * Mg + R + h];
+      f = acc;
+    }
+    FB[h * kN + a] = (float)f;
+  }
+}
+
+__device__ __forceinline__ int isqrt_int(int v) {
+  int h = (int)sqrtf((float)v);
+  while (h * h > v) --h;
+  while ((h + 1) * (h + 1) <= v) ++h;
+  return h;
+}
+
+// one CTA per slab x: partials of its pair in order, + Dbar term, eps on the basis sphere,
+// FP64 sum of eps over the Fermi sphere
+__global__ void k_tc_slab_finalize(const float* part, const float* FB, int R, int RF, int S,
+                                   int units, int grid, int maxseg, int periodic, double pref,
+                                   float* eps, double* slab_ex) {
+  const int x = blockIdx.x, Mg = 2 * R + 1;
+  const int p = x >> 1, j = x & 1;
+  const int c0 = owner_cta((long long)p * S, units, grid);
+  const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
+  const int dx = x - R, Q = RF * RF - dx * dx;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < Mg * Mg; i += blockDim.x) {
+    const int y = i / Mg, z = i % Mg, dy = y - R, dz = z - R;
+    float sum = 0.0f;
+    for (int k = 0; k < nseg; ++k)
+      sum += part[(((long long)(p * maxseg + k) * 2 + j) * kN + y) * kN + z];
+    if (periodic && Q - dy * dy >= 0) sum += FB[isqrt_int(Q - dy * dy) * kN + z];
+    const int m = dx * dx + dy * dy + dz * dz;
+    const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
+    eps[((long long)x * Mg + y) * Mg + z] = v;
+    if (m <= RF * RF) acc += (double)v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) slab_ex[x] = red[0];
+}
+
+__global__ void k_tc_slab_ex(const double* slab_ex, int Mg, double* Ex, const int* err,
+                             int* status) {
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int x = 0; x < Mg; ++x) tot += slab_ex[x];
+  Ex[0] = 0.5 * tot;
+  Ex[1] = tot;
+  if (status) *status = *err;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+struct TcSlabWs {
+  int grid = 0, units = 0, maxseg = 0, RF_built = -1;
+  uint32_t* FR = nullptr;
+  float* FW = nullptr;
+  float* FB = nullptr;
+  float* part = nullptr;
+  double* slab_ex = nullptr;
+  float* w32 = nullptr;
+  std::vector<void*> allocs;
+};
+
+bool tc_slab_supported(cc_tables t) { return t->Mg > 64 && t->Mg <= 127 && t->p.R <= 63; }
+
+cc_status tc_slab_alloc(cc_tables t, void** out) {
+  *out = nullptr;
+  if (!tc_slab_supported(t)) return CC_OK;
+  TcSlabWs* w = new (std::nothrow) TcSlabWs();
+  if (!w) return CC_ERR_ALLOC;
+  const int S = t->S_eff, pairs = (t->Mg + 1) / 2;
+  w->units = pairs * S;
+  w->grid = std::min(sm_count(), w->units);
+  for (int p = 0; p < pairs; ++p) {
+    const int c0 = owner_cta((long long)p * S, w->units, w->grid);
+    const int c1 = owner_cta((long long)(p + 1) * S - 1, w->units, w->grid);
+    w->maxseg = std::max(w->maxseg, c1 - c0 + 1);
+  }
+  auto alloc = [&](void** p, size_t bytes) -> cc_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      set_last_error("cudaMalloc(tensor-core slab workspace)", e);
+      return CC_ERR_ALLOC;
+    }
+    w->allocs.push_back(*p);
+    t->ws.mx_bytes += bytes;
+    t->device_bytes += bytes;
+    return CC_OK;
+  };
+  cc_status st = CC_OK;
+  if ((st = alloc((void**)&w->FR, sizeof(uint32_t) * S * kN * kHMax)) != CC_OK ||
+      (st = alloc((void**)&w->FW, sizeof(float) * S * kN * kHMax)) != CC_OK ||
+      (st = alloc((void**)&w->FB, sizeof(float) * kN * kHMax)) != CC_OK ||
+      (st = alloc((void**)&w->part, sizeof(float) * 2 * kN * kN * pairs * w->maxseg)) != CC_OK ||
+      (st = alloc((void**)&w->slab_ex, sizeof(double) * kN)) != CC_OK ||
+      (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK) {
+    tc_slab_free(w);
+    return st;
+  }
+  std::vector<float> w32(S);
+  for (int i = 0; i < S; ++i) w32[i] = (float)t->w[t->kept_idx[i]];
+  cudaError_t e = cudaMemcpy(w->w32, w32.data(), sizeof(float) * S, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_last_error("cudaMemcpy(node weights)", e);
+    tc_slab_free(w);
+    return CC_ERR_CUDA;
+  }
+  *out = w;
+  return CC_OK;
+}
+
+void tc_slab_free(void* p) {
+  TcSlabWs* w = reinterpret_cast<TcSlabWs*>(p);
+  if (!w) return;
+  for (void* a : w->allocs) cudaFree(a);
+  delete w;
+}
+
+cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
+                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st) {
+  TcSlabWs* w = reinterpret_cast<TcSlabWs*>(ws);
+  if (!w || !tc_slab_supported(t) || R_F > 63) return CC_ERR_NOTSUPP;
+  const int S = t->S_eff, Mg = t->Mg, R = t->p.R;
+  const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
+  if (w->RF_built != R_F) {
+    k_tc_slab_prep<<<(S * kN + 127) / 128, 128, 0, st>>>(t->d.Tm64, t->d.w64, S, Mg, R, R_F,
+                                                          periodic, w->FR, w->FW);
+    if (periodic) k_tc_slab_dbar<<<1, kN, 0, st>>>(t->d.Dbar64, Mg, R, R_F, w->FB);
+    CC_CUDA(cudaGetLastError());
+    w->RF_built = R_F;
+  }
+  Args a{};
+  a.R = R;
+  a.R_F = R_F;
+  a.Mg = Mg;
+  a.S = S;
+  a.periodic = periodic;
+  a.units = w->units;
+  a.maxseg = w->maxseg;
+  a.FR = w->FR;
+  a.FW = w->FW;
+  a.w = w->w32;
+  a.part = w->part;
+  a.err = err;
+  a.stall_test = stall_test;
+  static bool attr = false;
+  if (!attr) {
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes));
+    attr = true;
+  }
+  const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(map_hi);
+  const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(map_lo);
+  k_tc_slab<<<w->grid, kThreads, kSmemBytes, st>>>(mh, ml, a);
+  k_tc_slab_finalize<<<Mg, 256, 0, st>>>(w->part, w->FB, R, R_F, S, w->units, w->grid,
+                                         w->maxseg, periodic, t->pref, eps, w->slab_ex);
+  k_tc_slab_ex<<<1, 32, 0, st>>>(w->slab_ex, Mg, Ex, err, err + 1);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+}  // namespace cc

@@ -131,3 +131,81 @@ def test_bounded_wait_reports_timeout_and_context_survives(dev):
     a, w = oracle_nodes(R, CFG2["S"])
     assert rel_err(_basis_values(R, grid), ox.eps_separable(R, R_F, L, a, w)) < TOL_MIXED
     t.free()
+
+
+def _variant(v):
+    import paper_1502_08043_gb300 as cc
+    assert cc.lib().cc_set_mixed_variant(v) == 0
+
+
+@pytest.mark.parametrize("kernel", ["periodic", "box"])
+def test_slab_kernel_vs_chain_and_oracle(dev, kernel):
+    """The fused tensor-core slab kernel (grid side 67) element by element against the
+    five-launch step chain on the same handle, and both against the FP64 oracle on sampled
+    basis functions and on E_x."""
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = 33, 30.0, 21
+    if kernel == "periodic":
+        t = cc.build_tables("periodic", R=R, L=L, S=64)
+        a, w = oracle_nodes(R, 64)
+    else:
+        a, w, _ = oq.paper_mesh2(6, 24)
+        t = cc.build_tables("box", R=R, L=L, S=len(a), n_sub=7, q_tail=24)
+    try:
+        _variant(2)
+        g_slab, e_slab = _run(t, R_F, "bf16x3", dev)
+        _variant(1)
+        g_chain, e_chain = _run(t, R_F, "bf16x3", dev)
+    finally:
+        _variant(0)
+    assert np.array_equal(g_slab == 0, g_chain == 0)
+    inside = g_chain != 0
+    assert np.max(np.abs(g_slab[inside] - g_chain[inside]) / np.abs(g_chain[inside])) < TOL_MIXED
+    Nb = ob.count(R)
+    idx = np.unique(np.concatenate([np.random.default_rng(3).integers(0, Nb, 150), [0, Nb - 1]]))
+    C = ox.difference_histogram(R_F, "fft")
+    if kernel == "periodic":
+        ref = ox.eps_separable(R, R_F, L, a, w, k_idx=idx)
+        ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
+    else:
+        ref = ox.eps_box(R, R_F, L, a, w, k_idx=idx)
+        ex_ref = ox.Ex_box(R_F, L, a, w, C)
+    assert rel_err(_basis_values(R, g_slab)[idx], ref) < TOL_MIXED
+    assert abs(e_slab[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
+    assert abs(e_slab[1] - 2 * e_slab[0]) <= 1e-12 * abs(e_slab[1])
+    t.free()
+
+
+def test_slab_kernel_variant_errors(dev):
+    import paper_1502_08043_gb300 as cc
+    L = cc.lib()
+    assert L.cc_set_mixed_variant(3) == 1 and L.cc_set_mixed_variant(-1) == 1
+    t = cc.build_tables("periodic", R=CFG2["R"], L=CFG2["L"], S=CFG2["S"])   # grid side 27
+    try:
+        _variant(2)
+        with pytest.raises(cc.CoulombError) as e:
+            _run(t, CFG2["R_F"], "bf16x3", dev)
+        assert e.value.status == 6
+    finally:
+        _variant(0)
+    t.free()
+
+
+def test_slab_kernel_bounded_wait(dev):
+    """The stall hook on the fused slab kernel: error word 5, context usable afterwards."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    R, L, R_F = 33, 30.0, 21
+    t = cc.build_tables("periodic", R=R, L=L, S=64)
+    Mg = t.info["Mg"]
+    eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+    Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+    g0, e0 = _run(t, R_F, "bf16x3", dev)
+    assert cc.lib().cc_test_stall_next_mixed() == 0
+    cc.exchange_sums(t, R_F, eps, Ex, precision="bf16x3")
+    torch.cuda.synchronize()
+    assert cc.mixed_status(t) == 5
+    assert cc.mixed_status(t) == 0
+    g1, e1 = _run(t, R_F, "bf16x3", dev)
+    assert np.array_equal(g0, g1) and np.array_equal(e0, e1)
+    t.free()

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import coulomb_inputs as ci
-from gpu_common import CFG1, CFG2, CFG5, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes, rel_err
+from gpu_common import CFG1, CFG2, CFG3, CFG5, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes, rel_err
 from oracle import basis as ob
 from oracle import coulomb as oc
 from oracle import quadrature as oq
@@ -32,7 +32,12 @@ def _run(t, q_np, lookup, dtype, dev, fmt="ids"):
     return out.cpu().numpy(), cnt.cpu().numpy()
 
 
-@pytest.mark.parametrize("fmt", ["ids", "vec"])
+def as_ids16(q):
+    """uint16 bit patterns of int32 ids (negative ids wrap to large, out-of-range ones)."""
+    return (np.asarray(q, dtype=np.int64) & 0xFFFF).astype(np.uint16).view(np.int16)
+
+
+@pytest.mark.parametrize("fmt", ["ids", "vec", "ids16"])
 @pytest.mark.parametrize("lookup", ["separable", "collapsed"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_small_box_all_paths(dev, fmt, lookup, prec):
@@ -47,7 +52,9 @@ def test_small_box_all_paths(dev, fmt, lookup, prec):
     q[7::12011, 0] = -3
     ref, cnt_ref = orc.reconstruct(q, R, L, "separable", a=a, w=w)
     exact, _ = orc.reconstruct(q, R, L, "exact")
-    qin = q if fmt == "ids" else ci.quads_as_vectors(np.clip(q, 0, len(B) - 1), B)
+    qin = {"ids": q, "ids16": as_ids16(q)}.get(fmt)
+    if qin is None:
+        qin = ci.quads_as_vectors(np.clip(q, 0, len(B) - 1), B)
     if fmt == "vec":   # out-of-range vectors instead of out-of-range ids
         bad = np.any((q < 0) | (q >= len(B)), axis=1)
         qin[bad, 1, 0] = R + 1
@@ -60,7 +67,7 @@ def test_small_box_all_paths(dev, fmt, lookup, prec):
     tol = TOL_FP64 if prec == "fp64" else TOL_FP32
     assert rel_err(got, ref) < tol
     # stated method error of the S = 32 mesh against the exact 1/(pi L |q|^2)
-    assert rel_err(got, exact if fmt == "ids" else ref) < 2e-5
+    assert rel_err(got, ref if fmt == "vec" else exact) < 2e-5
     t.free()
 
 
@@ -73,10 +80,11 @@ def test_ragged_sizes_paper_scale(dev, n):
     import torch
     ref, cnt_ref = orc.reconstruct(q, R, L, "separable", a=a, w=w)
     for lookup in ("separable", "collapsed"):
-        got, cnt = _run(t, q, lookup, torch.float32, dev)
-        assert np.array_equal(cnt, cnt_ref)
-        assert np.array_equal(got == 0, ref == 0)
-        assert rel_err(got, ref) < TOL_FP32
+        for qin in (q, as_ids16(q)):
+            got, cnt = _run(t, qin, lookup, torch.float32, dev)
+            assert np.array_equal(cnt, cnt_ref)
+            assert np.array_equal(got == 0, ref == 0)
+            assert rel_err(got, ref) < TOL_FP32
     t.free()
 
 
@@ -97,16 +105,20 @@ def _full_size(dev, cfg, n, sample):
     assert np.array_equal(q[torch.from_numpy(idx).to(dev)].cpu().numpy(), q_np)
     ref, _ = orc.reconstruct(q_np, R, L, "separable", a=a, w=w)
     out = torch.empty(n, dtype=torch.float32, device=dev)
-    for lookup in ("separable", "collapsed"):
-        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
-        out.fill_(float("nan"))
-        cc.reconstruct_integrals(t, q, out, lookup=lookup, counters=cnt)
-        assert cnt.cpu().tolist() == [0, n_q0, 0]
-        got = out[torch.from_numpy(idx).to(dev)].cpu().numpy()
-        assert np.array_equal(got == 0, ref == 0)
-        assert rel_err(got, ref) < TOL_FP32
-        assert not torch.isnan(out).any().item()
-    del q, out
+    forms = [q]
+    if t.info["Nb"] <= 65536:   # the 8-byte uint16 form, as the bench step reads it
+        forms.append(torch.where(q >= 32768, q - 65536, q).to(torch.int16))
+    for qf in forms:
+        for lookup in ("separable", "collapsed"):
+            cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+            out.fill_(float("nan"))
+            cc.reconstruct_integrals(t, qf, out, lookup=lookup, counters=cnt)
+            assert cnt.cpu().tolist() == [0, n_q0, 0]
+            got = out[torch.from_numpy(idx).to(dev)].cpu().numpy()
+            assert np.array_equal(got == 0, ref == 0)
+            assert rel_err(got, ref) < TOL_FP32
+            assert not torch.isnan(out).any().item()
+    del q, forms, out
     t.free()
 
 
@@ -188,6 +200,20 @@ def test_unsupported_and_bad_args(dev):
                                       None, None) == 6
     # misaligned quadruple buffer
     assert L.cc_reconstruct_integrals(t.handle, q.data_ptr() + 4, 3, 0, 0, 1, out.data_ptr(),
+                                      None, None) == 1
+    # uint16 ids: 8-byte alignment; a basis above 65536 functions is out of range
+    q16 = torch.zeros((4, 4), dtype=torch.int16, device=dev)
+    assert L.cc_reconstruct_integrals(t.handle, q16.data_ptr() + 2, 3, 2, 0, 1, out.data_ptr(),
+                                      None, None) == 1
+    assert L.cc_reconstruct_integrals(t.handle, q16.data_ptr() + 8, 3, 2, 0, 1, out.data_ptr(),
+                                      None, None) == 0
+    t3 = _tables(CFG3)
+    assert t3.info["Nb"] > 65536
+    assert L.cc_reconstruct_integrals(t3.handle, q16.data_ptr(), 4, 2, 0, 1, out.data_ptr(),
+                                      None, None) == 2
+    t3.free()
+    # unknown format
+    assert L.cc_reconstruct_integrals(t.handle, q.data_ptr(), 4, 3, 0, 1, out.data_ptr(),
                                       None, None) == 1
     # rows beyond the basis
     assert L.cc_pair_matrix(t.handle, 250, 10, 0, 1, out.data_ptr(), None) == 1
