@@ -13,7 +13,7 @@
 // One CTA per SM walks a contiguous run of work units (slab pair, node).  For every unit:
 //   MMA1  U_j = T_s R_{s,x_j}                 (A = T_s, B = R from shared memory)
 //   epi   U_j <- w_s U_j + w_s A_{s,x_j}, split into bf16 hi + lo, written back into the
-//         same tensor-memory columns (each 32-column chunk becomes 16 hi + 16 lo columns)
+//         same tensor-memory columns (each 16-column piece becomes 8 hi + 8 lo columns)
 //   MMA2  E_j += U_j T_s                      (A = U_j from tensor memory, B = T_s)
 // for the two slabs x_0 = 2p, x_1 = 2p + 1 of the pair, issued in the order
 //   MMA1(i, 0), MMA2(i-1, 1), MMA1(i, 1), MMA2(i, 0)
@@ -55,10 +55,16 @@ constexpr uint32_t kPlane = 128 * 64 * 2;   // one 64-wide K block of one plane:
 constexpr uint32_t kOp = 4 * kPlane;        // 128 x 128 operand, hi + lo: 64 KB
 constexpr uint32_t kOffT = 0;               // two T_s buffers
 constexpr uint32_t kOffR = 2 * kOp;         // the R operand
-constexpr uint32_t kOffIsq = 3 * kOp;       // floor(sqrt(v)), v < 4096
-constexpr uint32_t kOffBar = kOffIsq + 4096;
+// the row of F_s of a build, replicated 32 times so that lane l reads its copy from bank
+// l (entry h of copy l at word 32 h + l): conflict-free gathers; two of them alternate
+constexpr uint32_t kFtabBytes = kHMax * 32 * 4;  // 8 KB
+constexpr uint32_t kOffFtab = 3 * kOp;
+constexpr uint32_t kOffBar = kOffFtab + 2 * kFtabBytes;  // mbarriers, tensor-memory slot
 constexpr int kNumBars = 16;
-constexpr uint32_t kSmemBytes = kOffBar + 8 * kNumBars + 16 + 1024;
+constexpr uint32_t kOffIsq = kOffBar + 8 * kNumBars + 16;  // floor(sqrt(v)), v <= R_F^2
+__host__ __device__ constexpr uint32_t slab_smem_bytes(int R_F) {
+  return kOffIsq + (((uint32_t)(R_F * R_F + 1) + 15u) & ~15u) + 1024u;
+}
 
 struct Args {
   int R, R_F, Mg, S, periodic;
@@ -103,6 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto a2full = [&](int j) { return bar + 8u * (8 + j); };   // 8, 9
   const uint32_t efull = bar + 8u * 10, edone = bar + 8u * 11;
   const uint32_t never = bar + 8u * 12, drain = bar + 8u * 13;
+  auto ftfull = [&](int k) { return bar + 8u * (14 + k); };  // 14, 15
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
   __shared__ volatile int s_abort;
 
@@ -122,6 +129,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(edone, kEpiWarps);
     mbar_init(never, 1);
     mbar_init(drain, 1);
+    mbar_init(ftfull(0), kBldWarps);
+    mbar_init(ftfull(1), kBldWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // isqrt table and a zero R operand (the builders only ever write the square
   // |y - R|, |z - R| <= R_F; the rest of the operand stays zero)
-  for (int v = tid; v < 4096; v += kThreads) {
+  for (int v = tid; v <= RF * RF; v += kThreads) {
     int h = (int)sqrtf((float)v);
     while (h * h > v) --h;
     while ((h + 1) * (h + 1) <= v) ++h;
@@ -199,12 +208,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {  // K step m covers z = 16 m .. 16 m + 15
           const int kb = m >> 2, k = m & 3;
-          const uint32_t aH = tmem + (uint32_t)(j * 128 + 32 * (m >> 1) + 8 * (m & 1));
+          const uint32_t aH = tmem + (uint32_t)(j * 128 + 16 * m);  // hi; lo 8 columns on
           const uint64_t dB = sdesc(tb + kb * 2 * kPlane) + (uint64_t)(2 * k);
           const uint64_t dBl = sdesc(tb + kb * 2 * kPlane + kPlane) + (uint64_t)(2 * k);
           mma_f16_ts(d, aH, dB, idesc, (first && m == 0) ? 0u : 1u);
           mma_f16_ts(d, aH, dBl, idesc, 1u);
-          mma_f16_ts(d, aH + 16u, dB, idesc, 1u);
+          mma_f16_ts(d, aH + 8u, dB, idesc, 1u);
         }
       };
       bool ok = !s_abort;
@@ -267,46 +276,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= kEpiWarps) {
     // ---------------- R operand builders (warps 8-13)
-    const int bt = tid - 32 * kEpiWarps;
-    const int zlo = R - RF, nz = 2 * RF + 1;
+    // R_{s,x}[y][z] = F_s[x][h(y, z)]: the x line of the sphere at (y, z) does not depend
+    // on x, only the row of F_s does, and rows z and 2R - z of the operand are equal.  A
+    // builder thread always forms the same 16-byte chunks (row z <= R of the square
+    // |y - R|, |z - R| <= R_F, 8 consecutive y) and stores each into both mirror rows, so
+    // it keeps their h values in registers (packed bytes) from the start.  The row of F_s
+    // of a build is written by all builder warps into a replicated table (copy l in bank
+    // l) and every element is one conflict-free shared-memory load away.
+    const int bt = tid - 32 * kEpiWarps, bw = warp - kEpiWarps;
+    const int zlo = R - RF, nzh = RF + 1;
     const int clo = (R - RF) >> 3, nc = ((R + RF) >> 3) - clo + 1;
-    const int tasks = nz * nc;
+    const int tasks = nzh * nc;  // <= 64 x 16 = 1024 = 5.3 x 192
+    constexpr int kMaxTasks = 6;
+    uint32_t hb[kMaxTasks][2];
+#pragma unroll
+    for (int k = 0; k < kMaxTasks; ++k) {
+      const int t = bt + k * kBldThreads;
+      hb[k][0] = hb[k][1] = 0xffffffffu;
+      if (t < tasks) {
+        const int z = zlo + t / nc, c = clo + t % nc, dz = z - R;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int dy = 8 * c + e - R;
+          const int q = RF * RF - dy * dy - dz * dz;
+          const uint32_t h = q >= 0 ? (uint32_t)isq[q] : 0xffu;
+          hb[k][e >> 2] = (hb[k][e >> 2] & ~(0xffu << (8 * (e & 3)))) | (h << (8 * (e & 3)));
+        }
+      }
+    }
+    auto frow = [&](long long u, int j) {
+      return g.FR + ((long long)(u % S) * kN + 2 * (u / S) + j) * kHMax;
+    };
+    // this warp fills entries h = hw0 .. hw0 + 10 (11 per warp, 6 warps cover 64)
+    const int hw0 = 11 * bw;
+    uint32_t nf0 = __ldg(frow(u0, 0) + lane), nf1 = __ldg(frow(u0, 0) + lane + 32);
     uint32_t r = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u) {
-      const long long p = u / S;
-      const int s = (int)(u % S);
       for (int j = 0; j < 2 && ok; ++j, ++r) {
-        ok = mbar_wait(rfree, (r & 1u) ^ 1u, g.err, 21, &s_abort);
-        if (!ok) break;
-        // R_{s,x}[y][z] = F_s[x][h(y, z)]: the x line of the sphere at (y, z) does not
-        // depend on x, only the row of F_s does
-        const int x = (int)(2 * p + j);
-        const int Q = RF * RF;
-        const uint32_t* Fx = g.FR + ((long long)s * kN + x) * kHMax;
-        for (int t = bt; t < tasks; t += kBldThreads) {
-          const int z = zlo + t / nc, c = clo + t % nc;
-          const int dz = z - R, q2 = Q - dz * dz;
-          uint32_t v[8];
+        const uint32_t f0 = nf0, f1 = nf1;
+        const long long un = j == 0 ? u : u + 1;
+        if (un < u1) {  // the next build's row
+          nf0 = __ldg(frow(un, j ^ 1) + lane);
+          nf1 = __ldg(frow(un, j ^ 1) + lane + 32);
+        }
+        // every warp has finished build r - 2, so table (r & 1) is free
+        uint32_t* ft = reinterpret_cast<uint32_t*>(gb + kOffFtab + (r & 1u) * kFtabBytes);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int dy = 8 * c + e - R;
-            const int q = q2 - dy * dy;
-            v[e] = q >= 0 ? __ldg(Fx + isq[q]) : 0u;
+        for (int i = 0; i < 11; ++i) {
+          const int h = hw0 + i;
+          const uint32_t a = __shfl_sync(0xffffffffu, f0, h & 31);
+          const uint32_t b = __shfl_sync(0xffffffffu, f1, h & 31);
+          if (h < kHMax) ft[32 * h + lane] = h < 32 ? a : b;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ftfull(r & 1u));
+        ok = mbar_wait(ftfull(r & 1u), (r >> 1) & 1u, g.err, 22, &s_abort) &&
+             mbar_wait(rfree, (r & 1u) ^ 1u, g.err, 21, &s_abort);
+        if (!ok) break;
+#pragma unroll
+        for (int k = 0; k < kMaxTasks; ++k) {
+          const int t = bt + k * kBldThreads;
+          if (k * kBldThreads >= tasks) break;  // warp-uniform
+          if (t < tasks) {
+            uint32_t v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const uint32_t h = (hb[k][e >> 2] >> (8 * (e & 3))) & 0xffu;
+              v[e] = h == 0xffu ? 0u : ft[32 * h + lane];
+            }
+            const int z = zlo + t / nc, c = clo + t % nc;
+            uint4 hi, lo;
+            hi.x = __byte_perm(v[0], v[1], 0x5410);
+            hi.y = __byte_perm(v[2], v[3], 0x5410);
+            hi.z = __byte_perm(v[4], v[5], 0x5410);
+            hi.w = __byte_perm(v[6], v[7], 0x5410);
+            lo.x = __byte_perm(v[0], v[1], 0x7632);
+            lo.y = __byte_perm(v[2], v[3], 0x7632);
+            lo.z = __byte_perm(v[4], v[5], 0x7632);
+            lo.w = __byte_perm(v[6], v[7], 0x7632);
+            const uint32_t kb = (uint32_t)(c >> 3) * 2 * kPlane;
+            const int zm = 2 * R - z;
+            const uint32_t off = kOffR + kb + (uint32_t)z * 128u +
+                                 ((uint32_t)((c & 7) ^ (z & 7)) << 4);
+            *reinterpret_cast<uint4*>(gb + off) = hi;
+            *reinterpret_cast<uint4*>(gb + off + kPlane) = lo;
+            if (zm != z) {
+              const uint32_t offm = kOffR + kb + (uint32_t)zm * 128u +
+                                    ((uint32_t)((c & 7) ^ (zm & 7)) << 4);
+              *reinterpret_cast<uint4*>(gb + offm) = hi;
+              *reinterpret_cast<uint4*>(gb + offm + kPlane) = lo;
+            }
           }
-          uint4 hi, lo;
-          hi.x = __byte_perm(v[0], v[1], 0x5410);
-          hi.y = __byte_perm(v[2], v[3], 0x5410);
-          hi.z = __byte_perm(v[4], v[5], 0x5410);
-          hi.w = __byte_perm(v[6], v[7], 0x5410);
-          lo.x = __byte_perm(v[0], v[1], 0x7632);
-          lo.y = __byte_perm(v[2], v[3], 0x7632);
-          lo.z = __byte_perm(v[4], v[5], 0x7632);
-          lo.w = __byte_perm(v[6], v[7], 0x7632);
-          const uint32_t off = kOffR + (uint32_t)(c >> 3) * 2 * kPlane + (uint32_t)z * 128u +
-                               ((uint32_t)((c & 7) ^ (z & 7)) << 4);
-          *reinterpret_cast<uint4*>(gb + off) = hi;
-          *reinterpret_cast<uint4*>(gb + off + kPlane) = lo;
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -324,39 +385,67 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (long long u = u0; u < u1 && ok;) {
       const long long p = u / S;
       const long long ue = u1 < (p + 1) * S ? u1 : (p + 1) * S;
+      // h(x_j, z) for the columns z = 32 cc + lane of this warp's two chunks (fixed for the
+      // whole pair; broadcast by shuffle per column), -1 outside the sphere
+      int hz[2][2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int dx = (int)(2 * p + j) - R, dz = 32 * (2 * half + k) + lane - R;
+          const int q = RF * RF - dx * dx - dz * dz;
+          hz[j][k] = q >= 0 ? (int)isq[q] : -1;
+        }
       for (; u < ue && ok; ++u, ++n) {
         const int s = (int)(u % S);
         const float ws = g.w[s];
         const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
+        if (g.periodic && u + 1 < u1) {
+          // the next unit's A-term table (4 lines per h) into L1 ahead of its use
+          const int line = tid;  // 256 epilogue threads, (R_F + 1) * 4 <= 256 lines
+          if (line < (RF + 1) * 4) {
+            const float* nx = g.FW + (long long)((u + 1) % S) * kHMax * kN + line * 32;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
+          }
+        }
         for (int j = 0; j < 2; ++j) {
+          // the A-term values of this warp's 64 columns, requested before the MMA result is
+          // waited for (their L2 latency hides behind the wait)
+          float a[2][32];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int hzk = j == 0 ? hz[0][k] : hz[1][k];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int h = __shfl_sync(0xffffffffu, hzk, e);
+              a[k][e] = (g.periodic && h >= 0) ? __ldg(FWs + h * kN) : 0.0f;
+            }
+          }
           ok = mbar_wait(d1full(j), n & 1u, g.err, 31, &s_abort);
           if (!ok) break;
           tc_fence_after();
-          const int dx = (int)(2 * p + j) - R;
-          const int Q = RF * RF - dx * dx;
-#pragma unroll 1
-          for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-            const uint32_t ta = tmem + lane_off + (uint32_t)(j * 128 + 32 * cc);
-            uint32_t v[32];
-            tmem_ld32(ta, v);
-            uint32_t hi[16], lo[16];
+          // in place, 16 columns at a time: FP32 U of z = 16 m .. 16 m + 15 in columns
+          // 16 m .. 16 m + 15 becomes 8 columns of bf16 hi pairs followed by 8 of lo pairs
 #pragma unroll
-            for (int e = 0; e < 32; e += 2) {
-              float a0 = 0.0f, a1 = 0.0f;
-              if (g.periodic) {
-                const int dz0 = 32 * cc + e - R, dz1 = dz0 + 1;
-                const int q0 = Q - dz0 * dz0, q1 = Q - dz1 * dz1;
-                if (q0 >= 0) a0 = __ldg(FWs + (int)isq[q0] * kN);
-                if (q1 >= 0) a1 = __ldg(FWs + (int)isq[q1] * kN);
+          for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int sub = 0; sub < 2; ++sub) {
+              const uint32_t ta = tmem + lane_off +
+                                  (uint32_t)(j * 128 + 32 * (2 * half + k) + 16 * sub);
+              uint32_t v[16];
+              tmem_ld16(ta, v);
+              uint32_t hi[8], lo[8];
+#pragma unroll
+              for (int e = 0; e < 16; e += 2) {
+                const float x0 = fmaf(__uint_as_float(v[e]), ws, a[k][16 * sub + e]);
+                const float x1 = fmaf(__uint_as_float(v[e + 1]), ws, a[k][16 * sub + e + 1]);
+                const uint32_t h = pack_bf16x2(x0, x1);
+                hi[e >> 1] = h;
+                lo[e >> 1] = pack_bf16x2(x0 - bf16_lo_f(h), x1 - bf16_hi_f(h));
               }
-              const float x0 = fmaf(__uint_as_float(v[e]), ws, a0);
-              const float x1 = fmaf(__uint_as_float(v[e + 1]), ws, a1);
-              const uint32_t h = pack_bf16x2(x0, x1);
-              hi[e >> 1] = h;
-              lo[e >> 1] = pack_bf16x2(x0 - bf16_lo_f(h), x1 - bf16_hi_f(h));
+              tmem_st8(ta, hi);
+              tmem_st8(ta + 8u, lo);
             }
-            tmem_st16(ta, hi);
-            tmem_st16(ta + 16u, lo);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -592,15 +681,16 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   a.part = w->part;
   a.err = err;
   a.stall_test = stall_test;
-  static bool attr = false;
-  if (!attr) {
+  const uint32_t smem = slab_smem_bytes(R_F);
+  static uint32_t attr = 0;
+  if (attr < smem) {
     CC_CUDA(cudaFuncSetAttribute(k_tc_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes));
-    attr = true;
+                                 (int)slab_smem_bytes(63)));
+    attr = slab_smem_bytes(63);
   }
   const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(map_hi);
   const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(map_lo);
-  k_tc_slab<<<w->grid, kThreads, kSmemBytes, st>>>(mh, ml, a);
+  k_tc_slab<<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   k_tc_slab_finalize<<<Mg, 256, 0, st>>>(w->part, w->FB, R, R_F, S, w->units, w->grid,
                                          w->maxseg, periodic, t->pref, eps, w->slab_ex);
   k_tc_slab_ex<<<1, 32, 0, st>>>(w->slab_ex, Mg, Ex, err, err + 1);
