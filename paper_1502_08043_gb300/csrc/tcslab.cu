@@ -156,6 +156,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // U and R vanish outside the band [R - R_F, R + R_F] of z (and of y for R): the products
+  // run over the 16-aligned band [zs, ze) only (U column n holds z = zs + n)
+  const int zs = (R - RF) & ~15, ze = (R + RF + 16) & ~15, nact = ze - zs;
   const long long u0 = (long long)blockIdx.x * g.units / gridDim.x;
   const long long u1 = (long long)(blockIdx.x + 1) * g.units / gridDim.x;
 
@@ -183,37 +186,43 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                 ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
+      const uint32_t idesc1 = idesc0 | ((uint32_t)(nact >> 3) << 17);  // N = band width
+      const uint32_t idesc2 = idesc0 | ((uint32_t)(kN >> 3) << 17);    // N = 128
       if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
       uint32_t n = 0, r = 0, segc = 0;
+      // descriptors as base + constant: the start-address field holds address / 16, so a
+      // byte offset o (all addresses < 256 KB) adds o / 16
+      const int ms = zs >> 4, me = ze >> 4;
+      const uint64_t dR = sdesc(base + kOffR + zs * 128u);  // B rows z = zs ..
       auto mma1 = [&](uint32_t tb, int j) {
         const uint32_t d = tmem + (uint32_t)(j * 128);
+        const uint64_t dT = sdesc(tb);
 #pragma unroll
-        for (int kb = 0; kb < 2; ++kb) {
-          const uint64_t dA = sdesc(tb + kb * 2 * kPlane), dAl = sdesc(tb + kb * 2 * kPlane + kPlane);
-          const uint64_t dB = sdesc(base + kOffR + kb * 2 * kPlane);
-          const uint64_t dBl = sdesc(base + kOffR + kb * 2 * kPlane + kPlane);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint64_t adv = (uint64_t)(2 * k);  // 32 bytes per K = 16 step
-            mma_f16(d, dA + adv, dB + adv, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-            mma_f16(d, dA + adv, dBl + adv, idesc, 1u);
-            mma_f16(d, dAl + adv, dB + adv, idesc, 1u);
-          }
+        for (int m = 0; m < 8; ++m) {  // K step m covers y = 16 m .. 16 m + 15
+          if (m < ms || m >= me) continue;
+          constexpr uint64_t kPl = kPlane >> 4;
+          const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
+          const uint32_t acc = m > ms ? 1u : 0u;
+          mma_f16(d, dT + o, dR + o, idesc1, acc);
+          mma_f16(d, dT + o, dR + o + kPl, idesc1, 1u);
+          mma_f16(d, dT + o + kPl, dR + o, idesc1, 1u);
         }
       };
       auto mma2 = [&](uint32_t tb, int j, bool first) {
         const uint32_t d = tmem + 256u + (uint32_t)(j * 128);
+        const uint32_t a0 = tmem + (uint32_t)(j * 128) - (uint32_t)(16 * ms);
+        const uint64_t dT = sdesc(tb);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {  // K step m covers z = 16 m .. 16 m + 15
-          const int kb = m >> 2, k = m & 3;
-          const uint32_t aH = tmem + (uint32_t)(j * 128 + 16 * m);  // hi; lo 8 columns on
-          const uint64_t dB = sdesc(tb + kb * 2 * kPlane) + (uint64_t)(2 * k);
-          const uint64_t dBl = sdesc(tb + kb * 2 * kPlane + kPlane) + (uint64_t)(2 * k);
-          mma_f16_ts(d, aH, dB, idesc, (first && m == 0) ? 0u : 1u);
-          mma_f16_ts(d, aH, dBl, idesc, 1u);
-          mma_f16_ts(d, aH + 8u, dB, idesc, 1u);
+          if (m < ms || m >= me) continue;
+          constexpr uint64_t kPl = kPlane >> 4;
+          const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
+          // U piece of z = 16 m ..: columns 16 (m - zs / 16) .., 8 hi then 8 lo
+          const uint32_t aH = a0 + (uint32_t)(16 * m);
+          mma_f16_ts(d, aH, dT + o, idesc2, (first && m == ms) ? 0u : 1u);
+          mma_f16_ts(d, aH, dT + o + kPl, idesc2, 1u);
+          mma_f16_ts(d, aH + 8u, dT + o, idesc2, 1u);
         }
       };
       bool ok = !s_abort;
@@ -392,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const int dx = (int)(2 * p + j) - R, dz = 32 * (2 * half + k) + lane - R;
+          const int dx = (int)(2 * p + j) - R, dz = zs + 32 * (2 * half + k) + lane - R;
           const int q = RF * RF - dx * dx - dz * dz;
           hz[j][k] = q >= 0 ? (int)isq[q] : -1;
         }
@@ -424,12 +433,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = mbar_wait(d1full(j), n & 1u, g.err, 31, &s_abort);
           if (!ok) break;
           tc_fence_after();
-          // in place, 16 columns at a time: FP32 U of z = 16 m .. 16 m + 15 in columns
+          // in place, 16 columns at a time: FP32 U of the piece z = zs + 16 m .. in columns
           // 16 m .. 16 m + 15 becomes 8 columns of bf16 hi pairs followed by 8 of lo pairs
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
+              if (32 * (2 * half + k) + 16 * sub >= nact) continue;  // beyond the band
               const uint32_t ta = tmem + lane_off +
                                   (uint32_t)(j * 128 + 32 * (2 * half + k) + 16 * sub);
               uint32_t v[16];
@@ -533,46 +543,58 @@ __device__ __forceinline__ int isqrt_int(int v) {
   return h;
 }
 
-// one CTA per slab x: partials of its pair in order, + Dbar term, eps on the basis sphere,
-// FP64 sum of eps over the Fermi sphere
-__global__ void k_tc_slab_finalize(const float* part, const float* FB, int R, int RF, int S,
-                                   int units, int grid, int maxseg, int periodic, double pref,
-                                   float* eps, double* slab_ex) {
-  const int x = blockIdx.x, Mg = 2 * R + 1;
+// one warp per grid row (x, y), four z per lane: partials of the pair in order, + Dbar
+// term, eps on the basis sphere; FP64 sum of the row's eps over the Fermi sphere (fixed
+// butterfly order)
+__global__ void __launch_bounds__(256)
+    k_tc_slab_finalize(const float* part, const float* FB, int R, int RF, int S, int units,
+                       int grid, int maxseg, int periodic, double pref, float* eps,
+                       double* row_ex) {
+  const int Mg = 2 * R + 1;
+  const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (y >= Mg) return;  // whole warps
   const int p = x >> 1, j = x & 1;
   const int c0 = owner_cta((long long)p * S, units, grid);
   const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
-  const int dx = x - R, Q = RF * RF - dx * dx;
+  const int dx = x - R, dy = y - R;
+  const int qb = RF * RF - dx * dx - dy * dy;  // z line at (x, y) for the Dbar term
+  const float* fb = (periodic && qb >= 0) ? FB + isqrt_int(qb) * kN : nullptr;
+  const float* pp = part + (((long long)p * maxseg * 2 + j) * kN + y) * kN;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < Mg * Mg; i += blockDim.x) {
-    const int y = i / Mg, z = i % Mg, dy = y - R, dz = z - R;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int z = lane + 32 * i;
+    if (z >= Mg) continue;
     float sum = 0.0f;
-    for (int k = 0; k < nseg; ++k)
-      sum += part[(((long long)(p * maxseg + k) * 2 + j) * kN + y) * kN + z];
-    if (periodic && Q - dy * dy >= 0) sum += FB[isqrt_int(Q - dy * dy) * kN + z];
-    const int m = dx * dx + dy * dy + dz * dz;
+    for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 2 * kN * kN + z);
+    if (fb) sum += __ldg(fb + z);
+    const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
     const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
     eps[((long long)x * Mg + y) * Mg + z] = v;
     if (m <= RF * RF) acc += (double)v;
   }
-  __shared__ double red[256];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
+}
+
+// E_x from the Mg^2 row sums, fixed order: thread t adds rows t, t + 1024, ..., then a tree
+__global__ void __launch_bounds__(1024)
+    k_tc_slab_ex(const double* row_ex, int n, double* Ex, const int* err, int* status) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) acc += row_ex[i];
   red[threadIdx.x] = acc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = 512; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) slab_ex[x] = red[0];
-}
-
-__global__ void k_tc_slab_ex(const double* slab_ex, int Mg, double* Ex, const int* err,
-                             int* status) {
-  if (threadIdx.x != 0) return;
-  double tot = 0.0;
-  for (int x = 0; x < Mg; ++x) tot += slab_ex[x];
-  Ex[0] = 0.5 * tot;
-  Ex[1] = tot;
-  if (status) *status = *err;
+  if (threadIdx.x == 0) {
+    Ex[0] = 0.5 * red[0];
+    Ex[1] = red[0];
+    if (status) *status = *err;
+  }
 }
 
 int sm_count() {
@@ -594,7 +616,7 @@ struct TcSlabWs {
   float* FW = nullptr;
   float* FB = nullptr;
   float* part = nullptr;
-  double* slab_ex = nullptr;
+  double* row_ex = nullptr;
   float* w32 = nullptr;
   std::vector<void*> allocs;
 };
@@ -630,7 +652,7 @@ cc_status tc_slab_alloc(cc_tables t, void** out) {
       (st = alloc((void**)&w->FW, sizeof(float) * S * kN * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->FB, sizeof(float) * kN * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->part, sizeof(float) * 2 * kN * kN * pairs * w->maxseg)) != CC_OK ||
-      (st = alloc((void**)&w->slab_ex, sizeof(double) * kN)) != CC_OK ||
+      (st = alloc((void**)&w->row_ex, sizeof(double) * kN * kN)) != CC_OK ||
       (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK) {
     tc_slab_free(w);
     return st;
@@ -691,9 +713,10 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(map_hi);
   const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(map_lo);
   k_tc_slab<<<w->grid, kThreads, smem, st>>>(mh, ml, a);
-  k_tc_slab_finalize<<<Mg, 256, 0, st>>>(w->part, w->FB, R, R_F, S, w->units, w->grid,
-                                         w->maxseg, periodic, t->pref, eps, w->slab_ex);
-  k_tc_slab_ex<<<1, 32, 0, st>>>(w->slab_ex, Mg, Ex, err, err + 1);
+  k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, w->FB, R, R_F, S,
+                                                             w->units, w->grid, w->maxseg,
+                                                             periodic, t->pref, eps, w->row_ex);
+  k_tc_slab_ex<<<1, 1024, 0, st>>>(w->row_ex, Mg * Mg, Ex, err, err + 1);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

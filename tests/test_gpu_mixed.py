@@ -138,13 +138,17 @@ def _variant(v):
     assert cc.lib().cc_set_mixed_variant(v) == 0
 
 
-@pytest.mark.parametrize("kernel", ["periodic", "box"])
-def test_slab_kernel_vs_chain_and_oracle(dev, kernel):
-    """The fused tensor-core slab kernel (grid side 67) element by element against the
-    five-launch step chain on the same handle, and both against the FP64 oracle on sampled
-    basis functions and on E_x."""
+@pytest.mark.parametrize("kernel,R,R_F", [("periodic", 33, 21), ("box", 33, 21),
+                                           ("periodic", 40, 10), ("periodic", 33, 33)],
+                         ids=["periodic-R33-RF21", "box-R33-RF21", "narrow-band-R40-RF10",
+                              "full-band-R33-RF33"])
+def test_slab_kernel_vs_chain_and_oracle(dev, kernel, R, R_F):
+    """The fused tensor-core slab kernel (grid sides 67 and 81; occupied bands of width 21 to
+    67, so the products run over 48, 64 and 80 of the 128 padded columns) element by element
+    against the five-launch step chain on the same handle, and against the FP64 oracle on
+    sampled basis functions and on E_x."""
     import paper_1502_08043_gb300 as cc
-    R, L, R_F = 33, 30.0, 21
+    L = 30.0
     if kernel == "periodic":
         t = cc.build_tables("periodic", R=R, L=L, S=64)
         a, w = oracle_nodes(R, 64)
