@@ -224,12 +224,11 @@ cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
  * later calls are not affected. */
 cc_status cc_test_stall_next_mixed(void);
 
-/* Which bf16x3 form the tensor-core exchange takes (not part of the paper; a diagnostic and
- * tuning switch of this implementation, process-wide): 0 = automatic, 1 = the step chain of
- * five batched GEMM launches (any grid side <= 128), 2 = the fused slab kernel (grid side
- * 65 .. 127 only; smaller grids then return CC_ERR_NOTSUPP).  Automatic takes the fused
- * slab kernel wherever it applies.  The fp16x3 precision always takes the step chain.
- * CC_ERR_ARG for any other value. */
+/* Which bf16x3 form the single-box tensor-core exchange takes (not part of the paper; a
+ * diagnostic and tuning switch of this implementation, process-wide): 0 = automatic (the
+ * fused slab kernel), 1 = the step chain of five batched GEMM launches, 2 = the fused slab
+ * kernel.  Both cover every grid side up to 127.  The fp16x3 precision and the batched
+ * engine always take the step chain.  CC_ERR_ARG for any other value. */
 cc_status cc_set_mixed_variant(int variant);
 
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the

@@ -112,7 +112,8 @@ cc_status mixed_workspace_alloc(cc_tables t);
 void mixed_workspace_free(cc_tables t);
 cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
                          cudaStream_t st);
-// tcslab.cu (fused tensor-core exchange, grid side 65 .. 127, bf16x3)
+cc_status tc_make_map_bf16(void* map, void* ptr, long long rows, int cols, int box_rows);
+// tcslab.cu (fused tensor-core exchange, bf16x3, grid side up to 127)
 bool tc_slab_supported(cc_tables t);
 cc_status tc_slab_alloc(cc_tables t, void** out);
 void tc_slab_free(void* ws);

@@ -1,4 +1,5 @@
-// Fused tensor-core exchange sums for grid sides 65 .. 127 (Np = 128), bf16 hi + lo.
+// Fused tensor-core exchange sums, bf16 hi + lo, any grid side up to 127 (operands padded
+// to 128).
 //
 // Sec. III exchange of the uniform electron gas with the node sum of Sec. II Eq. 14; the
 // periodic kernel uses the D_s = T_s - I split, so with the Fermi-sphere occupation O
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- MMA issuer
       constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
       const uint32_t idesc1 = idesc0 | ((uint32_t)(nact >> 3) << 17);  // N = band width
-      const uint32_t idesc2 = idesc0 | ((uint32_t)(kN >> 3) << 17);    // N = 128
+      // N = the grid side rounded up to 16 (columns z' >= Mg are never read)
+      const uint32_t idesc2 = idesc0 | ((uint32_t)(((g.Mg + 15) & ~15) >> 3) << 17);
       if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
       uint32_t n = 0, r = 0, segc = 0;
       // descriptors as base + constant: the start-address field holds address / 16, so a
@@ -522,6 +524,21 @@ __global__ void k_tc_slab_prep(const double* Tm, const double* w, int S, int Mg,
   }
 }
 
+// T_s as bf16 hi + lo planes padded to 128 x 128 (grids of side <= 64, whose step-chain
+// planes are 64 x 64)
+__global__ void k_tc_slab_tplanes(const double* Tm, int S, int Mg, __nv_bfloat16* hi,
+                                  __nv_bfloat16* lo) {
+  const long long n = (long long)S * kN * kN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / (kN * kN)), a = (int)((i / kN) % kN), c = (int)(i % kN);
+    const double t = (a < Mg && c < Mg) ? Tm[((long long)s * Mg + a) * Mg + c] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)t);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn((float)t - __bfloat162float(h));
+  }
+}
+
 // window sums of Dbar (I x I x Dbar term), FB[h][z'] = sum_{k=R-h}^{R+h} Dbar[z'][k]
 __global__ void k_tc_slab_dbar(const double* Dbar, int Mg, int R, int RF, float* FB) {
   const int a = threadIdx.x;
@@ -618,10 +635,13 @@ struct TcSlabWs {
   float* part = nullptr;
   double* row_ex = nullptr;
   float* w32 = nullptr;
+  // grids of side <= 64: own 128-padded T planes and their maps (else the step chain's)
+  void* T128[2] = {nullptr, nullptr};
+  alignas(64) unsigned char map_hi[128], map_lo[128];
   std::vector<void*> allocs;
 };
 
-bool tc_slab_supported(cc_tables t) { return t->Mg > 64 && t->Mg <= 127 && t->p.R <= 63; }
+bool tc_slab_supported(cc_tables t) { return t->Mg <= 127 && t->p.R <= 63; }
 
 cc_status tc_slab_alloc(cc_tables t, void** out) {
   *out = nullptr;
@@ -656,6 +676,27 @@ cc_status tc_slab_alloc(cc_tables t, void** out) {
       (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK) {
     tc_slab_free(w);
     return st;
+  }
+  if (t->Mg <= 64) {
+    const size_t plane = sizeof(__nv_bfloat16) * (size_t)S * kN * kN;
+    if ((st = alloc(&w->T128[0], plane)) != CC_OK || (st = alloc(&w->T128[1], plane)) != CC_OK) {
+      tc_slab_free(w);
+      return st;
+    }
+    static_assert(sizeof(CUtensorMap) <= 128, "tensor map size");
+    if ((st = tc_make_map_bf16(w->map_hi, w->T128[0], (long long)S * kN, kN, kN)) != CC_OK ||
+        (st = tc_make_map_bf16(w->map_lo, w->T128[1], (long long)S * kN, kN, kN)) != CC_OK) {
+      tc_slab_free(w);
+      return st;
+    }
+    k_tc_slab_tplanes<<<1024, 256>>>(t->d.Tm64, S, t->Mg, (__nv_bfloat16*)w->T128[0],
+                                     (__nv_bfloat16*)w->T128[1]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_last_error("k_tc_slab_tplanes", e);
+      tc_slab_free(w);
+      return CC_ERR_CUDA;
+    }
   }
   std::vector<float> w32(S);
   for (int i = 0; i < S; ++i) w32[i] = (float)t->w[t->kept_idx[i]];
@@ -710,8 +751,10 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
                                  (int)slab_smem_bytes(63)));
     attr = slab_smem_bytes(63);
   }
-  const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(map_hi);
-  const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(map_lo);
+  const CUtensorMap& mh =
+      *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);
+  const CUtensorMap& ml =
+      *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_lo : map_lo);
   k_tc_slab<<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, w->FB, R, R_F, S,
                                                              w->units, w->grid, w->maxseg,

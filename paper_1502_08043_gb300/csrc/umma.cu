@@ -1,6 +1,6 @@
 // Mixed-precision exchange mode products on the 5th-generation tensor cores (tcgen05):
-// the step chain below (fp16x3, bf16x3 at grid side <= 63, the batched engine) and the
-// routing to the fused slab kernel of tcslab.cu (bf16x3, grid side 65 .. 127).
+// the step chain below (fp16x3, the batched engine, and bf16x3 on request) and the routing
+// to the fused slab kernel of tcslab.cu (bf16x3 single boxes, grid side up to 127).
 //
 // Same sums as exchange.cu (Sec. III exchange of the uniform electron gas, node sum of
 // Sec. II Eq. 14 with the D = T - I split for the periodic kernel), reordered so that
@@ -581,6 +581,12 @@ static cc_status make_map(CUtensorMap* m, void* ptr, long long rows, int Np, int
   return CC_OK;
 }
 
+// for tcslab.cu: a 2D bf16 map over [rows][cols], 64-column x box_rows boxes, 128-byte swizzle
+cc_status tc_make_map_bf16(void* map, void* ptr, long long rows, int cols, int box_rows) {
+  CC_TRY(get_encoder());
+  return make_map(reinterpret_cast<CUtensorMap*>(map), ptr, rows, cols, box_rows, true);
+}
+
 static cc_status mx_alloc(cc_tables t, MxWorkspace* w, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -798,23 +804,20 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
     if (w->Np == 64) return run_mixed<64, __half>(t, w, w->hf, R_F, eps, Ex, st);
     return run_mixed<128, __half>(t, w, w->hf, R_F, eps, Ex, st);
   }
-  if (w->Np == 64) {
-    if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
-    return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
-  }
   if (w->slab && g_mixed_variant != 1) {
     const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
     return tc_slab_run(t, w->slab, &w->bf.mTT[0], &w->bf.mTT[1], w->err, stall, R_F, eps, Ex,
                        st);
   }
   if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
+  if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
   return run_mixed<128, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
 }
 
 }  // namespace cc
 
-// Choice between the two bf16x3 forms (automatic: the fused slab kernel wherever it
-// applies, grid side 65 .. 127).
+// Choice between the two bf16x3 forms (automatic: the fused slab kernel, every grid side
+// up to 127).
 extern "C" cc_status cc_set_mixed_variant(int variant) {
   if (variant < 0 || variant > 2) return CC_ERR_ARG;
   __atomic_store_n(&cc::g_mixed_variant, variant, __ATOMIC_RELEASE);
