@@ -119,4 +119,12 @@ cc_status tc_slab_alloc(cc_tables t, void** out);
 void tc_slab_free(void* ws);
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
                       int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st);
+// tcslab_batch.cu: a batch of boxes through the batched form of the slab kernel, over the
+// step chain's concatenated T planes ([rows][Np] bf16; box b's node 0 at row t_row0[b])
+cc_status tc_slab_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
+                               const std::vector<long long>& eps_off, void* tt_hi, void* tt_lo,
+                               long long tt_rows, const std::vector<long long>& t_row0, int Np,
+                               void** out);
+cc_status tc_slab_batch_run(void* p, int* err, float* eps, double* Ex, cudaStream_t st);
+void tc_slab_batch_free(void* p);
 }  // namespace cc

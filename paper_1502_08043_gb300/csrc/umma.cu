@@ -858,6 +858,7 @@ struct MxBatchImpl {
   std::vector<long long*> t123[3], t4;
   std::vector<int> n123, n4;
   std::vector<void*> allocs;
+  void* slab = nullptr;  // the batch through the fused slab kernel (tcslab.cu)
 };
 
 __global__ void k_mxb_occ(int nbox, const int* R, const int* RF, __nv_bfloat16* O,
@@ -932,6 +933,7 @@ static cc_status mxb_upload(MxBatchImpl* m, V** dst, const std::vector<V>& src) 
 void mixed_batch_free(void* p) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return;
+  tc_slab_batch_free(m->slab);
   for (void* q : m->allocs) cudaFree(q);
   delete m;
 }
@@ -1040,6 +1042,10 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
   if (s == CC_OK) s = mxb_upload(m, &m->eps_off_dev, eps_off);
   if (s == CC_OK && cudaMemset(m->err, 0, sizeof(int) * 2) != cudaSuccess) s = CC_ERR_CUDA;
   if (s == CC_OK && cudaDeviceSynchronize() != cudaSuccess) s = CC_ERR_CUDA;
+  // the same boxes through the fused slab kernel, over the concatenated T planes above
+  if (s == CC_OK)
+    s = tc_slab_batch_create(tabs, R_F, eps_off, P.TT[0], P.TT[1], rows_x1, off_x1, Np,
+                             &m->slab);
   if (s != CC_OK) {
     mixed_batch_free(m);
     return s;
@@ -1051,6 +1057,7 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
 cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return CC_ERR_NOTSUPP;
+  if (m->slab && g_mixed_variant != 1) return tc_slab_batch_run(m->slab, m->err, eps, Ex, st);
   constexpr int Np = 64;
   using E = __nv_bfloat16;
   const long long NN = (long long)Np * Np;

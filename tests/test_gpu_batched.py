@@ -129,3 +129,30 @@ def test_mixed_batch_all_boxes(batch):
     B.exchange(eps2, Ex2, precision="bf16x3")
     torch.cuda.synchronize()
     assert torch.equal(eps2, eps) and torch.equal(Ex2, Ex)
+
+
+def test_mixed_batch_slab_kernel_vs_chain(batch):
+    """The bf16x3 batch through the fused slab kernel (the automatic choice) against the same
+    batch through the five-launch step chain, element by element, and E_x of every box."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    dev, boxes, B = batch
+    n = int(B.offsets[-1])
+    eps_s = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+    Ex_s = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
+    B.exchange(eps_s, Ex_s, precision="bf16x3")
+    assert cc.lib().cc_set_mixed_variant(1) == 0
+    try:  # fresh buffers: a graph of its own, captured with the chain
+        eps_c = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+        Ex_c = torch.zeros((B.nbox, 2), dtype=torch.float64, device=dev)
+        B.exchange(eps_c, Ex_c, precision="bf16x3")
+        torch.cuda.synchronize()
+    finally:
+        assert cc.lib().cc_set_mixed_variant(0) == 0
+    s = eps_s.cpu().numpy().astype(np.float64)
+    c = eps_c.cpu().numpy().astype(np.float64)
+    assert not np.isnan(s).any() and np.array_equal(s == 0, c == 0)
+    nz = c != 0
+    assert np.max(np.abs(s[nz] - c[nz]) / np.abs(c[nz])) < 1e-4
+    xs, xc = Ex_s.cpu().numpy(), Ex_c.cpu().numpy()
+    assert np.max(np.abs(xs[:, 0] - xc[:, 0]) / np.abs(xc[:, 0])) < 1e-4
