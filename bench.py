@@ -232,7 +232,7 @@ def run_gpu(args):
         # copy stream while the quadruples come up in chunks on another; each chunk is
         # reconstructed as soon as it has landed and its values follow the pairs down
         # (H2D, compute and D2H overlap; the link carries both directions at once)
-        nchunk = 8
+        nchunk = args.e2e_chunks
         bounds = [n * c // nchunk for c in range(nchunk + 1)]
         up = torch.cuda.Stream(dev)
         down = torch.cuda.Stream(dev)
@@ -553,6 +553,8 @@ def main():
     ap.add_argument("--mixed", action="store_true")
     ap.add_argument("--mixed-launches", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="quadruple chunks the end-to-end step pipelines its copies over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0)
