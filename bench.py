@@ -325,7 +325,8 @@ def run_gpu(args):
                   "pairs_per_s": Nb * Nb / (parts["pairs_ms"] * 1e-3)},
     }
     if rank == 0 and world == 1 and args.mode_products:
-        line["mode_products"] = {n: mode_products(n) for n in args.mode_products.split(",")}
+        line["mode_products"] = {n: mode_products(n, with_fp16=True)
+                                 for n in args.mode_products.split(",")}
     if rank == 0 and world == 1 and not args.no_extras:
         line["batched"] = batched()
         line["large_lookups"] = large_lookups()
@@ -342,11 +343,11 @@ def run_gpu(args):
 MP_CONFIGS = {"precision": (31, 40.0, 96, 20), "large": (63, 60.0, 128, 40)}
 
 
-def mode_products(name, reps=10, oracle_sample=200, with_fp16=False):
+def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
     """Exchange sums of one single-box workload by the plain FP32 mode products and by the
-    bf16x3 tensor-core path: device time per call (CUDA events, inputs resident), useful
-    flop rate 6 Mg^4 S_eff, and the accuracy of both against the FP64 oracle on a seeded
-    sample of basis functions."""
+    bf16x3 and fp16x3 tensor-core paths: device time per call (CUDA events, inputs
+    resident), useful flop rate 6 Mg^4 S_eff, and the accuracy of each against the FP64
+    oracle on a seeded sample of basis functions."""
     import torch
 
     import paper_1502_08043_gb300 as cc
@@ -376,6 +377,8 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=False):
         out[prec + "_ms"] = ms
         out[prec + "_useful_tflops"] = 6.0 * Mg ** 4 * S_eff / (ms * 1e-3) / 1e12
     out["speedup_bf16x3_vs_fp32"] = res["fp32"][0] / res["bf16x3"][0]
+    if with_fp16:
+        out["speedup_fp16x3_vs_fp32"] = res["fp32"][0] / res["fp16x3"][0]
     if oracle_sample:
         from oracle import basis as ob
         from oracle import exchange as ox

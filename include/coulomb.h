@@ -224,11 +224,12 @@ cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
  * later calls are not affected. */
 cc_status cc_test_stall_next_mixed(void);
 
-/* Which bf16x3 form the single-box tensor-core exchange takes (not part of the paper; a
+/* Which form the tensor-core exchange (bf16x3, fp16x3) takes (not part of the paper; a
  * diagnostic and tuning switch of this implementation, process-wide): 0 = automatic (the
  * fused slab kernel), 1 = the step chain of five batched GEMM launches, 2 = the fused slab
- * kernel.  Both cover every grid side up to 127.  The fp16x3 precision and the batched
- * engine always take the step chain.  CC_ERR_ARG for any other value. */
+ * kernel.  Both cover every grid side up to 127; batches (bf16x3) likewise take the batched
+ * form of the slab kernel or, on 1, the chain.  The setting is read when a batch's graph is
+ * captured.  CC_ERR_ARG for any other value. */
 cc_status cc_set_mixed_variant(int variant);
 
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the

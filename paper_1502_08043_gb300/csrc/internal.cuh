@@ -113,12 +113,14 @@ void mixed_workspace_free(cc_tables t);
 cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double* Ex,
                          cudaStream_t st);
 cc_status tc_make_map_bf16(void* map, void* ptr, long long rows, int cols, int box_rows);
+cc_status tc_make_map_16(void* map, void* ptr, long long rows, int cols, int box_rows, bool bf16);
 // tcslab.cu (fused tensor-core exchange, bf16x3, grid side up to 127)
 bool tc_slab_supported(cc_tables t);
 cc_status tc_slab_alloc(cc_tables t, void** out);
 void tc_slab_free(void* ws);
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
-                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st);
+                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
+                      bool half);
 // tcslab_batch.cu: a batch of boxes through the batched form of the slab kernel, over the
 // step chain's concatenated T planes ([rows][Np] bf16; box b's node 0 at row t_row0[b])
 cc_status tc_slab_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,

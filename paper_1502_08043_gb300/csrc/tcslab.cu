@@ -94,6 +94,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
 __device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
+// x0, x1 -> (hi pair, lo pair) of 16-bit values, bf16 or fp16
+template <bool kHalf>
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  if constexpr (kHalf) {
+    __half2 h = __floats2half2_rn(x0, x1);
+    __half2 l = __floats2half2_rn(x0 - __low2float(h), x1 - __high2float(h));
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    lo = *reinterpret_cast<uint32_t*>(&l);
+  } else {
+    hi = pack_bf16x2(x0, x1);
+    lo = pack_bf16x2(x0 - bf16_lo_f(hi), x1 - bf16_hi_f(hi));
+  }
+}
+
+template <bool kHalf>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_slab(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
               Args g) {
@@ -187,7 +202,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
+      // F32 accumulate; A and B both bf16 (format 1) or both fp16 (format 0)
+      constexpr uint32_t fmt = kHalf ? 0u : 1u;
+      constexpr uint32_t idesc0 =
+          (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(128 >> 4) << 24);
       const uint32_t idesc1 = idesc0 | ((uint32_t)(nact >> 3) << 17);  // N = band width
       // N = the grid side rounded up to 16 (columns z' >= Mg are never read)
       const uint32_t idesc2 = idesc0 | ((uint32_t)(((g.Mg + 15) & ~15) >> 3) << 17);
@@ -451,9 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int e = 0; e < 16; e += 2) {
                 const float x0 = fmaf(__uint_as_float(v[e]), ws, a[k][16 * sub + e]);
                 const float x1 = fmaf(__uint_as_float(v[e + 1]), ws, a[k][16 * sub + e + 1]);
-                const uint32_t h = pack_bf16x2(x0, x1);
-                hi[e >> 1] = h;
-                lo[e >> 1] = pack_bf16x2(x0 - bf16_lo_f(h), x1 - bf16_hi_f(h));
+                split_pair<kHalf>(x0, x1, hi[e >> 1], lo[e >> 1]);
               }
               tmem_st8(ta, hi);
               tmem_st8(ta + 8u, lo);
@@ -536,6 +552,83 @@ __global__ void k_tc_slab_tplanes(const double* Tm, int S, int Mg, __nv_bfloat16
     const __nv_bfloat16 h = __float2bfloat16_rn((float)t);
     hi[i] = h;
     lo[i] = __float2bfloat16_rn((float)t - __bfloat162float(h));
+  }
+}
+
+// fp16x3 keeps every operand inside fp16's range with power-of-two scales per node s:
+//   R' = 2^j F (largest value 2^14), T' = 2^a T for both products, and the epilogue forms
+//   U'' = 2^-a w (T R + A) = (T' R') w 2^(-2a-j) + (2^-a w F) so that U'' T' = w (T R + A) T;
+//   a balances the largest T' (2^a) and U'' (2^-a w (Mg + 1) max F).
+// The largest window sum of each node (F grows with h, so it is reached at h = R_F), as the
+// bits of a non-negative float.  One thread per (s, a).
+__global__ void k_tc_slab_fmax(const double* Tm, int S, int Mg, int R, int RF, int periodic,
+                               unsigned* fmax_bits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S * Mg) return;
+  const int s = i / Mg, a = i % Mg;
+  const double* row = Tm + ((long long)s * Mg + a) * Mg;
+  double f = 0.0;
+  for (int k = R - RF; k <= R + RF; ++k) f += (periodic && k == a) ? 0.0 : row[k];
+  atomicMax(fmax_bits + s, __float_as_uint((float)f));
+}
+
+__global__ void k_tc_slab_scales(const unsigned* fmax_bits, const double* w, int S, int Mg,
+                                 int* jexp, int* aexp, float* wsc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const double fm = (double)__uint_as_float(fmax_bits[s]);
+  int j = 0, a = 0;
+  if (fm > 0.0) {
+    int e;
+    frexp(fm, &e);  // fm < 2^e
+    j = 14 - e;
+    frexp(w[s] * (Mg + 1) * fm, &e);
+    a = (int)floor(0.5 * e + 0.5);
+    a = a < -14 ? -14 : (a > 14 ? 14 : a);
+  }
+  jexp[s] = j;
+  aexp[s] = a;
+  wsc[s] = (float)ldexp(w[s], -2 * a - j);
+}
+
+// fp16: R' = 2^j F as fp16 hi | lo pairs, 2^-a w F for the A term
+__global__ void k_tc_slab_prep16(const double* Tm, const double* w, int S, int Mg, int R,
+                                 int RF, int periodic, const int* jexp, const int* aexp,
+                                 uint32_t* FR, float* FW) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S * kN) return;
+  const int s = i / kN, a = i % kN;
+  const double* row = Tm + ((long long)s * Mg + (a < Mg ? a : 0)) * Mg;
+  auto X = [&](int k) { return (periodic && k == a) ? 0.0 : row[k]; };
+  const int js = jexp[s], as = aexp[s];
+  double acc = 0.0;
+  for (int h = 0; h < kHMax; ++h) {
+    double f = 0.0;
+    if (a < Mg && h <= RF) {
+      acc += h == 0 ? X(R) : X(R - h) + X(R + h);
+      f = acc;
+    }
+    const double fs = ldexp(f, js);
+    const __half hb = __float2half_rn((float)fs);
+    const __half lb = __float2half_rn((float)(fs - (double)__half2float(hb)));
+    FR[(long long)i * kHMax + h] = (uint32_t)__half_as_ushort(hb) |
+                                   ((uint32_t)__half_as_ushort(lb) << 16);
+    if (periodic) FW[((long long)s * kHMax + h) * kN + a] = (float)ldexp(w[s] * f, -as);
+  }
+}
+
+// fp16: T' = 2^a T as fp16 hi + lo planes padded to 128 x 128
+__global__ void k_tc_slab_tplanes16(const double* Tm, int S, int Mg, const int* aexp,
+                                    __half* hi, __half* lo) {
+  const long long n = (long long)S * kN * kN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / (kN * kN)), a = (int)((i / kN) % kN), c = (int)(i % kN);
+    const double t =
+        (a < Mg && c < Mg) ? ldexp(Tm[((long long)s * Mg + a) * Mg + c], aexp[s]) : 0.0;
+    const __half h = __float2half_rn((float)t);
+    hi[i] = h;
+    lo[i] = __float2half_rn((float)(t - (double)__half2float(h)));
   }
 }
 
@@ -638,6 +731,17 @@ struct TcSlabWs {
   // grids of side <= 64: own 128-padded T planes and their maps (else the step chain's)
   void* T128[2] = {nullptr, nullptr};
   alignas(64) unsigned char map_hi[128], map_lo[128];
+  // fp16x3: scaled operands of their own (see k_tc_slab_scales)
+  int RF16_built = -1;
+  uint32_t* FR16 = nullptr;
+  float* FW16 = nullptr;
+  float* FB16 = nullptr;
+  float* w16 = nullptr;
+  unsigned* fmax = nullptr;
+  int* jexp = nullptr;
+  int* aexp = nullptr;
+  void* T16[2] = {nullptr, nullptr};
+  alignas(64) unsigned char map16_hi[128], map16_lo[128];
   std::vector<void*> allocs;
 };
 
@@ -698,6 +802,24 @@ cc_status tc_slab_alloc(cc_tables t, void** out) {
       return CC_ERR_CUDA;
     }
   }
+  {
+    const size_t plane = sizeof(__half) * (size_t)S * kN * kN;
+    if ((st = alloc((void**)&w->FR16, sizeof(uint32_t) * S * kN * kHMax)) != CC_OK ||
+        (st = alloc((void**)&w->FW16, sizeof(float) * S * kN * kHMax)) != CC_OK ||
+        (st = alloc((void**)&w->FB16, sizeof(float) * kN * kHMax)) != CC_OK ||
+        (st = alloc((void**)&w->w16, sizeof(float) * S)) != CC_OK ||
+        (st = alloc((void**)&w->fmax, sizeof(unsigned) * S)) != CC_OK ||
+        (st = alloc((void**)&w->jexp, sizeof(int) * S)) != CC_OK ||
+        (st = alloc((void**)&w->aexp, sizeof(int) * S)) != CC_OK ||
+        (st = alloc(&w->T16[0], plane)) != CC_OK || (st = alloc(&w->T16[1], plane)) != CC_OK ||
+        (st = tc_make_map_16(w->map16_hi, w->T16[0], (long long)S * kN, kN, kN, false)) !=
+            CC_OK ||
+        (st = tc_make_map_16(w->map16_lo, w->T16[1], (long long)S * kN, kN, kN, false)) !=
+            CC_OK) {
+      tc_slab_free(w);
+      return st;
+    }
+  }
   std::vector<float> w32(S);
   for (int i = 0; i < S; ++i) w32[i] = (float)t->w[t->kept_idx[i]];
   cudaError_t e = cudaMemcpy(w->w32, w32.data(), sizeof(float) * S, cudaMemcpyHostToDevice);
@@ -718,12 +840,28 @@ void tc_slab_free(void* p) {
 }
 
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
-                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st) {
+                      int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
+                      bool half) {
   TcSlabWs* w = reinterpret_cast<TcSlabWs*>(ws);
   if (!w || !tc_slab_supported(t) || R_F > 63) return CC_ERR_NOTSUPP;
   const int S = t->S_eff, Mg = t->Mg, R = t->p.R;
   const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
-  if (w->RF_built != R_F) {
+  if (half && w->RF16_built != R_F) {
+    CC_CUDA(cudaMemsetAsync(w->fmax, 0, sizeof(unsigned) * S, st));
+    k_tc_slab_fmax<<<(S * Mg + 127) / 128, 128, 0, st>>>(t->d.Tm64, S, Mg, R, R_F, periodic,
+                                                         w->fmax);
+    k_tc_slab_scales<<<(S + 127) / 128, 128, 0, st>>>(w->fmax, t->d.w64, S, Mg, w->jexp,
+                                                      w->aexp, w->w16);
+    k_tc_slab_prep16<<<(S * kN + 127) / 128, 128, 0, st>>>(t->d.Tm64, t->d.w64, S, Mg, R, R_F,
+                                                            periodic, w->jexp, w->aexp, w->FR16,
+                                                            w->FW16);
+    k_tc_slab_tplanes16<<<1024, 256, 0, st>>>(t->d.Tm64, S, Mg, w->aexp, (__half*)w->T16[0],
+                                              (__half*)w->T16[1]);
+    if (periodic) k_tc_slab_dbar<<<1, kN, 0, st>>>(t->d.Dbar64, Mg, R, R_F, w->FB16);
+    CC_CUDA(cudaGetLastError());
+    w->RF16_built = R_F;
+  }
+  if (!half && w->RF_built != R_F) {
     k_tc_slab_prep<<<(S * kN + 127) / 128, 128, 0, st>>>(t->d.Tm64, t->d.w64, S, Mg, R, R_F,
                                                           periodic, w->FR, w->FW);
     if (periodic) k_tc_slab_dbar<<<1, kN, 0, st>>>(t->d.Dbar64, Mg, R, R_F, w->FB);
@@ -738,25 +876,34 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   a.periodic = periodic;
   a.units = w->units;
   a.maxseg = w->maxseg;
-  a.FR = w->FR;
-  a.FW = w->FW;
-  a.w = w->w32;
+  a.FR = half ? w->FR16 : w->FR;
+  a.FW = half ? w->FW16 : w->FW;
+  a.w = half ? w->w16 : w->w32;
   a.part = w->part;
   a.err = err;
   a.stall_test = stall_test;
   const uint32_t smem = slab_smem_bytes(R_F);
   static uint32_t attr = 0;
   if (attr < smem) {
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)slab_smem_bytes(63)));
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slab_smem_bytes(63)));
     attr = slab_smem_bytes(63);
   }
-  const CUtensorMap& mh =
-      *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);
-  const CUtensorMap& ml =
-      *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_lo : map_lo);
-  k_tc_slab<<<w->grid, kThreads, smem, st>>>(mh, ml, a);
-  k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, w->FB, R, R_F, S,
+  if (half) {
+    const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(w->map16_hi);
+    const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(w->map16_lo);
+    k_tc_slab<true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+  } else {
+    const CUtensorMap& mh =
+        *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);
+    const CUtensorMap& ml =
+        *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_lo : map_lo);
+    k_tc_slab<false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+  }
+  k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, half ? w->FB16 : w->FB,
+                                                             R, R_F, S,
                                                              w->units, w->grid, w->maxseg,
                                                              periodic, t->pref, eps, w->row_ex);
   k_tc_slab_ex<<<1, 1024, 0, st>>>(w->row_ex, Mg * Mg, Ex, err, err + 1);

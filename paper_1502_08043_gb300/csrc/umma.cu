@@ -586,6 +586,11 @@ cc_status tc_make_map_bf16(void* map, void* ptr, long long rows, int cols, int b
   CC_TRY(get_encoder());
   return make_map(reinterpret_cast<CUtensorMap*>(map), ptr, rows, cols, box_rows, true);
 }
+cc_status tc_make_map_16(void* map, void* ptr, long long rows, int cols, int box_rows,
+                         bool bf16) {
+  CC_TRY(get_encoder());
+  return make_map(reinterpret_cast<CUtensorMap*>(map), ptr, rows, cols, box_rows, bf16);
+}
 
 static cc_status mx_alloc(cc_tables t, MxWorkspace* w, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
@@ -801,13 +806,18 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
   MxWorkspace* w = reinterpret_cast<MxWorkspace*>(t->ws.mx);
   if (!w) return CC_ERR_NOTSUPP;  // handle built without workspaces
   if (precision == CC_PREC_FP16X3) {
+    if (w->slab && g_mixed_variant != 1) {
+      const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
+      return tc_slab_run(t, w->slab, nullptr, nullptr, w->err, stall, R_F, eps, Ex, st, true);
+    }
+    if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
     if (w->Np == 64) return run_mixed<64, __half>(t, w, w->hf, R_F, eps, Ex, st);
     return run_mixed<128, __half>(t, w, w->hf, R_F, eps, Ex, st);
   }
   if (w->slab && g_mixed_variant != 1) {
     const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
     return tc_slab_run(t, w->slab, &w->bf.mTT[0], &w->bf.mTT[1], w->err, stall, R_F, eps, Ex,
-                       st);
+                       st, false);
   }
   if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
   if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);

@@ -185,6 +185,45 @@ def test_slab_kernel_vs_chain_and_oracle(dev, kernel, R, R_F):
     t.free()
 
 
+@pytest.mark.parametrize("kernel,R,R_F", [("periodic", 33, 21), ("box", 33, 21),
+                                           ("periodic", 13, 8)],
+                         ids=["periodic-R33-RF21", "box-R33-RF21", "grid27-R13-RF8"])
+def test_slab_kernel_fp16x3_vs_chain_and_oracle(dev, kernel, R, R_F):
+    """fp16x3 through the slab kernel (per-node power-of-two scales of T, the window sums
+    and the intermediate) element by element against the fp16x3 step chain, and against the
+    FP64 oracle on sampled basis functions and on E_x."""
+    import paper_1502_08043_gb300 as cc
+    L = 30.0
+    if kernel == "periodic":
+        t = cc.build_tables("periodic", R=R, L=L, S=64)
+        a, w = oracle_nodes(R, 64)
+    else:
+        a, w, _ = oq.paper_mesh2(6, 24)
+        t = cc.build_tables("box", R=R, L=L, S=len(a), n_sub=7, q_tail=24)
+    try:
+        _variant(2)
+        g_slab, e_slab = _run(t, R_F, "fp16x3", dev)
+        _variant(1)
+        g_chain, e_chain = _run(t, R_F, "fp16x3", dev)
+    finally:
+        _variant(0)
+    assert np.array_equal(g_slab == 0, g_chain == 0)
+    inside = g_chain != 0
+    assert np.max(np.abs(g_slab[inside] - g_chain[inside]) / np.abs(g_chain[inside])) < TOL_MIXED
+    Nb = ob.count(R)
+    idx = np.unique(np.concatenate([np.random.default_rng(4).integers(0, Nb, 150), [0, Nb - 1]]))
+    C = ox.difference_histogram(R_F, "fft")
+    if kernel == "periodic":
+        ref = ox.eps_separable(R, R_F, L, a, w, k_idx=idx)
+        ex_ref = ox.Ex_separable_periodic(R_F, L, a, w, C)
+    else:
+        ref = ox.eps_box(R, R_F, L, a, w, k_idx=idx)
+        ex_ref = ox.Ex_box(R_F, L, a, w, C)
+    assert rel_err(_basis_values(R, g_slab)[idx], ref) < TOL_MIXED
+    assert abs(e_slab[0] - ex_ref) < TOL_MIXED * abs(ex_ref)
+    t.free()
+
+
 def test_slab_kernel_variant_errors(dev):
     import paper_1502_08043_gb300 as cc
     L = cc.lib()
