@@ -92,6 +92,70 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
+// Warp-converged forms: all 32 lanes execute the call with the same operands and one lane,
+// chosen by elect.sync, issues the instruction.  Operands that are uniform over a converged
+// warp stay in uniform registers, so an MMA costs the issuing warp a few instructions only
+// (issued from a single-lane branch it costs many more, which other warps on the same
+// scheduler then delay).
+__device__ __forceinline__ void mma_f16_w(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                          uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// A operand in tensor memory
+__device__ __forceinline__ void mma_f16_ts_w(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                             uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// One K step of a split-precision product, warp-converged, from one asm block (one elected
+// lane, the descriptor offsets added in the block): D (+)= A B + A B' + A' B with
+// A' = A + da, B' = B + db (descriptor offsets of the lo planes).  Three MMAs per asm block
+// cost the issuing warp markedly fewer instructions than three single calls, which matters
+// while other warps on its scheduler are busy.
+__device__ __forceinline__ void mma_x3_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint64_t da,
+                                         uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, t, e;\n .reg .b64 a1, b1;\n setp.ne.b32 p, %4, 0;\n"
+      " setp.eq.u32 t, 0, 0;\n add.u64 a1, %1, %5;\n add.u64 b1, %2, %6;\n"
+      " elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, b1, %3, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, %2, %3, t;\n}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum), "l"(da), "l"(db)
+      : "memory");
+}
+
+// The same with A in tensor memory: hi in columns a .. a + 7, lo in a + 8 .. a + 15
+__device__ __forceinline__ void mma_x3_ts_w(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, t, e;\n .reg .b64 b1;\n .reg .b32 a1;\n setp.ne.b32 p, %4, 0;\n"
+      " setp.eq.u32 t, 0, 0;\n add.u32 a1, %1, 8;\n add.u64 b1, %2, %5;\n"
+      " elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], b1, %3, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], %2, %3, t;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum), "l"(db)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_w(uint32_t bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(
+          bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
