@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain, 0, g.err, 17, nullptr, 100000000ull);
     }
   } else if (warp >= kEpiWarps) {
-    // ---------------- R operand builders (warps 8-13)
+    // ---------------- R operand builders (warps 8-10, 12-14)
     // R_{s,x}[y][z] = F_s[x][h(y, z)]: the x line of the sphere at (y, z) does not depend
     // on x, only the row of F_s does, and rows z and 2R - z of the operand are equal.  A
     // builder thread always forms the same 16-byte chunks (row z <= R of the square
@@ -430,14 +430,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = (int)(u % S);
         const float ws = g.w[s];
         const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
-        if (g.periodic && u + 1 < u1) {
-          // the next unit's A-term table (4 lines per h) into L1 ahead of its use
-          const int line = tid;  // 256 epilogue threads, (R_F + 1) * 4 <= 256 lines
-          if (line < (RF + 1) * 4) {
-            const float* nx = g.FW + (long long)((u + 1) % S) * kHMax * kN + line * 32;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
-          }
-        }
         for (int j = 0; j < 2; ++j) {
           // the A-term values of this warp's 64 columns, requested before the MMA result is
           // waited for (their L2 latency hides behind the wait)

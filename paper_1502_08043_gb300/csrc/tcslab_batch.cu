@@ -28,8 +28,9 @@
 // forms eps and E_x.  Each product is bf16x3: hi*hi + hi*lo + lo*hi, FP32 accumulate.
 //
 // Tensor memory (512 columns): [0,128) U_0, [128,256) U_1, [256,384) E_0, [384,512) E_1.
-// Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..), 8-13 build R,
-// 14 TMA producer, 15 MMA issuer.  Every wait is bounded (global timer); on expiry the
+// Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..), 8-10 and 12-14
+// build R, 11 TMA producer, 15 MMA issuer (converged, one K step per elected asm block; no
+// builder shares the MMA warp's scheduler).  Every wait is bounded (global timer); on expiry the
 // error word is set, all roles stop, the MMA issuer drains its MMAs and tensor memory is
 // freed before the CTA returns.
 #include <cuda.h>
@@ -50,7 +51,7 @@ constexpr int kThreads = 512;
 constexpr int kEpiWarps = 8;
 constexpr int kBldWarps = 6;
 constexpr int kBldThreads = 32 * kBldWarps;
-constexpr int kProdWarp = 14;
+constexpr int kProdWarp = 11;
 constexpr int kMmaWarp = 15;
 constexpr int kN = 128;                 // padded grid side
 constexpr int kHMax = 64;               // window half-lengths h = 0 .. R_F <= 63
@@ -231,10 +232,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_wait(tfull(m & 1u), (m >> 1) & 1u, g.err, 12, nullptr, 100000000ull);
     }
   } else if (warp == kMmaWarp) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
+    {
+      // ---------------- MMA issuer (the whole warp; every wait result made warp-uniform)
+      auto all = [](bool v) { return __all_sync(0xffffffffu, v); };
       constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
-      if (g.stall_test && !mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)) s_abort = 1;
+      if (g.stall_test && !all(mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull))) s_abort = 1;
       uint32_t n = 0, r = 0, segc = 0;
       // per box: band [zs, ze) in K steps [ms, me); first MMA N = band width, second MMA
       // N = the grid side rounded up to 16 (columns z' >= Mg are never read).  Descriptors
@@ -252,9 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           constexpr uint64_t kPl = kPlane >> 4;
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           const uint32_t acc = m > ms ? 1u : 0u;
-          mma_f16(d, dT + o, dR + o, idesc1, acc);
-          mma_f16(d, dT + o, dR + o + kPl, idesc1, 1u);
-          mma_f16(d, dT + o + kPl, dR + o, idesc1, 1u);
+          mma_x3_w(d, dT + o, dR + o, kPl, kPl, idesc1, acc);
         }
       };
       auto mma2 = [&](uint32_t tb, int j, bool first) {
@@ -268,12 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           // U piece of z = 16 m ..: columns 16 (m - zs / 16) .., 8 hi then 8 lo
           const uint32_t aH = a0 + (uint32_t)(16 * m);
-          mma_f16_ts(d, aH, dT + o, idesc2, (first && m == ms) ? 0u : 1u);
-          mma_f16_ts(d, aH, dT + o + kPl, idesc2, 1u);
-          mma_f16_ts(d, aH + 8u, dT + o, idesc2, 1u);
+          mma_x3_ts_w(d, aH, dT + o, kPl, idesc2, (first && m == ms) ? 0u : 1u);
         }
       };
-      bool ok = !s_abort;
+      bool ok = all(!s_abort);
       int b = 0;
       for (long long u = u0; u < u1 && ok;) {
         b = advance_box<kBatch>(g, b, u);
@@ -292,34 +290,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t k = n & 1u, tb = base + kOffT + k * kOp;
           const uint32_t tbp = base + kOffT + (k ^ 1u) * kOp;
           // MMA1(i, 0)
-          ok = mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
-               mbar_wait(rfull, r & 1u, g.err, 15, &s_abort);
+          ok = all(mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
+                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort));
           if (!ok) break;
           tc_fence_after();
           mma1(tb, 0);
-          mma_commit(rfree);
-          mma_commit(d1full(0));
+          mma_commit_w(rfree);
+          mma_commit_w(d1full(0));
           ++r;
           // MMA2(i - 1, 1)
           if (i > 0) {
-            ok = mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort);
+            ok = all(mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort));
             if (!ok) break;
             tc_fence_after();
             mma2(tbp, 1, i - 1 == 0);
-            mma_commit(tfree(k ^ 1u));
+            mma_commit_w(tfree(k ^ 1u));
           }
           // MMA1(i, 1)
-          ok = mbar_wait(rfull, r & 1u, g.err, 15, &s_abort);
+          ok = all(mbar_wait(rfull, r & 1u, g.err, 15, &s_abort));
           if (!ok) break;
           tc_fence_after();
           mma1(tb, 1);
-          mma_commit(rfree);
-          mma_commit(d1full(1));
+          mma_commit_w(rfree);
+          mma_commit_w(d1full(1));
           ++r;
           // MMA2(i, 0); the first one of a pair also waits until the previous pair's E
           // has left tensor memory
-          ok = mbar_wait(a2full(0), n & 1u, g.err, 16, &s_abort) &&
-               (i > 0 || segc == 0 || mbar_wait(edone, (segc - 1) & 1u, g.err, 13, &s_abort));
+          ok = all(mbar_wait(a2full(0), n & 1u, g.err, 16, &s_abort) &&
+                   (i > 0 || segc == 0 || mbar_wait(edone, (segc - 1) & 1u, g.err, 13, &s_abort)));
           if (!ok) break;
           tc_fence_after();
           mma2(tb, 0, i == 0);
@@ -327,22 +325,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         // MMA2(U - 1, 1), then E of the pair is complete
         const uint32_t kl = (n - 1) & 1u;
-        ok = mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort);
+        ok = all(mbar_wait(a2full(1), (n - 1) & 1u, g.err, 16, &s_abort));
         if (!ok) break;
         tc_fence_after();
         mma2(base + kOffT + kl * kOp, 1, U == 1);
-        mma_commit(tfree(kl));
-        mma_commit(efull);
+        mma_commit_w(tfree(kl));
+        mma_commit_w(efull);
         ++segc;
         u = ue;
       }
       if (!ok) s_abort = 1;
       // every MMA issued has finished before tensor memory is released
-      mma_commit(drain);
+      mma_commit_w(drain);
       mbar_wait(drain, 0, g.err, 17, nullptr, 100000000ull);
     }
   } else if (warp >= kEpiWarps) {
-    // ---------------- R operand builders (warps 8-13)
+    // ---------------- R operand builders (warps 8-10, 12-14)
     // R_{s,x}[y][z] = F_s[x][h(y, z)]: the x line of the sphere at (y, z) does not depend
     // on x, only the row of F_s does, and rows z and 2R - z of the operand are equal.  A
     // builder thread always forms the same 16-byte chunks of a box (row z <= R of the
@@ -350,7 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // rows, so it keeps their h values in registers (packed bytes) for the whole box.  The
     // row of F_s of a build is written by all builder warps into a replicated table (copy
     // l in bank l) and every element is one conflict-free shared-memory load away.
-    const int bt = tid - 32 * kEpiWarps, bw = warp - kEpiWarps;
+    const int bw = warp < kProdWarp ? warp - kEpiWarps : warp - kEpiWarps - 1;
+    const int bt = 32 * bw + lane;
     constexpr int kMaxTasks = 6;  // (R_F + 1) x chunks <= 64 x 16 = 1024 = 5.3 x 192
     uint32_t hb[kMaxTasks][2];
     int cur = -1, R = 0, RF = 0, zlo = 0, clo = 0, nc = 1, tasks = 0;
