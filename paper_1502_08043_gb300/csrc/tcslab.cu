@@ -410,19 +410,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quad = warp & 3, half = warp >> 2;
     const int yrow = 32 * quad + lane;
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    // the band's 16-column pieces split evenly between the two warps of a lane quadrant:
+    // this warp's np pieces start at band column c0
+    const int npc = nact >> 4, n0 = (npc + 1) >> 1;
+    const int c0 = half ? 16 * n0 : 0, np = half ? npc - n0 : n0;
     uint32_t n = 0, segc = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok;) {
       const long long p = u / S;
       const long long ue = u1 < (p + 1) * S ? u1 : (p + 1) * S;
-      // h(x_j, z) for the columns z = 32 cc + lane of this warp's two chunks (fixed for the
-      // whole pair; broadcast by shuffle per column), -1 outside the sphere
+      // h(x_j, z) for the columns z = zs + c0 + 32 k + lane of this warp's two chunks (fixed
+      // for the whole pair; broadcast by shuffle per column), -1 outside the sphere
       int hz[2][2];
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const int dx = (int)(2 * p + j) - R, dz = zs + 32 * (2 * half + k) + lane - R;
+          const int dx = (int)(2 * p + j) - R, dz = zs + c0 + 32 * k + lane - R;
           const int q = RF * RF - dx * dx - dz * dz;
           hz[j][k] = q >= 0 ? (int)isq[q] : -1;
         }
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float ws = g.w[s];
         const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
         for (int j = 0; j < 2; ++j) {
-          // the A-term values of this warp's 64 columns, requested before the MMA result is
+          // the A-term values of this warp's columns, requested before the MMA result is
           // waited for (their L2 latency hides behind the wait)
           float a[2][32];
 #pragma unroll
@@ -452,9 +456,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int k = 0; k < 2; ++k) {
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
-              if (32 * (2 * half + k) + 16 * sub >= nact) continue;  // beyond the band
-              const uint32_t ta = tmem + lane_off +
-                                  (uint32_t)(j * 128 + 32 * (2 * half + k) + 16 * sub);
+              if (2 * k + sub >= np) continue;  // beyond this warp's pieces
+              const uint32_t ta = tmem + lane_off + (uint32_t)(j * 128 + c0 + 32 * k + 16 * sub);
               uint32_t v[16];
               tmem_ld16(ta, v);
               uint32_t hi[8], lo[8];
