@@ -148,6 +148,18 @@ __device__ __forceinline__ void mma_x3_ts_w(uint32_t tmem_d, uint32_t tmem_a, ui
       : "memory");
 }
 
+// D += A B + A2 B (accumulating), A and A2 in tensor memory, warp-converged as above: the hi
+// and lo planes of one A against a B that is exact in 16 bits
+__device__ __forceinline__ void mma_x2_ts_w(uint32_t tmem_d, uint32_t tmem_a, uint32_t tmem_a2,
+                                            uint64_t b, uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred t, e;\n setp.eq.u32 t, 0, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %4, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %3, %4, t;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "r"(tmem_a2), "l"(b), "r"(idesc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit_w(uint32_t bar) {
   asm volatile(
       "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"

@@ -63,8 +63,14 @@ constexpr uint32_t kOffR = 2 * kOp;         // the R operand
 // l (entry h of copy l at word 32 h + l): conflict-free gathers; two of them alternate
 constexpr uint32_t kFtabBytes = kHMax * 32 * 4;  // 8 KB
 constexpr uint32_t kOffFtab = 3 * kOp;
-constexpr uint32_t kOffBar = kOffFtab + 2 * kFtabBytes;  // mbarriers, tensor-memory slot
-constexpr int kNumBars = 16;
+// periodic bf16 boxes whose band is at most 96 columns wide add the A term on the tensor
+// cores: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h] (band rows z, K = h),
+// F_s as bf16 hi and lo in the tensor-memory columns the band leaves free in U_0 and U_1
+constexpr int kMmaABand = 96;
+constexpr uint32_t kOffP = kOffFtab + 2 * kFtabBytes;   // P_x, band rows x 128 bytes
+constexpr uint32_t kFhi = 96, kFlo = 224;               // F_s hi / lo columns
+constexpr uint32_t kOffBar = kOffP + kMmaABand * 128;  // mbarriers, tensor-memory slot
+constexpr int kNumBars = 17;
 constexpr uint32_t kOffIsq = kOffBar + 8 * kNumBars + 16;  // floor(sqrt(v)), v <= R_F^2
 __host__ __device__ constexpr uint32_t slab_smem_bytes(int R_F) {
   return kOffIsq + (((uint32_t)(R_F * R_F + 1) + 15u) & ~15u) + 1024u;
@@ -111,7 +117,7 @@ __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uin
   }
 }
 
-template <bool kHalf>
+template <bool kHalf, bool kMmaA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_slab(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
               Args g) {
@@ -129,6 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t efull = bar + 8u * 10, edone = bar + 8u * 11;
   const uint32_t never = bar + 8u * 12, drain = bar + 8u * 13;
   auto ftfull = [&](int k) { return bar + 8u * (14 + k); };  // 14, 15
+  const uint32_t ffull = bar + 8u * 16;  // F_s of the next unit is in tensor memory
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
   __shared__ volatile int s_abort;
 
@@ -150,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(drain, 1);
     mbar_init(ftfull(0), kBldWarps);
     mbar_init(ftfull(1), kBldWarps);
+    mbar_init(ffull, kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -219,6 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // byte offset o (all addresses < 256 KB) adds o / 16
       const int ms = zs >> 4, me = ze >> 4;
       const uint64_t dR = sdesc(base + kOffR + zs * 128u);  // B rows z = zs ..
+      // the A-term MMAs: K = h < 16 nh (h <= R_F), B = P_x (band rows), A = F_s hi and lo
+      const int nh = (RF + 16) >> 4;
+      const uint64_t dP = sdesc(base + kOffP);
       auto mma1 = [&](uint32_t tb, int j) {
         const uint32_t d = tmem + (uint32_t)(j * 128);
         const uint64_t dT = sdesc(tb);
@@ -229,6 +240,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           const uint32_t acc = m > ms ? 1u : 0u;
           mma_x3_w(d, dT + o, dR + o, kPl, kPl, idesc1, acc);
+        }
+        if constexpr (kMmaA) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (m < nh)
+              mma_x2_ts_w(d, tmem + kFhi + 8u * m, tmem + kFlo + 8u * m, dP + 2u * m, idesc1);
         }
       };
       auto mma2 = [&](uint32_t tb, int j, bool first) {
@@ -255,7 +272,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t tbp = base + kOffT + (k ^ 1u) * kOp;
           // MMA1(i, 0)
           ok = all(mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
-                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort));
+                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort) &&
+                   (!kMmaA || mbar_wait(ffull, n & 1u, g.err, 18, &s_abort)));
           if (!ok) break;
           tc_fence_after();
           mma1(tb, 0);
@@ -399,6 +417,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+        if constexpr (kMmaA) {
+          // P_x for x = 2 p + j: band row rr (z = zs + rr) is one-hot at h(x, z), zero
+          // outside the sphere; 16-byte chunk c holds h = 8 c .. 8 c + 7 (128-byte swizzle)
+          const int dx = (int)(2 * (u / S) + j) - R;
+          for (int t = bt; t < nact * 8; t += kBldThreads) {
+            const int rr = t >> 3, c = t & 7, dz = zs + rr - R;
+            const int q = RF * RF - dx * dx - dz * dz;
+            const int h = q >= 0 ? (int)isq[q] : -1;
+            const bool hit = h >= 0 && (h >> 3) == c;
+            const uint32_t one = 0x3F80u << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
+            const uint4 v = make_uint4(hit && wi == 0 ? one : 0u, hit && wi == 1 ? one : 0u,
+                                       hit && wi == 2 ? one : 0u, hit && wi == 3 ? one : 0u);
+            *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + ((c ^ (rr & 7)) << 4)) = v;
+          }
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(rfull);
@@ -416,6 +449,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = half ? 16 * n0 : 0, np = half ? npc - n0 : n0;
     uint32_t n = 0, segc = 0;
     bool ok = true;
+    // the A-term MMAs read F_s of unit uu from tensor memory: lane y, column kFhi + c
+    // (kFlo + c) holds the bf16 hi (lo) pair of h = 2 c, 2 c + 1; this warp writes
+    // h = 32 half .. 32 half + 31 of its lanes from the window-sum rows F_s[y][.]
+    auto stage_f = [&](long long uu) {
+      const uint4* src = reinterpret_cast<const uint4*>(
+          g.FR + ((long long)(uu % S) * kN + yrow) * kHMax + 32 * half);
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint4 f = __ldg(src + i);
+        hi[2 * i] = __byte_perm(f.x, f.y, 0x5410);
+        lo[2 * i] = __byte_perm(f.x, f.y, 0x7632);
+        hi[2 * i + 1] = __byte_perm(f.z, f.w, 0x5410);
+        lo[2 * i + 1] = __byte_perm(f.z, f.w, 0x7632);
+      }
+      tmem_st16(tmem + lane_off + kFhi + 16u * half, hi);
+      tmem_st16(tmem + lane_off + kFlo + 16u * half, lo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ffull);
+    };
+    if constexpr (kMmaA) {
+      if (u0 < u1) stage_f(u0);
+    }
     for (long long u = u0; u < u1 && ok;) {
       const long long p = u / S;
       const long long ue = u1 < (p + 1) * S ? u1 : (p + 1) * S;
@@ -438,18 +496,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the A-term values of this warp's columns, requested before the MMA result is
           // waited for (their L2 latency hides behind the wait)
           float a[2][32];
+          if constexpr (!kMmaA) {
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int hzk = j == 0 ? hz[0][k] : hz[1][k];
+            for (int k = 0; k < 2; ++k) {
+              const int hzk = j == 0 ? hz[0][k] : hz[1][k];
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int h = __shfl_sync(0xffffffffu, hzk, e);
-              a[k][e] = (g.periodic && h >= 0) ? __ldg(FWs + h * kN) : 0.0f;
+              for (int e = 0; e < 32; ++e) {
+                const int h = __shfl_sync(0xffffffffu, hzk, e);
+                a[k][e] = (g.periodic && h >= 0) ? __ldg(FWs + h * kN) : 0.0f;
+              }
             }
           }
           ok = mbar_wait(d1full(j), n & 1u, g.err, 31, &s_abort);
           if (!ok) break;
           tc_fence_after();
+          // the second first mode product of this unit is done with F_s: the next unit's
+          // goes into tensor memory (the MMA warp waits for it before that unit's first MMA)
+          if constexpr (kMmaA) {
+            if (j == 1 && u + 1 < u1) stage_f(u + 1);
+          }
           // in place, 16 columns at a time: FP32 U of the piece z = zs + 16 m .. in columns
           // 16 m .. 16 m + 15 becomes 8 columns of bf16 hi pairs followed by 8 of lo pairs
 #pragma unroll
@@ -463,8 +528,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t hi[8], lo[8];
 #pragma unroll
               for (int e = 0; e < 16; e += 2) {
-                const float x0 = fmaf(__uint_as_float(v[e]), ws, a[k][16 * sub + e]);
-                const float x1 = fmaf(__uint_as_float(v[e + 1]), ws, a[k][16 * sub + e + 1]);
+                float x0, x1;
+                if constexpr (kMmaA) {  // U already holds T_s R + A
+                  x0 = __uint_as_float(v[e]) * ws;
+                  x1 = __uint_as_float(v[e + 1]) * ws;
+                } else {
+                  x0 = fmaf(__uint_as_float(v[e]), ws, a[k][16 * sub + e]);
+                  x1 = fmaf(__uint_as_float(v[e + 1]), ws, a[k][16 * sub + e + 1]);
+                }
                 split_pair<kHalf>(x0, x1, hi[e >> 1], lo[e >> 1]);
               }
               tmem_st8(ta, hi);
@@ -881,22 +952,33 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   const uint32_t smem = slab_smem_bytes(R_F);
   static uint32_t attr = 0;
   if (attr < smem) {
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slab_smem_bytes(63)));
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)slab_smem_bytes(63)));
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slab_smem_bytes(63)));
     attr = slab_smem_bytes(63);
   }
+  // the A term on the tensor cores where the band leaves tensor memory free for F_s
+  const bool mma_a =
+      !half && periodic && ((R + R_F + 16) & ~15) - ((R - R_F) & ~15) <= kMmaABand;
   if (half) {
     const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(w->map16_hi);
     const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(w->map16_lo);
-    k_tc_slab<true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    k_tc_slab<true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   } else {
     const CUtensorMap& mh =
         *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);
     const CUtensorMap& ml =
         *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_lo : map_lo);
-    k_tc_slab<false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    if (mma_a)
+      k_tc_slab<false, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    else
+      k_tc_slab<false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   }
   k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, half ? w->FB16 : w->FB,
                                                              R, R_F, S,

@@ -144,14 +144,18 @@ def _variant(v):
 
 @pytest.mark.parametrize("kernel,R,R_F", [("periodic", 33, 21), ("box", 33, 21),
                                            ("periodic", 40, 10), ("periodic", 33, 33),
-                                           ("periodic", 13, 8), ("periodic", 31, 20)],
+                                           ("periodic", 13, 8), ("periodic", 31, 20),
+                                           ("periodic", 48, 48)],
                          ids=["periodic-R33-RF21", "box-R33-RF21", "narrow-band-R40-RF10",
-                              "full-band-R33-RF33", "grid27-R13-RF8", "grid63-R31-RF20"])
+                              "full-band-R33-RF33", "grid27-R13-RF8", "grid63-R31-RF20",
+                              "wide-band-R48-RF48"])
 def test_slab_kernel_vs_chain_and_oracle(dev, kernel, R, R_F):
-    """The fused tensor-core slab kernel (grid sides 27 to 81, operands padded to 128;
-    occupied bands of width 17 to 67, so the products run over 32 to 80 of the 128 padded
+    """The fused tensor-core slab kernel (grid sides 27 to 97, operands padded to 128;
+    occupied bands of width 17 to 97, so the products run over 32 to 112 of the 128 padded
     columns) element by element against the five-launch step chain on the same handle, and
-    against the FP64 oracle on sampled basis functions and on E_x."""
+    against the FP64 oracle on sampled basis functions and on E_x.  Periodic bands of at
+    most 96 columns add the A term on the tensor cores (F_s times a one-hot P_x); the
+    112-column band of R = 48, R_F = 48 takes the per-column gather of the A term."""
     import paper_1502_08043_gb300 as cc
     L = 30.0
     if kernel == "periodic":
