@@ -184,6 +184,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (uint32_t o = 16u * tid; o < kOp; o += 16u * kThreads)
     *reinterpret_cast<uint4*>(gb + kOffR + o) = make_uint4(0u, 0u, 0u, 0u);
+  if (kMmaA)  // P starts all zero; every build then moves the one of each row
+    for (uint32_t o = 16u * tid; o < kMmaABand * 128u; o += 16u * kThreads)
+      *reinterpret_cast<uint4*>(gb + kOffP + o) = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int hw0 = 11 * bw;
     uint32_t nf0 = __ldg(frow(u0, 0) + lane), nf1 = __ldg(frow(u0, 0) + lane + 32);
     uint32_t r = 0;
+    int p_h = -1;  // the h of this thread's row of P as it stands (-1: zero row)
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u) {
       for (int j = 0; j < 2 && ok; ++j, ++r) {
@@ -426,17 +430,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if constexpr (kMmaA) {
           // P_x for x = 2 p + j: band row rr (z = zs + rr) is one-hot at h(x, z), zero
-          // outside the sphere; 16-byte chunk c holds h = 8 c .. 8 c + 7 (128-byte swizzle)
-          const int dx = (int)(2 * (u / S) + j) - R;
-          for (int t = bt; t < nact * 8; t += kBldThreads) {
-            const int rr = t >> 3, c = t & 7, dz = zs + rr - R;
+          // outside the sphere; 16-byte chunk c holds h = 8 c .. 8 c + 7 (128-byte swizzle).
+          // Builder thread rr owns row rr and moves its one: the chunk of the previous h is
+          // cleared, the chunk of the new h written (at most two 16-byte stores)
+          if (bt < nact) {
+            const int rr = bt, dz = zs + rr - R, dx = (int)(2 * (u / S) + j) - R;
             const int q = RF * RF - dx * dx - dz * dz;
             const int h = q >= 0 ? (int)isq[q] : -1;
-            const bool hit = h >= 0 && (h >> 3) == c;
-            const uint32_t one = 0x3F80u << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
-            const uint4 v = make_uint4(hit && wi == 0 ? one : 0u, hit && wi == 1 ? one : 0u,
-                                       hit && wi == 2 ? one : 0u, hit && wi == 3 ? one : 0u);
-            *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + ((c ^ (rr & 7)) << 4)) = v;
+            if (h != p_h) {
+              if (p_h >= 0)
+                *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 +
+                                          (((p_h >> 3) ^ (rr & 7)) << 4)) =
+                    make_uint4(0u, 0u, 0u, 0u);
+              if (h >= 0) {
+                const uint32_t one = 0x3F80u << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
+                *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((h >> 3) ^ (rr & 7)) << 4)) =
+                    make_uint4(wi == 0 ? one : 0u, wi == 1 ? one : 0u, wi == 2 ? one : 0u,
+                               wi == 3 ? one : 0u);
+              }
+              p_h = h;
+            }
           }
         }
         fence_proxy_async_smem();
@@ -459,13 +472,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the A-term MMAs read F_s of unit uu from tensor memory: lane y, column kFhi + c
     // (kFlo + c) holds the bf16 hi (lo) pair of h = 2 c, 2 c + 1; this warp writes
     // h = 32 half .. 32 half + 31 of its lanes from the window-sum rows F_s[y][.]
-    auto stage_f = [&](long long uu) {
+    uint4 fpre[8];  // the next unit's row segment, loaded a unit ahead of its staging
+    auto load_f = [&](long long uu) {
       const uint4* src = reinterpret_cast<const uint4*>(
           g.FR + ((long long)(uu % S) * kN + yrow) * kHMax + 32 * half);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) fpre[i] = __ldg(src + i);
+    };
+    auto stage_f = [&]() {
       uint32_t hi[16], lo[16];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const uint4 f = __ldg(src + i);
+        const uint4 f = fpre[i];
         hi[2 * i] = __byte_perm(f.x, f.y, 0x5410);
         lo[2 * i] = __byte_perm(f.x, f.y, 0x7632);
         hi[2 * i + 1] = __byte_perm(f.z, f.w, 0x5410);
@@ -479,7 +497,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(ffull);
     };
     if constexpr (kMmaA) {
-      if (u0 < u1) stage_f(u0);
+      if (u0 < u1) {
+        load_f(u0);
+        stage_f();
+      }
     }
     for (long long u = u0; u < u1 && ok;) {
       const long long p = u / S;
@@ -499,6 +520,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = (int)(u % S);
         const float ws = g.w[s];
         const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
+        if constexpr (kMmaA) {
+          if (u + 1 < u1) load_f(u + 1);
+        }
         for (int j = 0; j < 2; ++j) {
           // the A-term values of this warp's columns, requested before the MMA result is
           // waited for (their L2 latency hides behind the wait)
@@ -520,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the second first mode product of this unit is done with F_s: the next unit's
           // goes into tensor memory (the MMA warp waits for it before that unit's first MMA)
           if constexpr (kMmaA) {
-            if (j == 1 && u + 1 < u1) stage_f(u + 1);
+            if (j == 1 && u + 1 < u1) stage_f();
           }
           // in place, 16 columns at a time: FP32 U of the piece z = zs + 16 m .. in columns
           // 16 m .. 16 m + 15 becomes 8 columns of bf16 hi pairs followed by 8 of lo pairs
