@@ -88,6 +88,41 @@ def test_ragged_sizes_paper_scale(dev, n):
     t.free()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ids16_alignment_forms(dev, prec):
+    """uint16-id quadruples on a 16-byte aligned buffer, on a buffer that is only 8-byte
+    aligned (the stated minimum) and with the output one value off its allocation: the
+    same values and counters bit for bit, and the oracle's."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    R, L = CFG2["R"], CFG2["L"]
+    t = _tables(CFG2)
+    a, w = oracle_nodes(R, CFG2["S"])
+    n = 4099
+    q = ci.quads(R, 777, n, stream=ci.STREAM_PLANTED)
+    q[3::1021, 2] = 65000  # out of range (also as a uint16 id)
+    ref, cnt_ref = orc.reconstruct(q, R, L, "separable", a=a, w=w)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    q16 = torch.from_numpy(as_ids16(q)).to(dev)
+    big = torch.zeros((n + 1, 4), dtype=torch.int16, device=dev)
+    big[1:] = q16
+    outs = []
+    for qin, shift in ((q16, 0), (big[1:], 0), (q16, 1)):
+        assert qin.is_contiguous()
+        ob_ = torch.full((n + 1,), float("nan"), dtype=dtype, device=dev)
+        out = ob_[shift:shift + n]
+        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+        cc.reconstruct_integrals(t, qin, out, lookup="collapsed", counters=cnt)
+        outs.append((out.cpu().numpy(), cnt.cpu().numpy()))
+    assert (big[1:].data_ptr() % 16) == 8
+    for got, cnt in outs:
+        assert np.array_equal(cnt, cnt_ref)
+        assert np.array_equal(got == 0, ref == 0)
+        assert np.array_equal(got, outs[0][0])
+    assert rel_err(outs[0][0], ref) < (TOL_FP64 if prec == "fp64" else TOL_FP32)
+    t.free()
+
+
 def _full_size(dev, cfg, n, sample):
     """Full-size batch generated on the GPU, both lookups as the bench launches them;
     sampled outputs recomputed by the oracle from its own copy of the inputs."""
