@@ -330,6 +330,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["batched"] = batched()
         line["large_lookups"] = large_lookups()
+        line["paper_replay"] = paper_replay()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -433,6 +434,91 @@ def batched(reps=10):
     out["pair_evals_per_batch"] = pairs
     B.free()
     return out
+
+
+# ---------------------------------------------------------------- paper replay: Table I, Fig. 1
+def _e_ks(M, L):
+    """Kohn-Sham exchange of M electrons per spin in a cube of side L, -(3/4)(6/pi)^(1/3)
+    M^(4/3) / L (Sec. III)."""
+    return -0.75 * (6.0 / np.pi) ** (1.0 / 3.0) * M ** (4.0 / 3.0) / L
+
+
+def _n_occupied(R_F):
+    """Integer vectors with |n|^2 <= R_F^2 (the occupied states of one spin)."""
+    r = np.arange(-R_F, R_F + 1)
+    return int(((r[:, None, None] ** 2 + r[None, :, None] ** 2 + r[None, None, :] ** 2)
+                <= R_F * R_F).sum())
+
+
+def _exchange_timed(t, R_F, prec, reps):
+    import torch
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev)
+    Mg = t.info["Mg"]
+    eps = torch.empty(Mg ** 3, dtype=torch.float64 if prec == "fp64" else torch.float32,
+                      device=dev)
+    Ex = torch.empty(2, dtype=torch.float64, device=dev)
+    import paper_1502_08043_gb300 as cc
+    cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(reps):
+        cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
+    b.record(st)
+    torch.cuda.synchronize()
+    return float(Ex[0].item()), a.elapsed_time(b) / reps
+
+
+def paper_replay(reps=5):
+    """Table I (M = 9171 parallel-spin electrons, L = 2 bohr, finite-box kernel, both meshes
+    of the paper) through the GPU box-kernel mode products in FP64, FP32 and bf16x3, each
+    ratio E_x / E_KS against the printed total; and Fig. 1 (E_x / E_KS against M^(-1/3) for
+    R_F = 1 .. 13, periodic kernel, |n| <= 13, L = 10, 64-node default mesh) with its
+    extrapolation to M -> infinity, which the paper puts at 1."""
+    import paper_1502_08043_gb300 as cc
+    rows = []
+    here = os.path.dirname(os.path.abspath(__file__))
+    for line in open(os.path.join(here, "tests", "golden", "table1.txt")):
+        if line.strip() and not line.startswith("#"):
+            mesh, par, _, total = line.split()
+            rows.append((mesh, int(par), float(total)))
+    ks = _e_ks(9171, 2.0)
+    table = []
+    for mesh, par, total in rows:
+        if mesh == "mesh1":
+            t = cc.build_tables("box", R=13, L=2.0, S=2 * par, n_sub=0, q_tail=par)
+        else:
+            t = cc.build_tables("box", R=13, L=2.0, S=8 * par + 90, n_sub=7, q_tail=90)
+        row = {"mesh": mesh, "param": par, "S": t.info["S_eff"], "paper_total": total}
+        for prec in ("fp64", "fp32", "bf16x3"):
+            ex, ms = _exchange_timed(t, 13, prec, reps)
+            row[prec] = ex / ks
+            row[prec + "_dev"] = ex / ks - total
+            row[prec + "_ms"] = ms
+        table.append(row)
+        t.free()
+    t = cc.build_tables("periodic", R=13, L=10.0, S=64)
+    fig = {"R_F": [], "M": [], "ratio_fp64": [], "ms_fp64": []}
+    for R_F in range(1, 14):
+        ex, ms = _exchange_timed(t, R_F, "fp64", reps)
+        M = _n_occupied(R_F)
+        fig["R_F"].append(R_F)
+        fig["M"].append(M)
+        fig["ratio_fp64"].append(ex / _e_ks(M, 10.0))
+        fig["ms_fp64"].append(ms)
+    t.free()
+    x = np.array(fig["M"], dtype=float) ** (-1.0 / 3.0)
+    y = np.array(fig["ratio_fp64"])
+    slope = (y[-1] - y[-2]) / (x[-1] - x[-2])
+    fig["extrapolated_M_inf"] = float(y[-1] - slope * x[-1])
+    fig["note"] = ("two-point linear extrapolation in M^(-1/3) from R_F = 12, 13; "
+                   "the paper's Fig. 1 data are not printed, only the trend and limit 1")
+    return {"table1": table,
+            "table1_max_abs_dev": {p: max(abs(r[p + "_dev"]) for r in table)
+                                   for p in ("fp64", "fp32", "bf16x3")},
+            "fig1": fig}
 
 
 def b_pair(b):
@@ -568,6 +654,8 @@ def main():
                     help="skip the batched-boxes and 1e9-lookup sections of the JSON line")
     ap.add_argument("--mp-only", default=None,
                     help="only run the mode-product comparison of this workload, print it")
+    ap.add_argument("--replay-only", action="store_true",
+                    help="only run the Table I / Fig. 1 replay through the GPU path, print it")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
@@ -577,6 +665,8 @@ def main():
         run_reference(args)
     elif args.mp_only:
         print(json.dumps({"mode_products": mode_products(args.mp_only, oracle_sample=0)}))
+    elif args.replay_only:
+        print(json.dumps({"paper_replay": paper_replay()}))
     else:
         run_gpu(args)
 
