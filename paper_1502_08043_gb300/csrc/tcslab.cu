@@ -16,12 +16,13 @@
 //   epi   U_j <- w_s U_j + w_s A_{s,x_j}, split into bf16 hi + lo, written back into the
 //         same tensor-memory columns (each 16-column piece becomes 8 hi + 8 lo columns)
 //   MMA2  E_j += U_j T_s                      (A = U_j from tensor memory, B = T_s)
-// Periodic bf16 boxes whose band is at most 96 columns wide form the A term on the tensor
-// cores instead of in the epilogue: A_{s,x} = F_s P_x with the one-hot P_x[z][h] =
-// [h(x, z) = h], exact in bf16, built with R; MMA1 adds F_s P_x (F_s hi and lo from the
-// tensor-memory columns the band leaves free, staged once per node by the epilogue warps)
-// to U_j, and the epilogue only scales and re-splits.  Both terms are non-negative, so the
-// sum has no cancellation.
+// Periodic boxes whose band is at most 96 columns wide form the A term on the tensor cores
+// instead of in the epilogue: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h],
+// exact in 16 bits, built with R; MMA1 adds F_s P_x (F_s hi and lo from the tensor-memory
+// columns the band leaves free, staged once per node by the epilogue warps) to U_j, and
+// the epilogue only scales and re-splits (fp16: F' = 2^j F and ones of 2^a, so the sum is
+// 2^(a + j) (T R + A) like T' R').  Both terms are non-negative, so the sum has no
+// cancellation.
 // for the two slabs x_0 = 2p, x_1 = 2p + 1 of the pair, issued in the order
 //   MMA1(i, 0), MMA2(i-1, 1), MMA1(i, 1), MMA2(i, 0)
 // so that the epilogue of one slab always overlaps two GEMMs of the other, the single
@@ -70,7 +71,7 @@ constexpr uint32_t kOffR = 2 * kOp;         // the R operand
 // l (entry h of copy l at word 32 h + l): conflict-free gathers; two of them alternate
 constexpr uint32_t kFtabBytes = kHMax * 32 * 4;  // 8 KB
 constexpr uint32_t kOffFtab = 3 * kOp;
-// periodic bf16 boxes whose band is at most 96 columns wide add the A term on the tensor
+// periodic boxes whose band is at most 96 columns wide add the A term on the tensor
 // cores: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h] (band rows z, K = h),
 // F_s as bf16 hi and lo in the tensor-memory columns the band leaves free in U_0 and U_1
 constexpr int kMmaABand = 96;
@@ -89,6 +90,7 @@ struct Args {
   const uint32_t* FR;  // [S][128][64] F_s[x][h] as bf16 hi (low half) | lo (high half)
   const float* FW;     // [S][64][128] w_s F_s[y][h], h-major (periodic)
   const float* w;      // [S]
+  const int* aexp;     // [S] fp16: T' = 2^a T, the one-hot entries of P are 2^a
   float* part;         // [pairs * maxseg][2][128][128] partial E of a slab pair
   int* err;
   int stall_test;
@@ -431,25 +433,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (kMmaA) {
           // P_x for x = 2 p + j: band row rr (z = zs + rr) is one-hot at h(x, z), zero
           // outside the sphere; 16-byte chunk c holds h = 8 c .. 8 c + 7 (128-byte swizzle).
-          // Builder thread rr owns row rr and moves its one: the chunk of the previous h is
-          // cleared, the chunk of the new h written (at most two 16-byte stores)
+          // The one is bf16 1 or, fp16, the node's 2^a (so that F' = 2^j F times P gives
+          // 2^(a + j) A, the scale of T' R').  Builder thread rr owns row rr: the chunk of
+          // the previous h is cleared, the chunk of the new h written (at most two 16-byte
+          // stores; bf16 skips both while h stays)
           if (bt < nact) {
             const int rr = bt, dz = zs + rr - R, dx = (int)(2 * (u / S) + j) - R;
             const int q = RF * RF - dx * dx - dz * dz;
             const int h = q >= 0 ? (int)isq[q] : -1;
-            if (h != p_h) {
-              if (p_h >= 0)
-                *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 +
-                                          (((p_h >> 3) ^ (rr & 7)) << 4)) =
-                    make_uint4(0u, 0u, 0u, 0u);
-              if (h >= 0) {
-                const uint32_t one = 0x3F80u << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
-                *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((h >> 3) ^ (rr & 7)) << 4)) =
-                    make_uint4(wi == 0 ? one : 0u, wi == 1 ? one : 0u, wi == 2 ? one : 0u,
-                               wi == 3 ? one : 0u);
-              }
-              p_h = h;
+            if (p_h >= 0 && p_h != h)
+              *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((p_h >> 3) ^ (rr & 7)) << 4)) =
+                  make_uint4(0u, 0u, 0u, 0u);
+            if (h >= 0 && (kHalf || h != p_h)) {
+              const uint32_t v1 =
+                  kHalf ? (uint32_t)(0x3C00 + 1024 * g.aexp[(int)(u % S)]) : 0x3F80u;
+              const uint32_t one = v1 << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
+              *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((h >> 3) ^ (rr & 7)) << 4)) =
+                  make_uint4(wi == 0 ? one : 0u, wi == 1 ? one : 0u, wi == 2 ? one : 0u,
+                             wi == 3 ? one : 0u);
             }
+            p_h = h;
           }
         }
         fence_proxy_async_smem();
@@ -977,6 +980,7 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   a.FR = half ? w->FR16 : w->FR;
   a.FW = half ? w->FW16 : w->FW;
   a.w = half ? w->w16 : w->w32;
+  a.aexp = half ? w->aexp : nullptr;
   a.part = w->part;
   a.err = err;
   a.stall_test = stall_test;
@@ -992,15 +996,20 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
     CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slab_smem_bytes(63)));
+    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)slab_smem_bytes(63)));
     attr = slab_smem_bytes(63);
   }
   // the A term on the tensor cores where the band leaves tensor memory free for F_s
-  const bool mma_a =
-      !half && periodic && ((R + R_F + 16) & ~15) - ((R - R_F) & ~15) <= kMmaABand;
+  const bool mma_a = periodic && ((R + R_F + 16) & ~15) - ((R - R_F) & ~15) <= kMmaABand;
   if (half) {
     const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(w->map16_hi);
     const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(w->map16_lo);
-    k_tc_slab<true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    if (mma_a)
+      k_tc_slab<true, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    else
+      k_tc_slab<true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   } else {
     const CUtensorMap& mh =
         *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);

@@ -190,12 +190,15 @@ def test_slab_kernel_vs_chain_and_oracle(dev, kernel, R, R_F):
 
 
 @pytest.mark.parametrize("kernel,R,R_F", [("periodic", 33, 21), ("box", 33, 21),
-                                           ("periodic", 13, 8)],
-                         ids=["periodic-R33-RF21", "box-R33-RF21", "grid27-R13-RF8"])
+                                           ("periodic", 13, 8), ("periodic", 48, 48)],
+                         ids=["periodic-R33-RF21", "box-R33-RF21", "grid27-R13-RF8",
+                              "wide-band-R48-RF48"])
 def test_slab_kernel_fp16x3_vs_chain_and_oracle(dev, kernel, R, R_F):
     """fp16x3 through the slab kernel (per-node power-of-two scales of T, the window sums
     and the intermediate) element by element against the fp16x3 step chain, and against the
-    FP64 oracle on sampled basis functions and on E_x."""
+    FP64 oracle on sampled basis functions and on E_x.  Periodic bands of at most 96
+    columns take the A term on the tensor cores (ones of 2^a in P), the 112-column band of
+    R = 48, R_F = 48 the per-column gather."""
     import paper_1502_08043_gb300 as cc
     L = 30.0
     if kernel == "periodic":
