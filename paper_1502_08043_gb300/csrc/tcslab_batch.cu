@@ -63,8 +63,15 @@ constexpr uint32_t kOffR = 2 * kOp;         // the R operand
 // l (entry h of copy l at word 32 h + l): conflict-free gathers; two of them alternate
 constexpr uint32_t kFtabBytes = kHMax * 32 * 4;  // 8 KB
 constexpr uint32_t kOffFtab = 3 * kOp;
-constexpr uint32_t kOffBar = kOffFtab + 2 * kFtabBytes;  // mbarriers, tensor-memory slot
-constexpr int kNumBars = 16;
+// batches whose boxes are all periodic with bands of at most 96 columns add the A term on
+// the tensor cores: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h] (band rows
+// of the box, K = h), F_s as bf16 hi and lo in the tensor-memory columns the band leaves
+// free in U_0 and U_1
+constexpr int kMmaABand = 96;
+constexpr uint32_t kOffP = kOffFtab + 2 * kFtabBytes;   // P_x, band rows x 128 bytes
+constexpr uint32_t kFhi = 96, kFlo = 224;               // F_s hi / lo columns
+constexpr uint32_t kOffBar = kOffP + kMmaABand * 128;  // mbarriers, tensor-memory slot
+constexpr int kNumBars = 17;
 constexpr uint32_t kOffIsq = kOffBar + 8 * kNumBars + 16;  // floor(sqrt(v)), v <= R_F^2
 __host__ __device__ constexpr uint32_t slab_smem_bytes(int R_F) {
   return kOffIsq + (((uint32_t)(R_F * R_F + 1) + 15u) & ~15u) + 1024u;
@@ -133,7 +140,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
 __device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-template <bool kBatch>
+template <bool kBatch, bool kMmaA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tcb_slab(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
               Args g) {
@@ -151,6 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t efull = bar + 8u * 10, edone = bar + 8u * 11;
   const uint32_t never = bar + 8u * 12, drain = bar + 8u * 13;
   auto ftfull = [&](int k) { return bar + 8u * (14 + k); };  // 14, 15
+  const uint32_t ffull = bar + 8u * 16;  // F_s of the next unit is in tensor memory
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
   __shared__ volatile int s_abort;
 
@@ -171,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(drain, 1);
     mbar_init(ftfull(0), kBldWarps);
     mbar_init(ftfull(1), kBldWarps);
+    mbar_init(ffull, kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -190,6 +199,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (uint32_t o = 16u * tid; o < kOp; o += 16u * kThreads)
     *reinterpret_cast<uint4*>(gb + kOffR + o) = make_uint4(0u, 0u, 0u, 0u);
+  if (kMmaA)  // P starts all zero; every build then moves the one of each row
+    for (uint32_t o = 16u * tid; o < kMmaABand * 128u; o += 16u * kThreads)
+      *reinterpret_cast<uint4*>(gb + kOffP + o) = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -242,9 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // N = the grid side rounded up to 16 (columns z' >= Mg are never read).  Descriptors
       // as base + constant: the start-address field holds address / 16, so a byte offset o
       // (all addresses < 256 KB) adds o / 16
-      int ms = 0, me = 0;
+      int ms = 0, me = 0, nh = 0;  // nh: K steps of the A-term MMAs (h < 16 nh)
       uint32_t idesc1 = 0, idesc2 = 0;
       uint64_t dR = 0;  // B rows z = zs ..
+      const uint64_t dP = sdesc(base + kOffP);
       auto mma1 = [&](uint32_t tb, int j) {
         const uint32_t d = tmem + (uint32_t)(j * 128);
         const uint64_t dT = sdesc(tb);
@@ -255,6 +268,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           const uint32_t acc = m > ms ? 1u : 0u;
           mma_x3_w(d, dT + o, dR + o, kPl, kPl, idesc1, acc);
+        }
+        if constexpr (kMmaA) {  // + F_s P_x: A = F_s hi and lo from tensor memory
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (m < nh)
+              mma_x2_ts_w(d, tmem + kFhi + 8u * m, tmem + kFlo + 8u * m, dP + 2u * m, idesc1);
         }
       };
       auto mma2 = [&](uint32_t tb, int j, bool first) {
@@ -283,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int zs = band_lo(bx), ze = band_hi(bx);
         ms = zs >> 4;
         me = ze >> 4;
+        nh = (kMmaA && bx.periodic) ? (bx.RF + 16) >> 4 : 0;
         idesc1 = idesc0 | ((uint32_t)((ze - zs) >> 3) << 17);
         idesc2 = idesc0 | ((uint32_t)(((bx.Mg + 15) & ~15) >> 3) << 17);
         dR = sdesc(base + kOffR + (uint32_t)zs * 128u);
@@ -291,7 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t tbp = base + kOffT + (k ^ 1u) * kOp;
           // MMA1(i, 0)
           ok = all(mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
-                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort));
+                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort) &&
+                   (!kMmaA || mbar_wait(ffull, n & 1u, g.err, 18, &s_abort)));
           if (!ok) break;
           tc_fence_after();
           mma1(tb, 0);
@@ -353,6 +374,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kMaxTasks = 6;  // (R_F + 1) x chunks <= 64 x 16 = 1024 = 5.3 x 192
     uint32_t hb[kMaxTasks][2];
     int cur = -1, R = 0, RF = 0, zlo = 0, clo = 0, nc = 1, tasks = 0;
+    int zsb = 0, nactb = 0, perb = 0, Sb = 1;  // the box's band, kernel and node count
+    long long unit0b = 0;
+    int p_h = -1;  // the h of this thread's row of P as it stands (-1: zero row)
     auto frow = [&](int b, long long u, int j) {
       const SlabBox bx = box_ref<kBatch>(g, b);
       const long long l = u - bx.unit0;
@@ -371,6 +395,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const SlabBox bx = box_ref<kBatch>(g, b);
         R = bx.R;
         RF = bx.RF;
+        zsb = band_lo(bx);
+        nactb = band_hi(bx) - zsb;
+        perb = bx.periodic;
+        Sb = bx.S;
+        unit0b = bx.unit0;
         zlo = R - RF;
         clo = (R - RF) >> 3;
         nc = ((R + RF) >> 3) - clo + 1;
@@ -407,6 +436,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!ok) break;
           for (uint32_t o = 16u * bt; o < kOp; o += 16u * kBldThreads)
             *reinterpret_cast<uint4*>(gb + kOffR + o) = make_uint4(0u, 0u, 0u, 0u);
+          if (kMmaA) {  // and P: its rows are band rows of the previous box
+            for (uint32_t o = 16u * bt; o < kMmaABand * 128u; o += 16u * kBldThreads)
+              *reinterpret_cast<uint4*>(gb + kOffP + o) = make_uint4(0u, 0u, 0u, 0u);
+            p_h = -1;
+          }
         }
         // every warp has finished build r - 2, so table (r & 1) is free
         uint32_t* ft = reinterpret_cast<uint32_t*>(gb + kOffFtab + (r & 1u) * kFtabBytes);
@@ -457,6 +491,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+        if constexpr (kMmaA) {
+          // P_x for x = 2 p + j: band row rr (z = zs + rr) is one-hot (bf16 1) at h(x, z),
+          // zero outside the sphere; 16-byte chunk c holds h = 8 c .. 8 c + 7 (128-byte
+          // swizzle).  Builder thread rr owns row rr and moves its one.
+          if (perb && bt < nactb) {
+            const int rr = bt, dz = zsb + rr - R;
+            const int dx = (int)(2 * ((u - unit0b) / Sb) + j) - R;
+            const int q = RF * RF - dx * dx - dz * dz;
+            const int h = q >= 0 ? (int)isq[q] : -1;
+            if (p_h >= 0 && p_h != h)
+              *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((p_h >> 3) ^ (rr & 7)) << 4)) =
+                  make_uint4(0u, 0u, 0u, 0u);
+            if (h >= 0 && h != p_h) {
+              const uint32_t one = 0x3F80u << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
+              *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((h >> 3) ^ (rr & 7)) << 4)) =
+                  make_uint4(wi == 0 ? one : 0u, wi == 1 ? one : 0u, wi == 2 ? one : 0u,
+                             wi == 3 ? one : 0u);
+            }
+            p_h = h;
+          }
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(rfull);
@@ -472,6 +527,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t n = 0, segc = 0;
     bool ok = true;
     int b = 0;
+    // the A-term MMAs read F_s of unit uu from tensor memory: lane y, column kFhi + c
+    // (kFlo + c) holds the bf16 hi (lo) pair of h = 2 c, 2 c + 1; this warp writes
+    // h = 32 half .. 32 half + 31 of its lanes from the box's rows F_s[y][h], y <= Mg,
+    // h <= R_F (zero elsewhere), loaded a unit ahead of the staging
+    uint32_t fpre[32];
+    auto load_f = [&](long long uu, int bb) {
+      const SlabBox fx = box_ref<kBatch>(g, bb);
+      const long long l = uu - fx.unit0;
+      const uint32_t* row = g.FR + fx.fr_off + ((l % fx.S) * (fx.Mg + 1) + yrow) * fx.frs;
+      const bool rowok = yrow <= fx.Mg;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int h = 32 * half + i;
+        fpre[i] = (rowok && h <= fx.RF) ? __ldg(row + h) : 0u;
+      }
+    };
+    auto stage_f = [&]() {
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        hi[c] = __byte_perm(fpre[2 * c], fpre[2 * c + 1], 0x5410);
+        lo[c] = __byte_perm(fpre[2 * c], fpre[2 * c + 1], 0x7632);
+      }
+      tmem_st16(tmem + lane_off + kFhi + 16u * half, hi);
+      tmem_st16(tmem + lane_off + kFlo + 16u * half, lo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ffull);
+    };
+    if constexpr (kMmaA) {
+      if (u0 < u1) {
+        load_f(u0, advance_box<kBatch>(g, 0, u0));
+        stage_f();
+      }
+    }
     for (long long u = u0; u < u1 && ok;) {
       b = advance_box<kBatch>(g, b, u);
       const SlabBox bx = box_ref<kBatch>(g, b);
@@ -488,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < 2; ++k) {
           const int dx = (int)(2 * p + j) - R, dz = zs + 32 * (2 * half + k) + lane - R;
           const int q = RF * RF - dx * dx - dz * dz;
-          hz[j][k] = q >= 0 ? (int)isq[q] : -1;
+          hz[j][k] = (!kMmaA && q >= 0) ? (int)isq[q] : -1;
         }
       const long long fw_node = (long long)bx.frs * bx.fws;
       const int fws = bx.fws, periodic = bx.periodic;
@@ -499,7 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = (int)((u - unit0) % S);
         const float ws = wb[s];
         const float* FWs = FWb + s * fw_node + yrow;
-        if (periodic && u + 1 < ue) {
+        if constexpr (kMmaA) {
+          if (u + 1 < u1) load_f(u + 1, advance_box<kBatch>(g, b, u + 1));
+        }
+        if (!kMmaA && periodic && u + 1 < ue) {
           // the next unit's A-term table into L1 ahead of its use
           const long long lines = (fw_node * 4 + 127) / 128;
           if (tid < lines) {
@@ -522,16 +616,23 @@ __global__ void __launch_bounds__(kThreads, 1)
               a[kBatch ? 0 : k][e] = (periodic && h >= 0) ? __ldg(FWs + h * fws) : 0.0f;
             }
           };
-          load_a(0);
-          if (!kBatch) load_a(1);
+          if constexpr (!kMmaA) {
+            load_a(0);
+            if (!kBatch) load_a(1);
+          }
           ok = mbar_wait(d1full(j), n & 1u, g.err, 31, &s_abort);
           if (!ok) break;
           tc_fence_after();
+          // the unit's second first mode product is done with F_s: the next unit's goes
+          // into tensor memory (the MMA warp waits for it before that unit's first MMA)
+          if constexpr (kMmaA) {
+            if (j == 1 && u + 1 < u1) stage_f();
+          }
           // in place, 16 columns at a time: FP32 U of the piece z = zs + 16 m .. in columns
           // 16 m .. 16 m + 15 becomes 8 columns of bf16 hi pairs followed by 8 of lo pairs
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            if (kBatch && k == 1) load_a(1);
+            if (!kMmaA && kBatch && k == 1) load_a(1);
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
               if (32 * (2 * half + k) + 16 * sub >= nact) continue;  // beyond the band
@@ -542,9 +643,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t hi[8], lo[8];
 #pragma unroll
               for (int e = 0; e < 16; e += 2) {
-                const float x0 = fmaf(__uint_as_float(v[e]), ws, a[kBatch ? 0 : k][16 * sub + e]);
-                const float x1 =
-                    fmaf(__uint_as_float(v[e + 1]), ws, a[kBatch ? 0 : k][16 * sub + e + 1]);
+                float x0, x1;
+                if constexpr (kMmaA) {  // U already holds T_s R + A
+                  x0 = __uint_as_float(v[e]) * ws;
+                  x1 = __uint_as_float(v[e + 1]) * ws;
+                } else {
+                  x0 = fmaf(__uint_as_float(v[e]), ws, a[kBatch ? 0 : k][16 * sub + e]);
+                  x1 = fmaf(__uint_as_float(v[e + 1]), ws, a[kBatch ? 0 : k][16 * sub + e + 1]);
+                }
                 const uint32_t h = pack_bf16x2(x0, x1);
                 hi[e >> 1] = h;
                 lo[e >> 1] = pack_bf16x2(x0 - bf16_lo_f(h), x1 - bf16_hi_f(h));
@@ -736,6 +842,7 @@ namespace {
 // with 128-row boxes: rows past a node only feed output rows y' >= Mg, never read.
 struct SlabPlan {
   int grid = 0, units = 0, maxseg = 0, rf_max = 0, nbox = 0;
+  bool mma_a = false;  // every box periodic with a band of at most 96 columns
   long long rows = 0;
   uint32_t* FR = nullptr;
   float* FW = nullptr;
@@ -881,7 +988,10 @@ cc_status plan_launch(SlabPlan* w, int* err, int stall_test, float* eps, double*
   const uint32_t smem = slab_smem_bytes(w->rf_max);
   const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(w->map_hi);
   const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(w->map_lo);
-  k_tcb_slab<true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+  if (w->mma_a)
+    k_tcb_slab<true, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+  else
+    k_tcb_slab<true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   k_tcb_finalize<<<(unsigned)((w->rows + 7) / 8), 256, 0, st>>>(a, w->grid, w->FB, w->rows,
                                                                     eps, w->row_ex);
   k_tcb_ex<<<w->nbox, 1024, 0, st>>>(a, w->row_ex, Ex, err, err + 1);
@@ -892,7 +1002,11 @@ cc_status plan_launch(SlabPlan* w, int* err, int stall_test, float* eps, double*
 cc_status set_smem_attr() {
   static bool done = false;
   if (!done) {
-    CC_CUDA(cudaFuncSetAttribute(k_tcb_slab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CC_CUDA(cudaFuncSetAttribute(k_tcb_slab<true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)slab_smem_bytes(63)));
+    CC_CUDA(cudaFuncSetAttribute(k_tcb_slab<true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slab_smem_bytes(63)));
     done = true;
   }
@@ -928,6 +1042,10 @@ cc_status tc_slab_batch_create(const std::vector<cc_tables>& tabs, const std::ve
     boxes.back().eps_off = eps_off[b];
     w->rf_max = std::max(w->rf_max, R_F[b]);
   }
+  w->mma_a = true;
+  for (const SlabBox& bx : boxes)
+    if (!bx.periodic || ((bx.R + bx.RF + 16) & ~15) - ((bx.R - bx.RF) & ~15) > kMmaABand)
+      w->mma_a = false;
   if (st == CC_OK) {
     plan_partition(w, boxes);
     long long nFR, nFW, nFB, nW, nPart;
