@@ -654,6 +654,8 @@ def main():
                     help="skip the batched-boxes and 1e9-lookup sections of the JSON line")
     ap.add_argument("--mp-only", default=None,
                     help="only run the mode-product comparison of this workload, print it")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only run the 256-box batched section, print it")
     ap.add_argument("--replay-only", action="store_true",
                     help="only run the Table I / Fig. 1 replay through the GPU path, print it")
     ap.add_argument("--traffic", type=float, default=None,
@@ -667,6 +669,8 @@ def main():
         print(json.dumps({"mode_products": mode_products(args.mp_only, oracle_sample=0)}))
     elif args.replay_only:
         print(json.dumps({"paper_replay": paper_replay()}))
+    elif args.batched_only:
+        print(json.dumps({"batched": batched()}))
     else:
         run_gpu(args)
 
