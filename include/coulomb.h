@@ -150,6 +150,18 @@ cc_status cc_tables_free(cc_tables t);
  * S nodes at cutoff R (host only, no GPU): see the default rule above. */
 cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail);
 
+/* Fewest nodes for a stated method error (host only, no GPU; Sec. II: the node count
+ * follows from the accuracy wanted over the range of |q|^2 the cutoff R allows).  Returns
+ * in *S the smallest S in 2 .. S_max whose default mesh (n_sub, q_tail), as chosen by the
+ * default rule above, has a periodic-kernel error max_m |sum_s w_s exp(-a_s m) - 1/m| m
+ * (the 96 points of the default rule) of at most target, with that mesh in *n_sub,
+ * *q_tail and its error in *err (if not NULL).  Errors below about 1e-10 are FP64
+ * rounding noise.  CC_ERR_ARG for NULL outputs or a target that is not positive and
+ * finite; CC_ERR_RANGE for R outside 1 .. 127, S_max outside 2 .. 1024, or when no S up to
+ * S_max reaches the target. */
+cc_status cc_mesh_for_error(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
+                            double* err);
+
 /* Basis of cutoff R (Sec. II Eq. 1 with |n|^2 <= R^2) in canonical order.  Writes the
  * count to *Nb; if vec_host is not NULL it must hold 4 * Nb int8 and receives
  * (n_x, n_y, n_z, 0) per function.  1 <= R <= 127. */

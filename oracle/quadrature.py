@@ -132,6 +132,18 @@ def default_periodic_mesh(S: int, R: int):
     return arg
 
 
+def mesh_for_error(R: int, target: float, S_max: int):
+    """The fewest nodes S in 2 .. S_max whose default mesh reaches mesh_error <= target
+    (the node count as a function of the accuracy wanted, Sec. II): (S, n_sub, q_tail,
+    error), or None when no S up to S_max does."""
+    for S in range(2, S_max + 1):
+        n_sub, q_tail = default_periodic_mesh(S, R)
+        e = mesh_error(S, n_sub, q_tail, R)
+        if e <= target:
+            return S, n_sub, q_tail, e
+    return None
+
+
 def prune_periodic(alpha_idx, w, R: int, tol: float):
     """Keep-mask of nodes for the periodic kernel in index units.
 

@@ -72,6 +72,8 @@ SIGNATURES = {
     "cc_tables_free": (_I, [_P]),
     "cc_basis": (_I, [_I, ctypes.POINTER(_I), _P]),
     "cc_default_mesh": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "cc_mesh_for_error": (_I, [_I, ctypes.c_double, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "cc_reconstruct_integrals": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _P]),
     "cc_pair_matrix": (_I, [_P, _I64, _I64, _I, _I, _P, _P]),
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -218,6 +220,19 @@ def default_mesh(S: int, R: int):
     _check("cc_default_mesh", lib().cc_default_mesh(int(S), int(R), ctypes.byref(n),
                                                     ctypes.byref(q)))
     return n.value, q.value
+
+
+def mesh_for_error(R: int, target: float, S_max: int = 1024):
+    """cc_mesh_for_error: (S, n_sub, q_tail, error) of the fewest nodes whose default mesh
+    reaches the stated method error."""
+    S = ctypes.c_int()
+    n = ctypes.c_int()
+    q = ctypes.c_int()
+    e = ctypes.c_double()
+    _check("cc_mesh_for_error", lib().cc_mesh_for_error(int(R), float(target), int(S_max),
+                                                        ctypes.byref(S), ctypes.byref(n),
+                                                        ctypes.byref(q), ctypes.byref(e)))
+    return S.value, n.value, q.value, e.value
 
 
 def basis(R: int) -> np.ndarray:

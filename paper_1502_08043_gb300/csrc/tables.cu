@@ -559,6 +559,29 @@ cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail) {
   return CC_OK;
 }
 
+// Smallest node count S in 2 .. S_max whose default mesh (default_mesh above, the
+// tabulated workloads included) has mesh_error <= target: the inverse of the default rule,
+// fewest nodes for a stated method error (Sec. II: the node count follows from the
+// accuracy wanted over the range of |q|^2 the cutoff allows).
+cc_status cc_mesh_for_error(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
+                            double* err) {
+  if (!S || !n_sub || !q_tail || !(target > 0.0) || !std::isfinite(target)) return CC_ERR_ARG;
+  if (R < 1 || R > kMaxR || S_max < 2 || S_max > kMaxS) return CC_ERR_RANGE;
+  for (int s = 2; s <= S_max; ++s) {
+    int n = -1, q = -1;
+    default_mesh(s, R, &n, &q);
+    const double e = mesh_error(s, n, q, R);
+    if (e <= target) {
+      *S = s;
+      *n_sub = n;
+      *q_tail = q;
+      if (err) *err = e;
+      return CC_OK;
+    }
+  }
+  return CC_ERR_RANGE;
+}
+
 cc_status cc_basis(int R, int* Nb, int8_t* vec_host) {
   if (!Nb) return CC_ERR_ARG;
   if (R < 1 || R > kMaxR) return CC_ERR_RANGE;

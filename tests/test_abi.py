@@ -70,3 +70,25 @@ def test_library_mesh_rule_equals_oracle_rule(lib):
     cases |= {(32, 4), (64, 13), (96, 31), (128, 63), (40, 9), (17, 2), (36, 5), (4, 3), (2, 1)}
     for S, R in sorted(cases):
         assert lib.default_mesh(S, R) == oq.default_periodic_mesh(S, R), (S, R)
+
+
+def test_library_mesh_for_error_equals_oracle(lib):
+    """Fewest nodes for a stated method error (the inverse of the default rule): library
+    and oracle give the same (S, n_sub, q_tail); that mesh reaches the target and the
+    default mesh of S - 1 nodes does not."""
+    from oracle import quadrature as oq
+    for R in (4, 13, 31):
+        for target in (1e-4, 1e-7):
+            got = lib.mesh_for_error(R, target, 200)
+            ref = oq.mesh_for_error(R, target, 200)
+            assert ref is not None, (R, target)
+            assert got[:3] == ref[:3], (R, target, got, ref)
+            assert got[3] <= target and abs(got[3] - ref[3]) <= 1e-9 * target + 1e-15
+            S = got[0]
+            if S > 2:
+                n, q = oq.default_periodic_mesh(S - 1, R)
+                assert oq.mesh_error(S - 1, n, q, R) > target
+    with pytest.raises(lib.CoulombError):
+        lib.mesh_for_error(4, 1e-30, 8)   # not reachable with 8 nodes
+    with pytest.raises(lib.CoulombError):
+        lib.mesh_for_error(4, -1.0, 8)
