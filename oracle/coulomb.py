@@ -101,6 +101,55 @@ def A_box(alpha, Delta, L: float, points: int = BOX_GL_POINTS):
     return out
 
 
+def A_box_general(alpha, D1, D2, L: float, points: int = BOX_GL_POINTS):
+    """Per-axis integral of the box kernel for a general (not necessarily momentum-
+    conserving) quadruple (Sec. II Eq. 8 with box-normalised planewaves on [0, L]):
+        A(alpha, D1, D2) = 1/L^2 int_0^L int_0^L g(x - x') exp(2 pi i (D1 x + D2 x') / L)
+                           dx dx',   g(u) = sqrt(pi/alpha) exp(-u^2 / (4 alpha)),
+    with D1 = J_x - I_x (the pair at r) and D2 = L_x - K_x (the pair at r').  With
+    u = x - x' the x integral at fixed u is elementary because D1 + D2 is an integer:
+        D1 + D2 = 0:  2/L^2 int_0^L (L - u) cos(2 pi D1 u / L) g(u) du   (= A_box),
+        otherwise:    -1/(pi (D1 + D2) L) int_0^L g(u) (sin(2 pi D1 u / L)
+                                                         + sin(2 pi D2 u / L)) du,
+    real and symmetric in (D1, D2).  Gauss-Legendre on [0, min(L, 14 sqrt(alpha))] as in
+    A_box.  D1, D2: int arrays of one shape; returns float64[len(alpha), *shape]."""
+    alpha = np.atleast_1d(np.asarray(alpha, dtype=np.float64))
+    D1 = np.asarray(D1, dtype=np.int64)
+    D2 = np.asarray(D2, dtype=np.int64)
+    shape = np.broadcast(D1, D2).shape
+    d1 = np.broadcast_to(D1, shape).reshape(-1).astype(np.float64)
+    d2 = np.broadcast_to(D2, shape).reshape(-1).astype(np.float64)
+    sig = d1 + d2
+    out = np.empty((alpha.size, d1.size))
+    for s, al in enumerate(alpha):
+        ub = min(L, 14.0 * np.sqrt(al))
+        u, wu = gauss_legendre(points, 0.0, ub)
+        g = np.sqrt(np.pi / al) * np.exp(-u * u / (4.0 * al))
+        c = np.cos(2.0 * np.pi * np.outer(d1, u) / L)
+        sn = np.sin(2.0 * np.pi * np.outer(d1, u) / L) + np.sin(2.0 * np.pi * np.outer(d2, u) / L)
+        cons = 2.0 / L ** 2 * ((L - u) * g * wu) @ c.T
+        with np.errstate(divide="ignore", invalid="ignore"):
+            gen = -(sn @ (g * wu)) / (np.pi * sig * L)
+        out[s] = np.where(sig == 0, cons, gen)
+    return out.reshape((alpha.size,) + shape)
+
+
+def V_box_general(nI, nJ, nK, nL, alpha, omega, L: float):
+    """(IJ|KL) of the box kernel for any quadruple of planewave index vectors ([..., 3]),
+    momentum-conserving or not: 1/(2 pi^2) sum_s omega_s prod_x A(alpha_s, D1_x, D2_x)
+    with D1 = n_J - n_I, D2 = n_L - n_K (the Eq. 14 node sum of Eq. 8)."""
+    D1 = np.asarray(nJ, dtype=np.int64) - np.asarray(nI, dtype=np.int64)
+    D2 = np.asarray(nL, dtype=np.int64) - np.asarray(nK, dtype=np.int64)
+    shape = D1.shape[:-1]
+    D1 = D1.reshape(-1, 3)
+    D2 = D2.reshape(-1, 3)
+    acc = np.zeros(D1.shape[0])
+    for s in range(len(alpha)):
+        A = [A_box_general(alpha[s], D1[:, x], D2[:, x], L)[0] for x in range(3)]
+        acc += omega[s] * A[0] * A[1] * A[2]
+    return (acc / (2.0 * np.pi ** 2)).reshape(shape)
+
+
 def box_table(alpha, Dmax: int, L: float):
     """A(alpha_s, D) for D = 0..Dmax: float64[S, Dmax + 1]."""
     return A_box(alpha, np.arange(Dmax + 1), L)

@@ -153,3 +153,51 @@ def test_table1_reproduced(mesh, q, int1, total, hist13):
     ks = ox.E_KS(M, L)
     assert abs(e1 / ks - int1) < 2e-6
     assert abs((e1 + e2) / ks - total) < 2e-6
+
+
+def test_box_general_axis_integral_brute_force():
+    """The per-axis integral of a general (non-conserving) box quadruple, Eq. 8 with
+    box-normalised planewaves, against a brute-force 2D Gauss-Legendre quadrature of its
+    defining double integral (complex exponentials over the square, no substitution):
+    the closed-form inner integral of A_box_general, its signs and factors."""
+    from oracle.quadrature import gauss_legendre
+    L = 2.0
+    # composite rule on [0, L]: 40 panels of 8 points
+    edges = np.linspace(0.0, L, 41)
+    xs, ws = [], []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        x, w = gauss_legendre(8, lo, hi)
+        xs.append(x)
+        ws.append(w)
+    x = np.concatenate(xs)
+    w = np.concatenate(ws)
+    X, XP = np.meshgrid(x, x, indexing="ij")
+    W = np.outer(w, w)
+    pairs = [(0, 0), (1, -1), (2, 1), (-1, 2), (3, 0), (1, 1), (-2, -3), (4, -1)]
+    for al in (0.05, 0.4, 2.5):
+        g = np.sqrt(np.pi / al) * np.exp(-(X - XP) ** 2 / (4.0 * al))
+        got = oc.A_box_general(al, [p[0] for p in pairs], [p[1] for p in pairs], L)[0]
+        for (d1, d2), v in zip(pairs, got):
+            ph = np.exp(2j * np.pi * (d1 * X + d2 * XP) / L)
+            ref = np.sum(W * g * ph) / L ** 2
+            assert abs(ref.imag) < 1e-10
+            assert abs(v - ref.real) < 1e-9 * max(1.0, abs(ref.real)), (al, d1, d2, v, ref)
+
+
+def test_box_general_integrals_symmetries_and_conserving_case():
+    """(IJ|KL) = (KL|IJ) = (JI|LK) for the real box-kernel integrals of arbitrary quadruples,
+    and on momentum-conserving ones the general form equals the conserving node sum."""
+    a, w, _ = oq.paper_mesh2(6, 24)
+    L = 3.0
+    rng = np.random.default_rng(5)
+    n = rng.integers(-3, 4, size=(40, 4, 3))
+    I, J, K, Lq = n[:, 0], n[:, 1], n[:, 2], n[:, 3]
+    v = oc.V_box_general(I, J, K, Lq, a, w, L)
+    assert np.allclose(v, oc.V_box_general(K, Lq, I, J, a, w, L), rtol=1e-13, atol=0)
+    assert np.allclose(v, oc.V_box_general(J, I, Lq, K, a, w, L), rtol=1e-13, atol=0)
+    # conserving quadruples: L = K + I - J
+    Lc = K + I - J
+    vc = oc.V_box_general(I, J, K, Lc, a, w, L)
+    assert np.allclose(vc, oc.V_box_separable(J - I, a, w, L), rtol=1e-12, atol=0)
+    # non-conserving ones are not zero in a finite box
+    assert np.all(np.abs(v[np.any(J - I + Lq - K != 0, axis=1)]) > 0)
