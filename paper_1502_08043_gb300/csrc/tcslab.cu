@@ -1,5 +1,5 @@
-// Fused tensor-core exchange sums, bf16 hi + lo, any grid side up to 127 (operands padded
-// to 128).
+// Fused tensor-core exchange sums, bf16 or fp16 hi + lo, any grid side up to 127 (operands
+// padded to 128).
 //
 // Sec. III exchange of the uniform electron gas with the node sum of Sec. II Eq. 14; the
 // periodic kernel uses the D_s = T_s - I split, so with the Fermi-sphere occupation O
@@ -16,13 +16,6 @@
 //   epi   U_j <- w_s U_j + w_s A_{s,x_j}, split into bf16 hi + lo, written back into the
 //         same tensor-memory columns (each 16-column piece becomes 8 hi + 8 lo columns)
 //   MMA2  E_j += U_j T_s                      (A = U_j from tensor memory, B = T_s)
-// Periodic boxes whose band is at most 96 columns wide form the A term on the tensor cores
-// instead of in the epilogue: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h],
-// exact in 16 bits, built with R; MMA1 adds F_s P_x (F_s hi and lo from the tensor-memory
-// columns the band leaves free, staged once per node by the epilogue warps) to U_j, and
-// the epilogue only scales and re-splits (fp16: F' = 2^j F and ones of 2^a, so the sum is
-// 2^(a + j) (T R + A) like T' R').  Both terms are non-negative, so the sum has no
-// cancellation.
 // for the two slabs x_0 = 2p, x_1 = 2p + 1 of the pair, issued in the order
 //   MMA1(i, 0), MMA2(i-1, 1), MMA1(i, 1), MMA2(i, 0)
 // so that the epilogue of one slab always overlaps two GEMMs of the other, the single
@@ -32,15 +25,24 @@
 // the partials of each pair in a fixed order (deterministic), adds the Dbar term and
 // forms eps and E_x.  Each product is bf16x3: hi*hi + hi*lo + lo*hi, FP32 accumulate.
 //
+// Periodic boxes whose band is at most 96 columns wide form the A term on the tensor cores
+// instead of in the epilogue: A_{s,x} = F_s P_x with the one-hot P_x[z][h] = [h(x, z) = h],
+// exact in 16 bits, built with R; MMA1 adds F_s P_x (F_s hi and lo from the tensor-memory
+// columns the band leaves free, staged once per node by the epilogue warps) to U_j, and
+// the epilogue only scales and re-splits (fp16: F' = 2^j F and ones of 2^a, so the sum is
+// 2^(a + j) (T R + A) like T' R').  Both terms are non-negative, so the sum has no
+// cancellation.
+//
 // Tensor memory (512 columns): [0,128) U_0, [128,256) U_1, [256,384) E_0, [384,512) E_1;
 // with the A term on the tensor cores F_s hi in [96,128), lo in [224,256).
-// Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..), 8-10 and 12-14
-// build R, 11 TMA producer, 15 MMA issuer.  Warp w runs on scheduler w % 4, and the MMA issue
-// rate drops with every busy warp on the MMA warp's scheduler: that scheduler hosts besides
-// it the two quadrant-3 epilogue warps and the mostly idle producer, and the MMA warp issues
-// converged, one K step (three MMAs) per elected instruction block.  Every wait is bounded
-// (global timer); on expiry the error word is set, all roles stop, the MMA issuer drains its
-// MMAs and tensor memory is freed before the CTA returns.
+// Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) ..; warps w and w + 4 share the band's
+// 16-column pieces evenly), 8-10 and 12-14 build R, 11 TMA producer, 15 MMA issuer.
+// Warp w runs on scheduler w % 4, and the MMA issue rate drops with every busy warp on the
+// MMA warp's scheduler: that scheduler hosts besides it the two quadrant-3 epilogue warps
+// and the mostly idle producer, and the MMA warp issues converged, one K step (three MMAs)
+// per elected instruction block.  Every wait is bounded (global timer); on expiry the error
+// word is set, all roles stop, the MMA issuer drains its MMAs and tensor memory is freed
+// before the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
