@@ -27,12 +27,19 @@
 // the partials of each pair in a fixed order (deterministic), adds the Dbar term and
 // forms eps and E_x.  Each product is bf16x3: hi*hi + hi*lo + lo*hi, FP32 accumulate.
 //
-// Tensor memory (512 columns): [0,128) U_0, [128,256) U_1, [256,384) E_0, [384,512) E_1.
+// When every box of the batch is periodic with a band of at most 96 columns, the A term is
+// formed on the tensor cores as in tcslab.cu: A_{s,x} = F_s P_x with the one-hot
+// P_x[z][h] = [h(x, z) = h] built with R (cleared with R when the box changes), F_s hi and
+// lo staged per node into the tensor-memory columns the band leaves free, two more MMAs per
+// K step of h <= R_F added to U in MMA1; the epilogue then only scales and re-splits.
+//
+// Tensor memory (512 columns): [0,128) U_0, [128,256) U_1, [256,384) E_0, [384,512) E_1;
+// with the A term on the tensor cores F_s hi in [96,128), lo in [224,256).
 // Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..), 8-10 and 12-14
 // build R, 11 TMA producer, 15 MMA issuer (converged, one K step per elected asm block; no
-// builder shares the MMA warp's scheduler).  Every wait is bounded (global timer); on expiry the
-// error word is set, all roles stop, the MMA issuer drains its MMAs and tensor memory is
-// freed before the CTA returns.
+// builder shares the MMA warp's scheduler).  Every wait is bounded (global timer); on
+// expiry the error word is set, all roles stop, the MMA issuer drains its MMAs and tensor
+// memory is freed before the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
