@@ -92,35 +92,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// Warp-converged forms: all 32 lanes execute the call with the same operands and one lane,
-// chosen by elect.sync, issues the instruction.  Operands that are uniform over a converged
-// warp stay in uniform registers, so an MMA costs the issuing warp a few instructions only
-// (issued from a single-lane branch it costs many more, which other warps on the same
-// scheduler then delay).
-__device__ __forceinline__ void mma_f16_w(uint32_t tmem_d, uint64_t a, uint64_t b,
-                                          uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-// A operand in tensor memory
-__device__ __forceinline__ void mma_f16_ts_w(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
-                                             uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-// One K step of a split-precision product, warp-converged, from one asm block (one elected
-// lane, the descriptor offsets added in the block): D (+)= A B + A B' + A' B with
-// A' = A + da, B' = B + db (descriptor offsets of the lo planes).  Three MMAs per asm block
-// cost the issuing warp markedly fewer instructions than three single calls, which matters
-// while other warps on its scheduler are busy.
+// Warp-converged MMA issue: all 32 lanes execute the call with the same operands and one
+// lane, chosen by elect.sync, issues the instructions.  Operands that are uniform over a
+// converged warp stay in uniform registers, so an MMA costs the issuing warp a few
+// instructions only (issued from a single-lane branch it costs many more, which other
+// warps on the same scheduler then delay), and several MMAs in one asm block cost fewer
+// again.
+//
+// One K step of a split-precision product from one asm block (the descriptor offsets added
+// in the block): D (+)= A B + A B' + A' B with A' = A + da, B' = B + db (descriptor offsets
+// of the lo planes).
 __device__ __forceinline__ void mma_x3_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint64_t da,
                                          uint64_t db, uint32_t idesc, uint32_t accum) {
   asm volatile(
@@ -202,17 +183,6 @@ template <>
 __device__ __forceinline__ void split2<__half>(float v, __half& hi, __half& lo) {
   hi = __float2half_rn(v);
   lo = __float2half_rn(v - __half2float(hi));
-}
-
-// tcgen05.mma with the A operand in tensor memory (M = 128 lanes, K = 16 elements packed
-// two per 32-bit column, lower K index in the lower half) and B in shared memory
-__device__ __forceinline__ void mma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
-                                           uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
