@@ -35,6 +35,7 @@ ATTEMPTS = 64
 # quadruple streams
 STREAM_CLEAN = 1        # only momentum-conserving quadruples
 STREAM_PLANTED = 2      # 5 % random L (non-conserving), 1 % I = J, L = K
+STREAM_UNIFORM = 3      # four independent uniform ids (almost all non-conserving)
 
 
 def _u64(x):
@@ -157,6 +158,20 @@ def quads(R: int, start: int, count: int, seed: int = SEED, stream: int = STREAM
     return out
 
 
+def quads_uniform(R: int, start: int, count: int, seed: int = SEED,
+                  stream: int = STREAM_UNIFORM) -> np.ndarray:
+    """Quadruples number start .. start+count-1 with four independent uniform ids, as
+    int32[count, 4]: component c of quadruple i uses counter 4 i + c.  The inputs of
+    general (not necessarily momentum-conserving) integrals."""
+    Nb = len(sphere_vectors(R))
+    key = stream_key(seed, stream)
+    i = np.arange(start, start + count, dtype=np.uint64)
+    out = np.empty((count, 4), dtype=np.int32)
+    for c in range(4):
+        out[:, c] = lemire(draw(key, i * np.uint64(4) + np.uint64(c)), Nb)
+    return out
+
+
 def quads_as_vectors(q: np.ndarray, vec: np.ndarray) -> np.ndarray:
     """The int8x4 form of id quadruples: int8[count, 4 functions, 4] = (n_x, n_y, n_z, 0)."""
     out = np.zeros((q.shape[0], 4, 4), dtype=np.int8)
@@ -211,7 +226,8 @@ def _gen_lib():
 def quads_device(R: int, start: int, count: int, out, seed: int = SEED,
                  stream: int = STREAM_CLEAN, cuda_stream=None):
     """Fill the int32[count, 4] CUDA tensor `out` with quadruples start .. start+count-1,
-    bit-identical to quads(R, start, count, seed, stream)."""
+    bit-identical to quads(R, start, count, seed, stream) (quads_uniform for
+    STREAM_UNIFORM)."""
     import torch
     dev = out.device
     key_t = (R, dev.index)
@@ -225,7 +241,8 @@ def quads_device(R: int, start: int, count: int, out, seed: int = SEED,
     assert out.dtype == torch.int32 and out.is_contiguous() and out.shape[0] >= count
     s = torch.cuda.current_stream(dev).cuda_stream if cuda_stream is None else cuda_stream
     rc = _gen_lib().ccgen_quads(R, Nb, v4.data_ptr(), idm.data_ptr(), stream_key(seed, stream),
-                                start, count, 1 if stream == STREAM_PLANTED else 0,
+                                start, count,
+                                {STREAM_PLANTED: 1, STREAM_UNIFORM: 2}.get(stream, 0),
                                 out.data_ptr(), s)
     if rc != 0:
         raise RuntimeError(f"ccgen_quads failed ({rc})")

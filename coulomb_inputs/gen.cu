@@ -2,6 +2,7 @@
 // Input generation only (no arithmetic of the Coulomb method).  Bit-identical to the
 // numpy version: quadruple i, attempt a, component c uses counter (i * 64 + a) * 4 + c;
 // I, J, K uniform ids by multiply-high; L = id of n_I + n_K - n_J if inside the sphere.
+// Mode 2 (coulomb_inputs.quads_uniform): four independent uniform ids, counter 4 i + c.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,6 +28,11 @@ __global__ void k_quads(int R, int Nb, const char4* __restrict__ vec, const int*
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
        t += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t i = (uint64_t)(start + t);
+    if (planted == 2) {
+      out[t] = make_int4(lemire(draw(key, 4 * i), Nb), lemire(draw(key, 4 * i + 1), Nb),
+                         lemire(draw(key, 4 * i + 2), Nb), lemire(draw(key, 4 * i + 3), Nb));
+      continue;
+    }
     int4 q = make_int4(0, 0, 0, 0);
     bool done = false;
     int I0 = 0, K0 = 0;

@@ -63,7 +63,9 @@ typedef enum {
 
 typedef enum {
   CC_LOOKUP_SEPARABLE = 0, /* Eq. 14 node sum: sum_s w_s T_s[q_x] T_s[q_y] T_s[q_z] */
-  CC_LOOKUP_COLLAPSED = 1  /* periodic only: one table over m = |q|^2 (node sum folded) */
+  CC_LOOKUP_COLLAPSED = 1, /* periodic only: one table over m = |q|^2 (node sum folded) */
+  CC_LOOKUP_GENERAL = 2    /* box only: any quadruple, conserving or not, from the
+                              two-index per-axis tables A(alpha_s, D1, D2) of Eq. 8 */
 } cc_lookup;
 
 typedef enum {
@@ -117,6 +119,10 @@ typedef struct {
   int m_max;          /* collapsed table covers m = 0..m_max = 4 R^2 */
   size_t device_bytes; /* device memory held by the handle (tables + workspace) */
   size_t table_bytes;  /* of which the FP32 lookup tables (the stored compression) */
+  int general_codes;   /* BOX: entries per node of the two-index tables, (2R + 1)^2; 0 for
+                          PERIODIC (Sec. III counts 4 N^{2/3} per node for N planewaves) */
+  size_t general_table_bytes; /* BOX: FP32 two-index lookup tables, general_codes x S_eff
+                                 entries padded to S_eff rounded up to 32; 0 for PERIODIC */
 } cc_tables_info_t;
 
 /* Build the node set, weights and tables on the device of the current context
@@ -137,6 +143,18 @@ cc_status cc_tables_nodes(cc_tables t, double* alpha_host, double* w_host, int* 
 /* Copy the FP64 per-node tables of the kept nodes to the host:
  * table_host[S_eff][2R + 1] = T_s[Delta] (PERIODIC exp(-a_s Delta^2), BOX A(alpha_s, Delta)). */
 cc_status cc_tables_values(cc_tables t, double* table_host);
+
+/* BOX tables only: copy the FP64 two-index per-axis tables of the kept nodes to the host,
+ * table_host[S_eff][(2R + 1)^2] = A(alpha_s, d1, d2) (Sec. II Eq. 8 with box-normalised
+ * planewaves on [0, L]: A = 1/L^2 int_0^L int_0^L g(x - x') exp(2 pi i (D1 x + D2 x') / L)
+ * dx dx', g(u) = sqrt(pi / alpha) exp(-u^2 / (4 alpha)), for the pair differences
+ * D1 = J_x - I_x at r and D2 = L_x - K_x at r').  A is real, symmetric in (D1, D2) and even
+ * under (D1, D2) -> (-D1, -D2), so only the canonical pairs d1 >= |d2| are stored, at code
+ * c = d1^2 + d1 + d2 (0 <= d1 <= 2R); any (D1, D2) maps to (d1, d2) by swapping so that
+ * |D1| >= |D2| and then negating both if the first is negative.  D1 + D2 = 0 entries equal
+ * the conserving table of cc_tables_values.  Built with the same 1200-point Gauss-Legendre
+ * rule per axis integral as the conserving table.  CC_ERR_NOTSUPP for PERIODIC tables. */
+cc_status cc_tables_general_values(cc_tables t, double* table_host);
 
 /* Checkpoint: write / read the node set and the FP64 tables (the "stored forever"
  * table of Sec. II) to a flat versioned file with a checksum.  Load rebuilds the
@@ -171,15 +189,24 @@ cc_status cc_basis(int R, int* Nb, int8_t* vec_host);
  *   quads_dev     n quadruples in `format` (16 bytes each and 16-byte aligned; 8 bytes and
  *                 8-byte aligned for CC_QUAD_IDS_U16, which needs Nb <= 65536, else
  *                 CC_ERR_RANGE).
- *   lookup        CC_LOOKUP_SEPARABLE (any kernel) or CC_LOOKUP_COLLAPSED (PERIODIC).
+ *   lookup        CC_LOOKUP_SEPARABLE (any kernel), CC_LOOKUP_COLLAPSED (PERIODIC) or
+ *                 CC_LOOKUP_GENERAL (BOX): see below.
  *   precision     CC_PREC_FP32 (out float[n]) or CC_PREC_FP64 (out double[n]).
  *   counters_dev  NULL or unsigned long long[3], ADDED to (not cleared):
  *                 [0] non-conserving quadruples, [1] periodic q = 0 (excluded) terms,
  *                 [2] ids outside [0, Nb) or vectors outside the cutoff sphere.
  *                 Each of these quadruples gets the value 0.
- *   BOX kernel: only momentum-conserving quadruples are represented by the per-axis
- *   tables; non-conserving ones get 0 and are counted in [0].
- * n may be 0.  Errors: CC_ERR_ARG, CC_ERR_NOTSUPP (collapsed BOX, mixed precision). */
+ *   BOX kernel, SEPARABLE: the one-index per-axis tables represent momentum-conserving
+ *   quadruples only; non-conserving ones get 0 and are counted in [0].
+ *   BOX kernel, GENERAL: every in-range quadruple gets its value, conserving or not,
+ *   (IJ|KL) = 1/(2 pi^2) sum_s w_s prod_{x,y,z} A(alpha_s, D1, D2) with D1 = n_J - n_I and
+ *   D2 = n_L - n_K per axis (Sec. II Eqs. 8 and 14; the two-index tables of
+ *   cc_tables_general_values, FP32 or FP64 by precision); [0] still counts the
+ *   non-conserving ones (informational, their values are not zeroed), [1] stays 0.
+ *   The box integrand changes sign, so a node sum can cancel: an FP32 result is accurate
+ *   to about 1e-7 of sum_s |w_s prod A| (the sum of the absolute terms), not of itself.
+ * n may be 0.  Errors: CC_ERR_ARG, CC_ERR_NOTSUPP (collapsed BOX, general PERIODIC,
+ * mixed precision). */
 cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n, int format,
                                    int lookup, int precision, void* out_dev,
                                    unsigned long long* counters_dev, void* stream);

@@ -134,25 +134,34 @@ def A_box_general(alpha, D1, D2, L: float, points: int = BOX_GL_POINTS):
     return out.reshape((alpha.size,) + shape)
 
 
-def V_box_general(nI, nJ, nK, nL, alpha, omega, L: float):
+def V_box_general(nI, nJ, nK, nL, alpha, omega, L: float, points: int = BOX_GL_POINTS,
+                  absolute: bool = False):
     """(IJ|KL) of the box kernel for any quadruple of planewave index vectors ([..., 3]),
     momentum-conserving or not: 1/(2 pi^2) sum_s omega_s prod_x A(alpha_s, D1_x, D2_x)
-    with D1 = n_J - n_I, D2 = n_L - n_K (the Eq. 14 node sum of Eq. 8)."""
+    with D1 = n_J - n_I, D2 = n_L - n_K (the Eq. 14 node sum of Eq. 8); `points`
+    Gauss-Legendre points per axis integral.  A is evaluated once per distinct (D1, D2)
+    pair of the batch.  absolute=True returns 1/(2 pi^2) sum_s |omega_s prod_x A| instead,
+    the scale against which the rounding of the (sign-changing) node sum is measured."""
     D1 = np.asarray(nJ, dtype=np.int64) - np.asarray(nI, dtype=np.int64)
     D2 = np.asarray(nL, dtype=np.int64) - np.asarray(nK, dtype=np.int64)
     shape = D1.shape[:-1]
     D1 = D1.reshape(-1, 3)
     D2 = D2.reshape(-1, 3)
+    pairs = np.stack([D1.reshape(-1), D2.reshape(-1)], axis=1)   # [n * 3, 2], axis fastest
+    uniq, inv = np.unique(pairs, axis=0, return_inverse=True)
+    inv = inv.reshape(-1, 3)
+    A = A_box_general(alpha, uniq[:, 0], uniq[:, 1], L, points)  # [S, distinct pairs]
     acc = np.zeros(D1.shape[0])
     for s in range(len(alpha)):
-        A = [A_box_general(alpha[s], D1[:, x], D2[:, x], L)[0] for x in range(3)]
-        acc += omega[s] * A[0] * A[1] * A[2]
+        term = omega[s] * A[s, inv[:, 0]] * A[s, inv[:, 1]] * A[s, inv[:, 2]]
+        acc += np.abs(term) if absolute else term
     return (acc / (2.0 * np.pi ** 2)).reshape(shape)
 
 
-def box_table(alpha, Dmax: int, L: float):
-    """A(alpha_s, D) for D = 0..Dmax: float64[S, Dmax + 1]."""
-    return A_box(alpha, np.arange(Dmax + 1), L)
+def box_table(alpha, Dmax: int, L: float, points: int = BOX_GL_POINTS):
+    """A(alpha_s, D) for D = 0..Dmax: float64[S, Dmax + 1] (`points` Gauss-Legendre points
+    per axis integral)."""
+    return A_box(alpha, np.arange(Dmax + 1), L, points)
 
 
 def V_box_separable(n, alpha, omega, L: float, table=None):

@@ -14,7 +14,8 @@ Sec. III also states E_x = beta(M, {q_k}) / L: E_x L does not depend on L.
 import numpy as np
 
 from .basis import basis, occupied
-from .coulomb import V_exact, V_separable, V_box_separable, box_table, V_of_m_separable
+from .coulomb import (BOX_GL_POINTS, V_exact, V_separable, V_box_separable, box_table,
+                      V_of_m_separable)
 
 
 def E_KS(M: int, L: float) -> float:
@@ -56,10 +57,39 @@ def eps_separable(R: int, R_F: int, L: float, a, w, k_idx=None, chunk: int = 256
     return _pairs(R, R_F, k_idx, chunk, val)
 
 
-def eps_box(R: int, R_F: int, L: float, alpha, omega, k_idx=None, chunk: int = 64):
-    """eps(k) = -sum_{j in F} V_box(k - n_j), node-sum form of the box kernel."""
-    table = box_table(alpha, R + R_F, L)
+def eps_box(R: int, R_F: int, L: float, alpha, omega, k_idx=None, chunk: int = 64,
+            points: int = BOX_GL_POINTS):
+    """eps(k) = -sum_{j in F} V_box(k - n_j), node-sum form of the box kernel (`points`
+    Gauss-Legendre points per axis integral of the table)."""
+    table = box_table(alpha, R + R_F, L, points)
     return _pairs(R, R_F, k_idx, chunk, lambda d: V_box_separable(d, alpha, omega, L, table))
+
+
+def eps_separable_grid(R: int, R_F: int, L: float, a, w) -> np.ndarray:
+    """eps_separable on the whole (2R+1)^3 grid, as a 3D linear convolution: eps = -(O * V)
+    with O the 0/1 Fermi-sphere occupation on [-R_F, R_F]^3 and V(n) the node sum of
+    V_of_m_separable at m = |n|^2 on [-(R + R_F), R + R_F]^3 (V(0) = 0, the excluded j = k
+    term).  The convolution is taken with an FP64 FFT (a library routine serving as one step)
+    and the cube [-R, R]^3 of the full result is returned, 0 outside the basis sphere.
+    Same values as eps_separable up to the FFT's rounding (about 1e-14 relative: every term
+    is positive)."""
+    G = 2 * R_F + 1
+    rv = np.arange(-(R + R_F), R + R_F + 1)
+    m = rv[:, None, None] ** 2 + rv[None, :, None] ** 2 + rv[None, None, :] ** 2
+    V = V_of_m_separable(np.arange(int(m.max()) + 1), L, a, w)[m]
+    r = np.arange(-R_F, R_F + 1)
+    occ = ((r[:, None, None] ** 2 + r[None, :, None] ** 2 + r[None, None, :] ** 2)
+           <= R_F * R_F).astype(np.float64)
+    n = V.shape[0] + G - 1
+    ax = (0, 1, 2)
+    full = np.fft.irfftn(np.fft.rfftn(V, s=(n, n, n), axes=ax) *
+                         np.fft.rfftn(occ, s=(n, n, n), axes=ax), s=(n, n, n), axes=ax)
+    # full[i] = sum_j occ[j] V[i - j]; output index i <-> k = i - (R + R_F) - R_F
+    lo = R_F + R_F
+    sub = -full[lo:lo + 2 * R + 1, lo:lo + 2 * R + 1, lo:lo + 2 * R + 1]
+    k = np.arange(-R, R + 1)
+    inside = (k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2) <= R * R
+    return np.where(inside, sub, 0.0)
 
 
 def eps_on_grid(R: int, values) -> np.ndarray:

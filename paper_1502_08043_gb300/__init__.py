@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libcoulomb.so")
 
 KERNELS = {"periodic": 0, "box": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp16x3": 3}
-LOOKUPS = {"separable": 0, "collapsed": 1}
+LOOKUPS = {"separable": 0, "collapsed": 1, "general": 2}
 FORMATS = {"ids": 0, "vec": 1, "ids16": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "size beyond limit", 3: "CUDA error",
           4: "allocation failed", 5: "device wait timed out", 6: "not supported",
@@ -51,7 +51,8 @@ class TablesInfo(ctypes.Structure):
                 ("alpha_c", ctypes.c_double), ("prune_tol", ctypes.c_double),
                 ("S_eff", ctypes.c_int), ("Nb", ctypes.c_int), ("Mg", ctypes.c_int),
                 ("m_max", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
-                ("table_bytes", ctypes.c_size_t)]
+                ("table_bytes", ctypes.c_size_t), ("general_codes", ctypes.c_int),
+                ("general_table_bytes", ctypes.c_size_t)]
 
 
 class Box(ctypes.Structure):
@@ -67,6 +68,7 @@ SIGNATURES = {
     "cc_tables_info": (_I, [_P, ctypes.POINTER(TablesInfo)]),
     "cc_tables_nodes": (_I, [_P, _P, _P, _P, _P]),
     "cc_tables_values": (_I, [_P, _P]),
+    "cc_tables_general_values": (_I, [_P, _P]),
     "cc_tables_save": (_I, [_P, ctypes.c_char_p]),
     "cc_tables_load": (_I, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "cc_tables_free": (_I, [_P]),
@@ -179,6 +181,14 @@ class Tables:
         T = np.zeros((self.info["S_eff"], 2 * self.info["R"] + 1))
         _check("cc_tables_values", lib().cc_tables_values(self.handle, T.ctypes.data))
         return T
+
+    def general_values(self):
+        """Box tables: the FP64 two-index tables A(alpha_s, d1, d2) of the kept nodes,
+        float64[S_eff, (2R + 1)^2] by canonical code d1^2 + d1 + d2 (d1 >= |d2|)."""
+        G = np.zeros((self.info["S_eff"], self.info["general_codes"]))
+        _check("cc_tables_general_values",
+               lib().cc_tables_general_values(self.handle, G.ctypes.data))
+        return G
 
     def save(self, path):
         _check("cc_tables_save", lib().cc_tables_save(self.handle, str(path).encode()))

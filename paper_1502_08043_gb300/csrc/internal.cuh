@@ -53,6 +53,12 @@ struct DevTables {
   float* Tm32 = nullptr;
   float* WDm32 = nullptr;
   float* Dbar32 = nullptr;
+  // BOX kernel, general (not necessarily momentum-conserving) integrals: the two-index
+  // per-axis tables A(alpha_s, D1, D2) of Sec. II Eq. 8 over the canonical codes
+  // c = d1^2 + d1 + d2 (d1 >= |d2|, see gen_code), Gc = (2R + 1)^2 codes per node
+  double* G64 = nullptr;      // [S_eff][Gc]      A(alpha_s, d1, d2)
+  double* sepG64 = nullptr;   // [Gc][S_pad]      cbrt(pref w_s) A(alpha_s, d1, d2), 0 padded
+  float* sepG32 = nullptr;    // same, FP32
 };
 
 // Exchange workspace (allocated with the handle; a chunk of nodes at a time).
@@ -86,6 +92,8 @@ struct cc_tables_s {
   void* fused = nullptr;          // fused small-grid exchange plan (grid side <= 49)
   size_t table_bytes = 0;
   size_t device_bytes = 0;
+  int Gc = 0;                     // codes of the general box tables per node (0: periodic)
+  size_t general_table_bytes = 0; // FP32 general box lookup tables
 };
 
 namespace cc {

@@ -65,6 +65,18 @@ struct IdsSrc {
     return classify<kPeriodic>(ld_word(basis, v.x), ld_word(basis, v.y), ld_word(basis, v.z),
                                ld_word(basis, v.w), qa);
   }
+  // the four index vectors of quadruple i; false if an id is out of range
+  __device__ __forceinline__ bool fetch(int64_t i, uint32_t w[4]) const {
+    const int4 v = raw(i);
+    if ((unsigned)v.x >= (unsigned)Nb || (unsigned)v.y >= (unsigned)Nb ||
+        (unsigned)v.z >= (unsigned)Nb || (unsigned)v.w >= (unsigned)Nb)
+      return false;
+    w[0] = ld_word(basis, v.x);
+    w[1] = ld_word(basis, v.y);
+    w[2] = ld_word(basis, v.z);
+    w[3] = ld_word(basis, v.w);
+    return true;
+  }
 };
 
 // uint16 ids: 8 bytes per quadruple (basis of at most 65536 functions)
@@ -90,6 +102,15 @@ struct Ids16Src {
     return classify<kPeriodic>(ld_word(basis, v.x), ld_word(basis, v.y), ld_word(basis, v.z),
                                ld_word(basis, v.w), qa);
   }
+  __device__ __forceinline__ bool fetch(int64_t i, uint32_t w[4]) const {
+    const int4 v = raw(i);
+    if (v.x >= Nb || v.y >= Nb || v.z >= Nb || v.w >= Nb) return false;
+    w[0] = ld_word(basis, v.x);
+    w[1] = ld_word(basis, v.y);
+    w[2] = ld_word(basis, v.z);
+    w[3] = ld_word(basis, v.w);
+    return true;
+  }
 };
 
 struct VecSrc {
@@ -113,6 +134,14 @@ struct VecSrc {
       return kRange;
     }
     return classify<kPeriodic>(a, b, c, d, qa);
+  }
+  __device__ __forceinline__ bool fetch(int64_t i, uint32_t w[4]) const {
+    const int4 v = raw(i);
+    w[0] = (uint32_t)v.x;
+    w[1] = (uint32_t)v.y;
+    w[2] = (uint32_t)v.z;
+    w[3] = (uint32_t)v.w;
+    return in_sphere(w[0]) && in_sphere(w[1]) && in_sphere(w[2]) && in_sphere(w[3]);
   }
 };
 
@@ -147,23 +176,25 @@ __device__ __forceinline__ void flush_counts(unsigned long long* counters, unsig
 }
 
 // ---------------------------------------------------------------- separable kernel
-// NCH consecutive nodes per lane (S_pad = 32 NCH); NCH = 0 selects a runtime loop
+// NCH consecutive nodes per lane (S_pad = 32 NCH); NCH = 0 selects a runtime loop.  The
+// products are always accumulated in ascending node order, a = fma(x_c y_c, z_c, a).
 template <typename T, int NCH>
 __device__ __forceinline__ T node_chunk(const T* rx, const T* ry, const T* rz, int nch) {
   T a = T(0);
-  if constexpr (sizeof(T) == 4 && (NCH == 2 || NCH == 4)) {
-    // the lane's chunk starts at a multiple of NCH words: one vector load per axis
-    using V = typename std::conditional<NCH == 2, float2, float4>::type;
-    const V x = *reinterpret_cast<const V*>(rx);
-    const V y = *reinterpret_cast<const V*>(ry);
-    const V z = *reinterpret_cast<const V*>(rz);
-    a = fma_t(x.x * y.x, z.x, a);
-    a = fma_t(x.y * y.y, z.y, a);
-    if constexpr (NCH == 4) {
-      a = fma_t(reinterpret_cast<const float4&>(x).z * reinterpret_cast<const float4&>(y).z,
-                reinterpret_cast<const float4&>(z).z, a);
-      a = fma_t(reinterpret_cast<const float4&>(x).w * reinterpret_cast<const float4&>(y).w,
-                reinterpret_cast<const float4&>(z).w, a);
+  if constexpr (sizeof(T) == 4 && NCH > 0 && (NCH % 4 == 0 || NCH % 2 == 0)) {
+    // the lane's chunk starts at a multiple of NCH words: vector loads per axis
+    constexpr int W = NCH % 4 == 0 ? 4 : 2;
+    using V = typename std::conditional<W == 4, float4, float2>::type;
+#pragma unroll
+    for (int c = 0; c < NCH; c += W) {
+      const V x = *reinterpret_cast<const V*>(rx + c);
+      const V y = *reinterpret_cast<const V*>(ry + c);
+      const V z = *reinterpret_cast<const V*>(rz + c);
+      const float* xf = reinterpret_cast<const float*>(&x);
+      const float* yf = reinterpret_cast<const float*>(&y);
+      const float* zf = reinterpret_cast<const float*>(&z);
+#pragma unroll
+      for (int e = 0; e < W; ++e) a = fma_t(xf[e] * yf[e], zf[e], a);
     }
   } else if constexpr (NCH > 0) {
 #pragma unroll
@@ -226,6 +257,99 @@ __global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __rest
     if (i < n) out[i] = flag ? T(0) : acc[0];
   }
   if (lane == 0) flush_counts(counters, c0, c1, c2);
+}
+
+// ---------------------------------------------------------------- general box kernel
+// Any quadruple, conserving or not (Sec. II Eq. 8 with the node sum of Eq. 14):
+//   (IJ|KL) = sum_s prod_{x,y,z} c_s A(alpha_s, D1, D2),  D1 = n_J - n_I, D2 = n_L - n_K,
+// c_s^3 = pref w_s folded into the table.  A is unchanged by swapping D1, D2 and by negating
+// both, so the table has one row per canonical pair d1 >= |d2|, code d1^2 + d1 + d2.
+__device__ __forceinline__ int gen_code(int d1, int d2) {
+  int a = d1, b = d2;
+  if (abs(b) > abs(a)) {
+    a = d2;
+    b = d1;
+  }
+  if (a < 0) {
+    a = -a;
+    b = -b;
+  }
+  return a * a + a + b;
+}
+
+__device__ __forceinline__ int sbyte(uint32_t w, int k) { return (int)(int8_t)(w >> (8 * k)); }
+
+// The same warp organisation as k_sep (lane l owns nodes l S_pad/32 ..; butterfly
+// transpose-reduce).  The table [codes][S_pad] is staged in shared memory when it fits
+// (tab_smem), otherwise read through the L1 cache from global memory.
+template <typename T, typename Src, int NCH>
+__global__ void __launch_bounds__(256) k_gen(Src src, int64_t n, const T* __restrict__ gtab,
+                                             int codes, int S_pad, T* __restrict__ out,
+                                             unsigned long long* counters, int tab_smem,
+                                             int basis_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const T* tab = gtab;
+  size_t off = 0;
+  if (tab_smem) {
+    T* st = reinterpret_cast<T*>(smem);
+    const int tab_elems = codes * S_pad;
+    for (int i = threadIdx.x; i < tab_elems; i += blockDim.x) st[i] = gtab[i];
+    tab = st;
+    off = ((size_t)tab_elems * sizeof(T) + 15) & ~(size_t)15;
+  }
+  if (basis_smem > 0) {
+    char4* sb = reinterpret_cast<char4*>(smem + off);
+    for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
+    src.basis = sb;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nch = S_pad >> 5;
+  unsigned c0 = 0, c2 = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * 32; base < n;
+       base += (int64_t)gridDim.x * nw * 32) {
+    const int64_t i = base + lane;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    const bool live = i < n;
+    const bool ok = live && src.fetch(i, w);
+    uint32_t pxy = 0, pz = 0;  // codes (x | y << 16, z); 0 (a valid row) for dead lanes
+    bool noncons = false;
+    if (ok) {
+      int cx[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int d1 = sbyte(w[1], k) - sbyte(w[0], k), d2 = sbyte(w[3], k) - sbyte(w[2], k);
+        noncons |= d1 + d2 != 0;
+        cx[k] = gen_code(d1, d2);
+      }
+      pxy = (uint32_t)cx[0] | ((uint32_t)cx[1] << 16);
+      pz = (uint32_t)cx[2];
+    }
+    c0 += __popc(__ballot_sync(kFull, ok && noncons));
+    c2 += __popc(__ballot_sync(kFull, live && !ok));
+    T acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t p = __shfl_sync(kFull, pxy, k), q = __shfl_sync(kFull, pz, k);
+      const int lo = lane * nch;
+      const T* rx = tab + (size_t)(p & 0xffffu) * S_pad + lo;
+      const T* ry = tab + (size_t)(p >> 16) * S_pad + lo;
+      const T* rz = tab + (size_t)q * S_pad + lo;
+      acc[k] = node_chunk<T, NCH>(rx, ry, rz, nch);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < o; ++j) {
+        const T send = up ? acc[j] : acc[j + o];
+        const T keep = up ? acc[j + o] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(kFull, send, o);
+      }
+    }
+    if (live) out[i] = ok ? acc[0] : T(0);
+  }
+  if (lane == 0) flush_counts(counters, c0, 0, c2);
 }
 
 // ---------------------------------------------------------------- collapsed kernel
@@ -369,6 +493,33 @@ static cc_status launch_sep(cc_tables t, Src src, int64_t n, T* out,
 }
 
 template <typename T, typename Src>
+static cc_status launch_gen(cc_tables t, Src src, int64_t n, T* out,
+                            unsigned long long* counters, cudaStream_t st) {
+  const T* tab;
+  if constexpr (sizeof(T) == 4) tab = reinterpret_cast<const T*>(t->d.sepG32);
+  else tab = reinterpret_cast<const T*>(t->d.sepG64);
+  if (!tab) return CC_ERR_NOTSUPP;
+  const size_t tb = (((size_t)t->Gc * t->S_pad * sizeof(T)) + 15) & ~(size_t)15;
+  const int tab_smem = tb <= kSmemCap ? 1 : 0;
+  const size_t tsm = tab_smem ? tb : 0;
+  int basis_smem = 0;
+  if (src.basis && tsm + (size_t)t->Nb * 4 <= (tab_smem ? kSmemCap : 96 * 1024)) basis_smem = t->Nb;
+  const size_t smem = tsm + (size_t)basis_smem * 4;
+  const int nch = t->S_pad / 32;
+  auto kern = nch == 1 ? k_gen<T, Src, 1>
+            : nch == 2 ? k_gen<T, Src, 2>
+            : nch == 4 ? k_gen<T, Src, 4>
+            : nch == 6 ? k_gen<T, Src, 6>
+                       : k_gen<T, Src, 0>;
+  int blocks = 0;
+  CC_TRY(grid_for(kern, 256, smem, (n + 7) / 8, &blocks));
+  kern<<<blocks, 256, smem, st>>>(src, n, tab, t->Gc, t->S_pad, out, counters, tab_smem,
+                                  basis_smem);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+template <typename T, typename Src>
 static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned long long* counters,
                             cudaStream_t st, bool uses_basis) {
   const T* Vm;
@@ -394,6 +545,13 @@ static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int fo
   const char4* basis = reinterpret_cast<const char4*>(t->d.basis);
   const int4* q = reinterpret_cast<const int4*>(quads);
   const uint2* q16 = reinterpret_cast<const uint2*>(quads);
+  if (lookup == CC_LOOKUP_GENERAL) {
+    if (format == CC_QUAD_IDS_U16)
+      return launch_gen<T>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
+    if (format == CC_QUAD_IDS_I32)
+      return launch_gen<T>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
+    return launch_gen<T>(t, VecSrc{q, nullptr, t->p.R * t->p.R}, n, out, counters, st);
+  }
   if (format == CC_QUAD_IDS_U16) {
     if (lookup == CC_LOOKUP_COLLAPSED)
       return launch_col<T>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st, true);
@@ -457,9 +615,12 @@ extern "C" cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev
   if (format != CC_QUAD_IDS_I32 && format != CC_QUAD_VEC_I8X4 && format != CC_QUAD_IDS_U16)
     return CC_ERR_ARG;
   if (format == CC_QUAD_IDS_U16 && t->Nb > 65536) return CC_ERR_RANGE;
-  if (lookup != CC_LOOKUP_SEPARABLE && lookup != CC_LOOKUP_COLLAPSED) return CC_ERR_ARG;
+  if (lookup != CC_LOOKUP_SEPARABLE && lookup != CC_LOOKUP_COLLAPSED &&
+      lookup != CC_LOOKUP_GENERAL)
+    return CC_ERR_ARG;
   if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
   if (lookup == CC_LOOKUP_COLLAPSED && t->p.kernel != CC_KERNEL_PERIODIC) return CC_ERR_NOTSUPP;
+  if (lookup == CC_LOOKUP_GENERAL && t->p.kernel != CC_KERNEL_BOX) return CC_ERR_NOTSUPP;
   if (n == 0) return CC_OK;
   if (!quads_dev || !out_dev) return CC_ERR_ARG;
   if (((uintptr_t)quads_dev & (format == CC_QUAD_IDS_U16 ? 7 : 15)) != 0) return CC_ERR_ARG;

@@ -128,6 +128,62 @@ __global__ void k_box_table(const double* a, int Dmax, double L, const double* g
   if (threadIdx.x == 0) T[s * (Dmax + 1) + D] = 2.0 / (L * L) * h * red[0];
 }
 
+// Sine integrals of the general box tables, Sn(alpha, D) = int_0^L sqrt(pi/alpha)
+// exp(-u^2 / (4 alpha)) sin(2 pi D u / L) du on [0, min(L, 14 sqrt(alpha))], D = 0..2R.
+// One block per (node, D); fixed-order tree reduction.
+__global__ void k_box_sin_table(const double* a, int Dmax, double L, const double* glx,
+                                const double* glw, int ngl, double* Sn) {
+  const int s = blockIdx.x / (Dmax + 1), D = blockIdx.x % (Dmax + 1);
+  const double al = a[s];
+  const double ub = fmin(L, 14.0 * sqrt(al));
+  const double h = 0.5 * ub;
+  const double g0 = sqrt(kPi / al);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ngl; i += blockDim.x) {
+    const double u = h * glx[i] + h;
+    acc += glw[i] * sin(2.0 * kPi * D * u / L) * g0 * exp(-u * u / (4.0 * al));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Sn[s * (Dmax + 1) + D] = h * red[0];
+}
+
+// General per-axis box tables (Sec. II Eq. 8 for a pair difference D1 = J_x - I_x at r and
+// D2 = L_x - K_x at r'):  A(alpha, D1, D2) = 1/L^2 int int g(x - x') e^{2 pi i (D1 x + D2 x')/L}.
+// With u = x - x' the x integral is elementary because D1 + D2 is an integer:
+//   D1 + D2 = 0:  the conserving table A(alpha, |D1|) (T64),
+//   otherwise:    -(Sn(D1) + Sn(D2)) / (pi (D1 + D2) L),   Sn odd in D.
+// A is unchanged by swapping D1, D2 and by negating both, so one entry per canonical code
+// c = d1^2 + d1 + d2 with d1 >= |d2| (d1 = floor(sqrt(c))).  One thread per (node, code).
+__global__ void k_general_tables(const double* T64, const double* Sn, const double* w, int S_eff,
+                                 int S_pad, int Dmax, int Gc, double L, double pref,
+                                 double* G64, double* sepG64, float* sepG32) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Gc * S_pad) return;
+  const int c = (int)(idx / S_pad), s = (int)(idx % S_pad);
+  double v = 0.0;
+  if (s < S_eff) {
+    int d1 = (int)sqrt((double)c);
+    while (d1 * d1 > c) --d1;
+    while ((d1 + 1) * (d1 + 1) <= c) ++d1;
+    const int d2 = c - d1 * d1 - d1;
+    const double* sn = Sn + (long long)s * (Dmax + 1);
+    auto sodd = [&](int d) { return d >= 0 ? sn[d] : -sn[-d]; };
+    const int sig = d1 + d2;
+    const double g = sig == 0 ? T64[(long long)s * (Dmax + 1) + d1]
+                              : -(sodd(d1) + sodd(d2)) / (kPi * (double)sig * L);
+    G64[(long long)s * Gc + c] = g;
+    v = cbrt(pref * w[s]) * g;
+  }
+  sepG64[idx] = v;
+  sepG32[idx] = (float)v;
+}
+
 // separable lookup tables [Delta][S_pad] with cbrt(pref w_s) folded into every axis
 __global__ void k_sep_tables(const double* T, const double* w, int S_eff, int S_pad, int Dmax,
                              double pref, double* sep64, float* sep32) {
@@ -335,10 +391,48 @@ static cc_status dmalloc(cc_tables t, T** ptr, size_t count) {
 static void free_tables(cc_tables t) {
   DevTables& d = t->d;
   void* ptrs[] = {d.T64, d.w64, d.a64, d.sep64, d.sep32, d.Vm64, d.Vm32, d.basis,
-                  d.Tm64, d.WDm64, d.Dbar64, d.Tm32, d.WDm32, d.Dbar32};
+                  d.Tm64, d.WDm64, d.Dbar64, d.Tm32, d.WDm32, d.Dbar32,
+                  d.G64, d.sepG64, d.sepG32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   d = DevTables();
+}
+
+// General box tables (any quadruple, Sec. II Eq. 8): the sine integrals of every kept node
+// with the library's Gauss-Legendre rule, then one entry per (canonical code, node).
+static cc_status build_general(cc_tables t, cudaStream_t st) {
+  const int S_eff = t->S_eff, Dmax = t->Dmax;
+  DevTables& d = t->d;
+  t->Gc = (2 * t->p.R + 1) * (2 * t->p.R + 1);
+  CC_TRY(dmalloc(t, &d.G64, (size_t)S_eff * t->Gc));
+  CC_TRY(dmalloc(t, &d.sepG64, (size_t)t->Gc * t->S_pad));
+  CC_TRY(dmalloc(t, &d.sepG32, (size_t)t->Gc * t->S_pad));
+  double *gx = nullptr, *gw = nullptr, *sn = nullptr;
+  if (cudaMalloc((void**)&gx, sizeof(double) * kBoxGLPoints) != cudaSuccess ||
+      cudaMalloc((void**)&gw, sizeof(double) * kBoxGLPoints) != cudaSuccess ||
+      cudaMalloc((void**)&sn, sizeof(double) * S_eff * (Dmax + 1)) != cudaSuccess) {
+    cudaFree(gx);
+    cudaFree(gw);
+    return CC_ERR_ALLOC;
+  }
+  k_gl_rule<<<(kBoxGLPoints + 127) / 128, 128, 0, st>>>(kBoxGLPoints, gx, gw);
+  k_box_sin_table<<<S_eff * (Dmax + 1), 256, 0, st>>>(d.a64, Dmax, t->p.L, gx, gw, kBoxGLPoints,
+                                                      sn);
+  const long long n = (long long)t->Gc * t->S_pad;
+  k_general_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      d.T64, sn, d.w64, S_eff, t->S_pad, Dmax, t->Gc, t->p.L, t->pref, d.G64, d.sepG64,
+      d.sepG32);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(gx);
+  cudaFree(gw);
+  cudaFree(sn);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error("general box tables", e);
+    return CC_ERR_CUDA;
+  }
+  t->general_table_bytes = sizeof(float) * (size_t)t->Gc * t->S_pad;
+  return CC_OK;
 }
 
 // Everything downstream of the FP64 tables T64 (shared by build and load).
@@ -375,6 +469,7 @@ static cc_status build_derived(cc_tables t, cudaStream_t st) {
   CC_TRY(dmalloc(t, &d.basis, b.size()));
   CC_CUDA(cudaMemcpyAsync(d.basis, b.data(), b.size(), cudaMemcpyHostToDevice, st));
   t->table_bytes = sizeof(float) * ((size_t)(Dmax + 1) * t->S_pad + t->m_max + 1);
+  if (!periodic) CC_TRY(build_general(t, st));
   return CC_OK;
 }
 
@@ -612,6 +707,8 @@ cc_status cc_tables_info(cc_tables t, cc_tables_info_t* info) {
   info->m_max = t->m_max;
   info->device_bytes = t->device_bytes;
   info->table_bytes = t->table_bytes;
+  info->general_codes = t->Gc;
+  info->general_table_bytes = t->general_table_bytes;
   return CC_OK;
 }
 
@@ -630,6 +727,14 @@ cc_status cc_tables_nodes(cc_tables t, double* alpha_host, double* w_host, int* 
 cc_status cc_tables_values(cc_tables t, double* table_host) {
   if (!t || !table_host) return CC_ERR_ARG;
   CC_CUDA(cudaMemcpy(table_host, t->d.T64, sizeof(double) * t->S_eff * (t->Dmax + 1),
+                     cudaMemcpyDeviceToHost));
+  return CC_OK;
+}
+
+cc_status cc_tables_general_values(cc_tables t, double* table_host) {
+  if (!t || !table_host) return CC_ERR_ARG;
+  if (t->p.kernel != CC_KERNEL_BOX || !t->d.G64) return CC_ERR_NOTSUPP;
+  CC_CUDA(cudaMemcpy(table_host, t->d.G64, sizeof(double) * t->S_eff * t->Gc,
                      cudaMemcpyDeviceToHost));
   return CC_OK;
 }

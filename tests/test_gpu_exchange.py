@@ -4,7 +4,8 @@ import os
 import numpy as np
 import pytest
 
-from gpu_common import CFG1, CFG2, CFG3, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes, rel_err
+from gpu_common import (BOX_POINTS, CFG1, CFG2, CFG3, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes,
+                        rel_err)
 from oracle import basis as ob
 from oracle import exchange as ox
 from oracle import quadrature as oq
@@ -136,8 +137,8 @@ def test_box_exchange_vs_oracle(dev):
     R, R_F, L = 5, 3, 3.0
     ao, wo, _ = oq.paper_mesh2(6, 24)
     t = cc.build_tables("box", R=R, L=L, S=len(ao), n_sub=7, q_tail=24)
-    ref = ox.eps_box(R, R_F, L, ao, wo)
-    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-6)):
+    ref = ox.eps_box(R, R_F, L, ao, wo, points=BOX_POINTS)
+    for prec, tol in (("fp64", 1e-11), ("fp32", TOL_FP32)):
         grid, Ex = _exchange(t, R_F, prec, dev)
         assert rel_err(_basis_values(R, grid), ref) < tol
     t.free()

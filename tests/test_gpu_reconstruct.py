@@ -3,7 +3,8 @@ import numpy as np
 import pytest
 
 import coulomb_inputs as ci
-from gpu_common import CFG1, CFG2, CFG3, CFG5, TOL_FP32, TOL_FP64, need_gpu, oracle_nodes, rel_err
+from gpu_common import (BOX_POINTS, CFG1, CFG2, CFG3, CFG5, TOL_FP32, TOL_FP64, TOL_FP64_BOX,
+                        need_gpu, oracle_nodes, rel_err)
 from oracle import basis as ob
 from oracle import coulomb as oc
 from oracle import quadrature as oq
@@ -172,13 +173,10 @@ def test_box_kernel_separable(dev):
     ao, wo, _ = oq.paper_mesh2(5, 20)
     t = cc.build_tables("box", R=R, L=L, S=len(ao), n_sub=7, q_tail=20)
     q = ci.quads(R, 0, 20000, stream=ci.STREAM_PLANTED)
-    tab = oc.box_table(ao, 2 * R, L)
+    tab = oc.box_table(ao, 2 * R, L, BOX_POINTS)
     ref, cnt_ref = orc.reconstruct(q, R, L, "box", a=ao, w=wo, box_table=tab)
     assert cnt_ref[1] == 0 and cnt_ref[0] > 0
-    # box tables: the device's 1200-point axis integrals and the oracle's 2000-point ones
-    # agree to ~1e-13 absolute; A(alpha, Delta) changes sign, so the node sum cancels and
-    # relative differences of the (small) results grow to ~1e-10
-    for dtype, tol in ((torch.float64, 1e-9), (torch.float32, 2e-6)):
+    for dtype, tol in ((torch.float64, TOL_FP64_BOX), (torch.float32, TOL_FP32)):
         got, cnt = _run(t, q, "separable", dtype, dev)
         assert np.array_equal(cnt, cnt_ref)
         assert rel_err(got, ref) < tol

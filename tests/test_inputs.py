@@ -44,3 +44,16 @@ def test_box_params_ranges():
         assert 4 <= b["R"] <= 24 and 8 <= b["L"] < 30 and 16 <= b["S"] <= 96
         assert 1 <= b["R_F"] <= b["R"]
     assert ci.box_params(3) == boxes[:3]
+
+
+def test_uniform_quads():
+    R = 6
+    B = ci.sphere_vectors(R)
+    q = ci.quads_uniform(R, 0, 20000)
+    assert q.min() >= 0 and q.max() < len(B)
+    assert np.array_equal(ci.quads_uniform(R, 500, 100), q[500:600])
+    v = B[q]
+    nonc = np.any(v[:, 1] - v[:, 0] + v[:, 3] - v[:, 2] != 0, axis=1)
+    assert nonc.mean() > 0.99
+    for c in range(4):   # every component covers the basis
+        assert len(np.unique(q[:, c])) > 0.95 * len(B)

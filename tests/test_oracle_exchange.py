@@ -82,3 +82,27 @@ def test_box_exchange_two_ways():
     eps = ox.eps_box(R, R_F, L, a, w)
     assert abs(ox.Ex_from_eps(R, R_F, eps) - ox.Ex_box(R_F, L, a, w)) < 1e-12 * abs(eps).max() * 100
     assert np.all(eps < 0)
+
+
+def test_whole_grid_convolution_equals_pair_sums():
+    """eps on the whole grid as a 3D convolution of the occupation with the node sum (FFT)
+    equals the direct pair sum of eps_separable at every basis function, and is 0 outside
+    the basis sphere; a brute-force loop pins one point independently of both."""
+    for R, R_F, L, S in ((4, 2, 10.0, 32), (6, 6, 7.0, 40), (9, 3, 12.0, 48), (12, 9, 20.0, 64)):
+        n_sub, q_tail = oq.default_periodic_mesh(S, R)
+        a, w, _ = oq.laplace_mesh(S, n_sub, q_tail)
+        grid = ox.eps_separable_grid(R, R_F, L, a, w)
+        ref = ox.eps_on_grid(R, ox.eps_separable(R, R_F, L, a, w))
+        inside = ref != 0
+        assert np.array_equal(grid == 0, ~inside)
+        assert np.max(np.abs(grid[inside] - ref[inside]) / np.abs(ref[inside])) < 1e-13
+    R, R_F, L, S = 3, 2, 5.0, 24
+    a, w, _ = oq.laplace_mesh(S, *oq.default_periodic_mesh(S, R))
+    grid = ox.eps_separable_grid(R, R_F, L, a, w)
+    k = np.array([1, -2, 2])
+    s = 0.0
+    for j in ob.occupied(R_F):
+        d = k - j
+        if np.any(d != 0):
+            s += np.sum(w * np.exp(-a * float(d @ d))) / (np.pi * L)
+    assert abs(grid[k[0] + R, k[1] + R, k[2] + R] + s) < 1e-14 * s
