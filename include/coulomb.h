@@ -271,6 +271,16 @@ cc_status cc_test_stall_next_mixed(void);
  * captured.  CC_ERR_ARG for any other value. */
 cc_status cc_set_mixed_variant(int variant);
 
+/* Which form the plain FP32 exchange (cc_exchange_sums with CC_PREC_FP32) takes at grid
+ * sides 50..127 (not part of the paper; a diagnostic and comparison switch of this
+ * implementation, process-wide): 0 = automatic, the slab algorithm on the SIMT cores (the
+ * first mode product as window sums of the Fermi sphere's lines, the other two restricted
+ * to the band |y - R|, |z - R| <= R_F where they do not vanish; the same algorithm as the
+ * tensor-core slab kernel, in FP32 with Kahan-compensated node sums); 1 = the dense chain
+ * of strided batched SIMT GEMMs over the full grid (eight Mg^4 flop per node).  Smaller
+ * grids always take the fused per-node kernel.  CC_ERR_ARG for any other value. */
+cc_status cc_set_simt_variant(int variant);
+
 /* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
  * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the
  * products with an Mg^2-long side, each 0 = 64x64, 1 = 32x32, 2 = 64x32 outputs per CTA;

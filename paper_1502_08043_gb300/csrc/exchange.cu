@@ -352,6 +352,9 @@ static cc_status exchange_simt(cc_tables t, int R_F, T* eps, double* Ex, cudaStr
 
 using namespace cc;
 
+// which form the plain FP32 exchange takes at grid sides 50..127 (process-wide)
+static int g_simt_variant = 0;  // 0: automatic (SIMT slab kernel), 1: dense GEMM chain
+
 extern "C" cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev,
                                       double* Ex_dev, void* stream) {
   if (!t || !eps_dev || !Ex_dev) return CC_ERR_ARG;
@@ -360,6 +363,10 @@ extern "C" cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void*
   // grids up to 49 per side: fused per-node work items with shared-memory intermediates
   if (t->fused && (precision == CC_PREC_FP32 || precision == CC_PREC_FP64))
     return fused_single_exchange(t, R_F, precision, eps_dev, Ex_dev, st);
+  // FP32 at grid sides 50..127: the slab algorithm on the SIMT cores
+  if (precision == CC_PREC_FP32 && t->simt &&
+      __atomic_load_n(&g_simt_variant, __ATOMIC_ACQUIRE) == 0)
+    return simt_slab_run(t, t->simt, R_F, (float*)eps_dev, Ex_dev, st);
   switch (precision) {
     case CC_PREC_FP32: return exchange_simt<float>(t, R_F, (float*)eps_dev, Ex_dev, st);
     case CC_PREC_FP64: return exchange_simt<double>(t, R_F, (double*)eps_dev, Ex_dev, st);
@@ -367,6 +374,12 @@ extern "C" cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void*
     case CC_PREC_FP16X3: return exchange_mixed(t, R_F, precision, (float*)eps_dev, Ex_dev, st);
   }
   return CC_ERR_ARG;
+}
+
+extern "C" cc_status cc_set_simt_variant(int variant) {
+  if (variant < 0 || variant > 1) return CC_ERR_ARG;
+  __atomic_store_n(&g_simt_variant, variant, __ATOMIC_RELEASE);
+  return CC_OK;
 }
 
 // Tile selection for the SIMT mode products: small = Mg x Mg batched products, large =

@@ -90,6 +90,7 @@ struct cc_tables_s {
   cc::DevTables d;
   cc::Workspace ws;
   void* fused = nullptr;          // fused small-grid exchange plan (grid side <= 49)
+  void* simt = nullptr;           // SIMT slab exchange workspace (FP32, grid side 50..127)
   size_t table_bytes = 0;
   size_t device_bytes = 0;
   int Gc = 0;                     // codes of the general box tables per node (0: periodic)
@@ -129,6 +130,11 @@ void tc_slab_free(void* ws);
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
                       int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
                       bool half);
+// simtslab.cu (plain FP32 exchange by the slab algorithm, grid side 50..127)
+bool simt_slab_supported(cc_tables t);
+cc_status simt_slab_alloc(cc_tables t, void** out);
+void simt_slab_free(void* ws);
+cc_status simt_slab_run(cc_tables t, void* ws, int R_F, float* eps, double* Ex, cudaStream_t st);
 // tcslab_batch.cu: a batch of boxes through the batched form of the slab kernel, over the
 // step chain's concatenated T planes ([rows][Np] bf16; box b's node 0 at row t_row0[b])
 cc_status tc_slab_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,

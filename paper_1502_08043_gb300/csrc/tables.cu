@@ -576,6 +576,7 @@ static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_t
     CC_TRY(workspace_alloc(t));
     if (t->Mg <= 128) CC_TRY(mixed_workspace_alloc(t));
     CC_TRY(fused_single_alloc(t));
+    CC_TRY(simt_slab_alloc(t, &t->simt));
   }
   return CC_OK;
 }
@@ -744,6 +745,8 @@ cc_status cc_tables_free(cc_tables t) {
   workspace_free(t);
   mixed_workspace_free(t);
   fused_single_free(t);
+  simt_slab_free(t->simt);
+  t->simt = nullptr;
   free_tables(t);
   delete t;
   return CC_OK;
@@ -843,6 +846,7 @@ cc_status cc_tables_load(const char* path, void* stream, cc_tables* out) {
     if (s == CC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = CC_ERR_CUDA;
     if (s == CC_OK && t->Mg <= 128) s = mixed_workspace_alloc(t);
     if (s == CC_OK) s = fused_single_alloc(t);
+    if (s == CC_OK) s = simt_slab_alloc(t, &t->simt);
   }
   if (s != CC_OK) {
     cc_tables_free(t);
