@@ -102,6 +102,23 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense bf16 tensor peak (TFLOP/s): the measured cuBLAS burst figure, else the
+    fallback measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def _sig(x, n=4):
+    """x rounded to n significant digits (compact JSON)."""
+    if x is None or x == 0 or not np.isfinite(x):
+        return x
+    return float(f"{x:.{n}g}")
+
+
 # ------------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -286,10 +303,8 @@ def run_gpu(args):
                "ms_per_step": ems}
 
     peak, peak_kind = _peaks()
-    # ncu DRAM bytes of one k_col launch for 2e7 quadruples, scaled by the quadruples of
-    # this launch: id form 320.1 MB read + 50.2 MB written (profiles/k_col_paper_scale.md),
-    # vector form profiles/k_col_vec_paper_scale.md, uint16 form
-    # profiles/k_col_ids16_paper_scale.md
+    # ncu DRAM bytes (read + written) of one k_col launch for 2e7 quadruples, per quadruple
+    # encoding (TRAFFIC_2E7), scaled by the quadruples of this launch
     if args.traffic is None and lookup == "collapsed":
         args.traffic = TRAFFIC_2E7.get(args.quad_format)
         args.traffic = None if args.traffic is None else args.traffic * n / 2e7
@@ -330,9 +345,16 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["batched"] = batched()
         line["large_lookups"] = large_lookups()
+        line["general_lookups"] = general_lookups()
         line["paper_replay"] = paper_replay()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    if rank == 0 and world == 1:
+        # last on the line: the metric's mixed-vs-FP32 comparison in compact form
+        line["mixed_vs_fp32"] = mixed_vs_fp32(line.get("mode_products"),
+                                              line.get("large_lookups"),
+                                              line.get("batched"),
+                                              line.get("general_lookups"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     t.free()
@@ -344,11 +366,31 @@ def run_gpu(args):
 MP_CONFIGS = {"precision": (31, 40.0, 96, 20), "large": (63, 60.0, 128, 40)}
 
 
+def tc_slab_executed_flop(R, R_F, Mg, S_eff, periodic=True):
+    """Flop the tensor-core slab kernel issues for one exchange call: per (slab pair, node)
+    unit and slab, MMA1 (3 x 128 x B x B), MMA2 (3 x 128 x B x N2) and, when the A term runs
+    on the tensor cores (periodic, band B <= 96), 2 x 128 x B x 16 nh; B = the band rounded
+    out to 16-column pieces, N2 = the grid side rounded up to 16, nh = ceil((R_F + 1) / 16)."""
+    B = ((R + R_F + 16) & ~15) - ((R - R_F) & ~15)
+    N2 = (Mg + 15) & ~15
+    nh = (R_F + 16) >> 4
+    per_slab = 2 * 128 * (3 * B * B + 3 * B * N2 + (2 * B * 16 * nh if periodic and B <= 96 else 0))
+    return per_slab * 2 * ((Mg + 1) // 2) * S_eff
+
+
+def simt_slab_flop(R_F, Mg, S_eff):
+    """Flop of the SIMT slab algorithm: per (slab, node), U = T[:, band] R' (Mg x nb x nb)
+    and E += U T[band, :] (Mg x nb x Mg), nb = 2 R_F + 1."""
+    nb = 2 * R_F + 1
+    return 2.0 * Mg * nb * (nb + Mg) * Mg * S_eff
+
+
 def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
-    """Exchange sums of one single-box workload by the plain FP32 mode products and by the
-    bf16x3 and fp16x3 tensor-core paths: device time per call (CUDA events, inputs
-    resident), useful flop rate 6 Mg^4 S_eff, and the accuracy of each against the FP64
-    oracle on a seeded sample of basis functions."""
+    """Exchange sums of one single-box workload by the plain FP32 SIMT path (the slab
+    algorithm, and the dense GEMM chain over the full grid), and by the bf16x3 and fp16x3
+    tensor-core slab kernel: device time per call (CUDA events, inputs resident), useful
+    flop rate 6 Mg^4 S_eff, executed tensor flop rate, and the accuracy of each against the
+    FP64 oracle on a seeded sample of basis functions."""
     import torch
 
     import paper_1502_08043_gb300 as cc
@@ -358,26 +400,43 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
     t = cc.build_tables("periodic", R=R, L=L, S=S)
     Mg, S_eff = t.info["Mg"], t.info["S_eff"]
     out = {"R": R, "L_bohr": L, "S": S, "S_eff": S_eff, "R_F": R_F, "Mg": Mg}
+    peak, peak_kind = _bf16_peak()
     res = {}
-    precs = ["fp32", "bf16x3"] + (["fp16x3"] if with_fp16 else [])
+    precs = ["fp32", "fp32_dense", "bf16x3"] + (["fp16x3"] if with_fp16 else [])
     for prec in precs:
         eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
         Ex = torch.empty(2, dtype=torch.float64, device=dev)
-        for _ in range(2):
-            cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(st)
-        for _ in range(reps):
-            cc.exchange_sums(t, R_F, eps, Ex, precision=prec)
-        b.record(st)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / reps
+        p = "fp32" if prec == "fp32_dense" else prec
+        cc.lib().cc_set_simt_variant(1 if prec == "fp32_dense" else 0)
+        try:
+            n = max(2, reps // 4) if prec == "fp32_dense" else reps
+            for _ in range(2):
+                cc.exchange_sums(t, R_F, eps, Ex, precision=p)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            for _ in range(n):
+                cc.exchange_sums(t, R_F, eps, Ex, precision=p)
+            b.record(st)
+            torch.cuda.synchronize()
+        finally:
+            cc.lib().cc_set_simt_variant(0)
+        ms = a.elapsed_time(b) / n
         res[prec] = (ms, eps.cpu().numpy().astype(np.float64), float(Ex[0].item()))
         out[prec + "_ms"] = ms
         out[prec + "_useful_tflops"] = 6.0 * Mg ** 4 * S_eff / (ms * 1e-3) / 1e12
+    out["fp32_executed_tflops"] = simt_slab_flop(R_F, Mg, S_eff) / (res["fp32"][0] * 1e-3) / 1e12
+    ex = tc_slab_executed_flop(R, R_F, Mg, S_eff)
+    for prec in ("bf16x3", "fp16x3") if with_fp16 else ("bf16x3",):
+        out[prec + "_executed_tflops"] = ex / (res[prec][0] * 1e-3) / 1e12
+        out[prec + "_useful_frac_of_peak"] = out[prec + "_useful_tflops"] / peak
+        out[prec + "_executed_frac_of_peak"] = out[prec + "_executed_tflops"] / peak
+    out["bf16_peak_tflops"] = peak
+    out["peak_source"] = peak_kind + " bf16 burst (MEASURED_PEAKS.json)"
     out["speedup_bf16x3_vs_fp32"] = res["fp32"][0] / res["bf16x3"][0]
+    out["speedup_bf16x3_vs_fp32_dense"] = res["fp32_dense"][0] / res["bf16x3"][0]
+    out["speedup_fp32_vs_fp32_dense"] = res["fp32_dense"][0] / res["fp32"][0]
     if with_fp16:
         out["speedup_fp16x3_vs_fp32"] = res["fp32"][0] / res["fp16x3"][0]
     if oracle_sample:
@@ -397,6 +456,38 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
             out[prec + "_max_rel_err_vs_oracle"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
         out["oracle_sample"] = f"{len(idx)} seeded basis functions of {Nb}"
     t.free()
+    return out
+
+
+def mixed_vs_fp32(mp, large, batched_sec, general):
+    """The metric's mixed-vs-FP32 comparison in a compact form (the end of the JSON line):
+    per single-box workload the FP32 times (slab algorithm and dense chain), the bf16x3 and
+    fp16x3 times, tensor fractions of the measured bf16 peak (useful 6 Mg^4 S flop and
+    executed flop), errors against the FP64 oracle, speedups at equal stated accuracy."""
+    out = {}
+    for name, tag in (("precision", "cfg3_grid63"), ("large", "cfg5_grid127")):
+        m = mp.get(name) if mp else None
+        if not m:
+            continue
+        out[tag] = {
+            "ms": {k: _sig(m.get(k + "_ms")) for k in ("fp32", "fp32_dense", "bf16x3", "fp16x3")},
+            "bf16x3_frac_useful": _sig(m.get("bf16x3_useful_frac_of_peak"), 3),
+            "bf16x3_frac_exec": _sig(m.get("bf16x3_executed_frac_of_peak"), 3),
+            "fp32_exec_tflops": _sig(m.get("fp32_executed_tflops"), 3),
+            "err": {k: _sig(m.get(k + "_max_rel_err_vs_oracle"), 2)
+                    for k in ("fp32", "bf16x3", "fp16x3")},
+            "x_bf16x3_vs_fp32": _sig(m.get("speedup_bf16x3_vs_fp32"), 3),
+            "x_bf16x3_vs_fp32_dense": _sig(m.get("speedup_bf16x3_vs_fp32_dense"), 3),
+        }
+    if batched_sec:
+        out["batch256_ms"] = {k: _sig(batched_sec[k]["ms_per_batch"]) for k in ("fp32", "bf16x3", "fp64")
+                              if k in batched_sec}
+    if large:
+        out["cfg5_1e9_lookups"] = {k: {"ms": _sig(v["ms"]), "hbm_frac": _sig(v["hbm_frac"], 3)}
+                                   for k, v in large.items() if isinstance(v, dict)}
+    if general:
+        out["general_box_lookups"] = {"integrals_per_s": _sig(general["fp32"]["integrals_per_s"]),
+                                      "fp64_integrals_per_s": _sig(general["fp64"]["integrals_per_s"])}
     return out
 
 
@@ -567,10 +658,66 @@ def large_lookups(n=1_000_000_000, reps=3):
     return out
 
 
+def general_lookups(n=20_000_000, reps=5):
+    """General (not necessarily momentum-conserving) box-kernel integrals at the paper's
+    stored-table case: 9171 planewaves (|n| <= 13), box side 2 bohr, Mesh 1 with Q = 90
+    (180 nodes; Sec. III quotes < 2.4 MB of tables for it).  n quadruples of four independent
+    uniform ids (almost all non-conserving), generated on the device, uint16 ids.  The
+    two-index tables (one row of S_pad node values per canonical (D1, D2) code) exceed
+    shared memory, so every integral reads 3 rows through L1: the kernel is bound by L1
+    bandwidth (152 SMs x 128 B/clk), not by HBM."""
+    import torch
+
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev)
+    t = cc.build_tables("box", R=13, L=2.0, S=180, n_sub=0, q_tail=90)
+    info = t.info
+    q = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    ci.quads_device(13, 0, n, q, stream=ci.STREAM_UNIFORM)
+    q16 = torch.where(q >= 32768, q - 65536, q).to(torch.int16)
+    del q
+    S_pad = 32 * ((info["S_eff"] + 31) // 32)
+    nb = 9171
+    out = {"quadruples": n, "R": 13, "L_bohr": 2.0, "S_eff": info["S_eff"],
+           "codes_per_node": info["general_codes"],
+           "paper_entries_per_node_4N23": 4.0 * nb ** (2.0 / 3.0),
+           "table_fp64_bytes": 8 * info["general_codes"] * info["S_eff"],
+           "table_fp32_lookup_bytes": info["general_table_bytes"],
+           "paper_table_bytes_claim": "< 2.4 MB (Sec. III, 9171 planewaves)"}
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = 2.07e9
+    for prec, dt, eb in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+        vals = torch.empty(n, dtype=dt, device=dev)
+        cc.reconstruct_integrals(t, q16, vals, lookup="general")
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            cc.reconstruct_integrals(t, q16, vals, lookup="general")
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        l1 = 3.0 * S_pad * eb * n / (ms * 1e-3)
+        out[prec] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3),
+                     "hbm_GBps": (8 + eb) * n / (ms * 1e-3) / 1e9,
+                     "l1_table_GBps": l1 / 1e9,
+                     "l1_frac": l1 / (sm * 128 * clk)}
+        del vals
+    out["l1_peak_note"] = f"{sm} SMs x 128 B/clk x 2.07 GHz"
+    t.free()
+    del q16
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------- oracle
-def oracle_sample(budget_s: float):
+def oracle_sample(budget_s: float, part: int = 0):
     """Run the FP64 oracle on a bounded sample of the workload; returns (evals, seconds,
-    description)."""
+    description).  `part` selects a disjoint slice of the quadruple stream, pair rows and k
+    points (one per worker of the all-core baseline)."""
     import coulomb_inputs as ci
     from oracle import exchange as ox
     from oracle import quadrature as oq
@@ -580,29 +727,79 @@ def oracle_sample(budget_s: float):
     keep = oq.prune_periodic(a, w, R, 1e-9)
     a, w = a[keep], w[keep]
     Nb, Mocc = 9171, 2109
-    nq, rows, nk = 0, 0, 0
     chunk_q, chunk_r, chunk_k = 200_000, 20, 64
+    q0, r0, k0 = part * 50_000_000, part * 577, part * 4099
+    nq, rows, nk = 0, 0, 0
     t0 = time.perf_counter()
     # the same mix as a GPU step: quadruples : pairs : exchange = 1e8 : Nb^2 : Nb Mocc
     while time.perf_counter() - t0 < budget_s:
-        q = ci.quads(R, nq, chunk_q)
+        q = ci.quads(R, q0 + nq, chunk_q)
         orc.reconstruct(q, R, L, "separable", a=a, w=w)
         nq += chunk_q
-        orc.pair_matrix(R, L, rows=np.arange(rows, rows + chunk_r) % Nb, value="separable", a=a, w=w)
+        orc.pair_matrix(R, L, rows=np.arange(r0 + rows, r0 + rows + chunk_r) % Nb,
+                        value="separable", a=a, w=w)
         rows += chunk_r
-        ox.eps_separable(R, R_F, L, a, w, k_idx=np.arange(nk, nk + chunk_k) % Nb)
+        ox.eps_separable(R, R_F, L, a, w, k_idx=np.arange(k0 + nk, k0 + nk + chunk_k) % Nb)
         nk += chunk_k
     dt = time.perf_counter() - t0
     evals = nq + rows * Nb + nk * Mocc
     desc = (f"{nq} quadruples + {rows} pair rows x {Nb} + eps at {nk} k x {Mocc} occupied, "
-            f"FP64 numpy node sums (oracle as it stands), single thread")
+            f"FP64 numpy node sums (oracle as it stands)")
     return evals, dt, desc
 
 
+def _oracle_worker(job):
+    budget, part = job
+    return oracle_sample(budget, part)
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_all_cores(seconds: float):
+    """The oracle on every host core at once: one single-threaded worker process per core
+    (spawned, numpy pinned to one thread), each on its own slice of the workload for
+    `seconds`; value = all evaluations / the slowest worker's time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                           "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(seconds, k) for k in range(cores)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    evals = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    desc = (f"{cores} workers x ({res[0][2]}), each {seconds:.0f} s on its own slice; "
+            f"{evals} evaluations in total")
+    return evals, dt, desc, cores
+
+
 def cpu_baseline(seconds=12.0):
-    evals, dt, desc = oracle_sample(seconds)
-    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-            "seconds": dt, "host_cores_available": os.cpu_count()}
+    evals, dt, desc, cores = oracle_all_cores(seconds)
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "seconds": dt, "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -611,9 +808,9 @@ def run_reference(args):
         return
     for _ in range(args.warmup):
         oracle_sample(0.2)
-    tot_e, tot_t, desc = 0, 0.0, ""
+    tot_e, tot_t, desc, cores = 0, 0.0, "", 1
     for _ in range(args.steps):
-        e, dt, desc = oracle_sample(args.ref_seconds)
+        e, dt, desc, cores = oracle_all_cores(args.ref_seconds)
         tot_e += e
         tot_t += dt
     v = tot_e / tot_t
@@ -622,10 +819,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 quadruples; shell-closed Fermi sphere)",
             "config": {"workload": WORKLOAD, "R": R, "L_bohr": L, "S": S, "R_F": R_F,
-                       "lookup": "separable", "parallelism": "oracle, rank 0 only"},
+                       "lookup": "separable", "parallelism": f"oracle, rank 0 only, {cores} host cores"},
             "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": desc, "value": v,
-                             "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": desc, "value": v,
+                             "unit": UNIT, "cpu_model": _cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -656,6 +853,8 @@ def main():
                     help="only run the mode-product comparison of this workload, print it")
     ap.add_argument("--batched-only", action="store_true",
                     help="only run the 256-box batched section, print it")
+    ap.add_argument("--general-only", action="store_true",
+                    help="only run the general box-integral lookup section, print it")
     ap.add_argument("--replay-only", action="store_true",
                     help="only run the Table I / Fig. 1 replay through the GPU path, print it")
     ap.add_argument("--traffic", type=float, default=None,
@@ -671,6 +870,8 @@ def main():
         print(json.dumps({"paper_replay": paper_replay()}))
     elif args.batched_only:
         print(json.dumps({"batched": batched()}))
+    elif args.general_only:
+        print(json.dumps({"general_lookups": general_lookups()}))
     else:
         run_gpu(args)
 
