@@ -130,6 +130,12 @@ void tc_slab_free(void* ws);
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
                       int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
                       bool half);
+// tcsmall.cu (tensor-core exchange, bf16x3, grid side up to 64: two slabs per 128-row MMA)
+bool tc_small_supported(cc_tables t);
+cc_status tc_small_alloc(cc_tables t, void** out);
+void tc_small_free(void* ws);
+cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F, float* eps,
+                       double* Ex, cudaStream_t st);
 // simtslab.cu (plain FP32 exchange by the slab algorithm, grid side 50..127)
 bool simt_slab_supported(cc_tables t);
 cc_status simt_slab_alloc(cc_tables t, void** out);

@@ -541,6 +541,7 @@ struct MxPlanes {  // one element type
 struct MxWorkspace {
   int Np = 0, C = 0, R_F_built = -1, R_F_built16 = -1;
   void* slab = nullptr;   // fused slab kernel workspace (Np = 128), tcslab.cu
+  void* small = nullptr;  // small-grid kernel workspace (grid side <= 64), tcsmall.cu
   float* E = nullptr;     // [Np^3]
   int* err = nullptr;     // device error word
   MxPlanes bf, hf;
@@ -672,6 +673,7 @@ cc_status mixed_workspace_alloc(cc_tables t) {
   CC_TRY(build_planes<__nv_bfloat16>(t, w, &w->bf, true));
   CC_TRY(build_planes<__half>(t, w, &w->hf, false));
   CC_TRY(tc_slab_alloc(t, &w->slab));
+  CC_TRY(tc_small_alloc(t, &w->small));
   CC_CUDA(cudaDeviceSynchronize());
   return CC_OK;
 }
@@ -680,6 +682,7 @@ void mixed_workspace_free(cc_tables t) {
   MxWorkspace* w = reinterpret_cast<MxWorkspace*>(t->ws.mx);
   if (!w) return;
   tc_slab_free(w->slab);
+  tc_small_free(w->small);
   for (void* p : w->allocs) cudaFree(p);
   delete w;
   t->ws.mx = nullptr;
@@ -697,7 +700,8 @@ static int tc_sm_count() {
 }
 
 static int g_stall_next = 0;
-static int g_mixed_variant = 0;  // 0: automatic, 1: step chain, 2: fused slab kernel
+// 0: automatic, 1: step chain, 2: fused slab kernel, 3: small-grid kernel (bf16x3)
+static int g_mixed_variant = 0;
 
 template <int NP, typename E>
 static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const CUtensorMap& B,
@@ -814,12 +818,18 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
     if (w->Np == 64) return run_mixed<64, __half>(t, w, w->hf, R_F, eps, Ex, st);
     return run_mixed<128, __half>(t, w, w->hf, R_F, eps, Ex, st);
   }
-  if (w->slab && g_mixed_variant != 1) {
+  const int variant = __atomic_load_n(&g_mixed_variant, __ATOMIC_ACQUIRE);
+  if (w->small && (variant == 0 || variant == 3)) {
+    const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
+    return tc_small_run(t, w->small, w->err, stall, R_F, eps, Ex, st);
+  }
+  if (variant == 3) return CC_ERR_NOTSUPP;
+  if (w->slab && variant != 1) {
     const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
     return tc_slab_run(t, w->slab, &w->bf.mTT[0], &w->bf.mTT[1], w->err, stall, R_F, eps, Ex,
                        st, false);
   }
-  if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
+  if (variant == 2) return CC_ERR_NOTSUPP;
   if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
   return run_mixed<128, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
 }
@@ -829,7 +839,7 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
 // Choice between the two bf16x3 forms (automatic: the fused slab kernel, every grid side
 // up to 127).
 extern "C" cc_status cc_set_mixed_variant(int variant) {
-  if (variant < 0 || variant > 2) return CC_ERR_ARG;
+  if (variant < 0 || variant > 3) return CC_ERR_ARG;
   __atomic_store_n(&cc::g_mixed_variant, variant, __ATOMIC_RELEASE);
   return CC_OK;
 }

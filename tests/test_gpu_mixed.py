@@ -234,7 +234,7 @@ def test_slab_kernel_fp16x3_vs_chain_and_oracle(dev, kernel, R, R_F):
 def test_slab_kernel_variant_errors(dev):
     import paper_1502_08043_gb300 as cc
     L = cc.lib()
-    assert L.cc_set_mixed_variant(3) == 1 and L.cc_set_mixed_variant(-1) == 1
+    assert L.cc_set_mixed_variant(4) == 1 and L.cc_set_mixed_variant(-1) == 1
     assert L.cc_set_mixed_variant(0) == 0
 
 
