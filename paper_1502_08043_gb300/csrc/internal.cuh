@@ -136,6 +136,11 @@ cc_status tc_small_alloc(cc_tables t, void** out);
 void tc_small_free(void* ws);
 cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F, float* eps,
                        double* Ex, cudaStream_t st);
+bool tc_small_batch_supported(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F);
+cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
+                                const std::vector<long long>& eps_off, void** out);
+cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStream_t st);
+void tc_small_batch_free(void* p);
 // simtslab.cu (plain FP32 exchange by the slab algorithm, grid side 50..127)
 bool simt_slab_supported(cc_tables t);
 cc_status simt_slab_alloc(cc_tables t, void** out);

@@ -41,8 +41,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete sleeps until it
+// completes or the hint (ns) runs out, instead of spinning and taking issue slots and
+// barrier-unit cycles from the other warps of its scheduler (the MMA issuer among them)
+__device__ __forceinline__ bool mbar_try_hint(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // bounded wait: gives up after ~2 s of wall time and reports through *err, or returns
-// early (without an error code of its own) once another role of the CTA has aborted
+// early (without an error code of its own) once another role of the CTA has aborted; the
+// abort flag and the timer are checked at least every 20 us of sleep
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
@@ -51,8 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
-    for (int i = 0; i < 256; ++i)
-      if (mbar_try(bar, parity)) return true;
+    if (mbar_try_hint(bar, parity, 20000u)) return true;
     if (abort_flag && *abort_flag) return false;
     if (global_ns() - t0 > limit_ns) {
       atomicCAS(err, 0, code);

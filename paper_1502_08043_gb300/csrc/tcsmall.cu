@@ -24,9 +24,10 @@
 // tensor memory over the CTA's run of nodes and leaves once as a partial; a second kernel
 // adds the partials of each pair in a fixed order, the Dbar term, and forms eps and E_x.
 //
-// Pipeline: the node planes (T_s, F_s), the R^T operand, D1 and the U operand are all
-// double buffered, so the MMA warp issues MMA1(i), MMA2(i - 1), MMA1(i + 1), ... while the
-// builders form R^T of unit i + 1 and the epilogue converts D1 of unit i.
+// Pipeline: T_s (read by both products) has three buffers and F_s, the R^T operand, D1 and
+// the U operand two each, so the MMA warp issues MMA1(i), MMA2(i - 1), MMA1(i + 1), ...
+// while the builders form R^T of unit i + 1, the epilogue converts D1 of unit i, and the
+// TMA loads of unit i + 2 need only MMA2(i - 1) (T) and MMA1(i) (F) to have finished.
 // Tensor memory (256 columns): [0, 64) D1[0], [64, 128) D1[1], [128, 192) E.
 // Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 32 (w / 4) ..), 8-10 and 12-14
 // build R^T and P, 11 TMA producer, 15 MMA issuer.  Every wait is bounded (global timer);
@@ -58,21 +59,34 @@ constexpr uint32_t kPl64 = kG * kG * 2;       // 64 x 64 bf16 plane: 8 KB
 constexpr uint32_t kPl128 = 128 * kG * 2;     // 128 x 64 bf16 plane: 16 KB
 // shared memory (1024-byte aligned base)
 constexpr uint32_t kOffU = 0;                       // 2 x (U hi, U lo) MN-major: 64 KB
-constexpr uint32_t kOffNode = kOffU + 4 * kPl128;   // 2 x (T hi, T lo, F hi, F lo): 64 KB
-constexpr uint32_t kOffA = kOffNode + 8 * kPl64;    // 2 x (R^T hi, R^T lo): 64 KB
+constexpr uint32_t kOffT = kOffU + 4 * kPl128;      // 3 x (T hi, T lo): 48 KB
+constexpr uint32_t kOffF = kOffT + 6 * kPl64;       // 2 x (F hi, F lo): 32 KB
+constexpr uint32_t kOffA = kOffF + 4 * kPl64;       // 2 x (R^T hi, R^T lo): 64 KB
 constexpr uint32_t kOffP = kOffA + 4 * kPl128;      // P one-hot: 16 KB
 constexpr uint32_t kOffBar = kOffP + kPl128;        // mbarriers, tensor-memory slot
-constexpr int kNumBars = 22;
+constexpr int kNumBars = 29;
 constexpr uint32_t kOffIsq = kOffBar + 8 * kNumBars + 16;  // floor(sqrt(v)), v <= R_F^2
 constexpr uint32_t kSmemBytes = kOffIsq + 1024 + 1024;     // isq (R_F <= 31) + alignment
 constexpr uint32_t kTmemCols = 256;
 
+// one box of a launch (single boxes: the only one, from the kernel parameters; batches:
+// a table in global memory, boxes in unit order)
+struct SBox {
+  int R, RF, Mg, S;
+  long long unit0;  // first work unit (units of a box: pair-major, node-minor)
+  long long fr0;    // FR / F / T planes: node s of the box at plane row (fr0 / 64) + 64 s
+  long long w0;     // w: node s at w0 + s
+  long long part0;  // part: pair p, segment k at part0 + (p * maxseg + k) * 128 * 64
+  int maxseg, pad;
+};
+
 struct Args {
-  int R, R_F, Mg, S, periodic;
-  int units, maxseg;
-  const uint32_t* FR;  // [S][64][64] F_s[a][h] as bf16 hi (low half) | lo (high half)
-  const float* w;      // [S]
-  float* part;         // [pairs * maxseg][128][64] partial E of a slab pair
+  const SBox* boxes;  // batches: nbox entries; single boxes: nullptr (b0 is used)
+  SBox b0;
+  int nbox, units, rf_max;
+  const uint32_t* FR;  // [nodes][64][64] F_s[a][h] as bf16 hi (low half) | lo (high half)
+  const float* w;      // [nodes]
+  float* part;         // partial E of a slab pair: [128][64] per (pair, segment)
   int* err;
   int stall_test;
 };
@@ -83,6 +97,42 @@ __host__ __device__ inline int owner_cta(long long u, int units, int grid) {
   while (c > 0 && (long long)c * units / grid > u) --c;
   return c;
 }
+
+// the box of a role's current unit; batches walk the table forward as units increase
+template <bool kBatch>
+struct BoxCursor {
+  SBox X;
+  int b = 0;
+  long long next = 0;
+  __device__ __forceinline__ void init(const Args& g, long long u) {
+    if constexpr (kBatch) {
+      int lo = 0, hi = g.nbox - 1;  // last box with unit0 <= u
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.boxes[mid].unit0 <= u) lo = mid;
+        else hi = mid - 1;
+      }
+      b = lo;
+      X = g.boxes[b];
+      next = b + 1 < g.nbox ? g.boxes[b + 1].unit0 : 0x7fffffffffffffffll;
+    } else {
+      X = g.b0;
+      next = 0x7fffffffffffffffll;
+    }
+  }
+  // true when u starts a new box
+  __device__ __forceinline__ bool advance(const Args& g, long long u) {
+    if constexpr (kBatch) {
+      if (u < next) return false;
+      while (b + 1 < g.nbox && g.boxes[b + 1].unit0 <= u) ++b;
+      X = g.boxes[b];
+      next = b + 1 < g.nbox ? g.boxes[b + 1].unit0 : 0x7fffffffffffffffll;
+      return true;
+    } else {
+      return false;
+    }
+  }
+};
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);
@@ -111,7 +161,7 @@ __device__ __forceinline__ void mma_x2_ss_w(uint32_t tmem_d, uint64_t a, uint64_
       : "memory");
 }
 
-template <bool kPeriodic>
+template <bool kPeriodic, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tcs(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
           const __grid_constant__ CUtensorMap mFh, const __grid_constant__ CUtensorMap mFl,
@@ -122,8 +172,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* gb = smem_raw + (base - raw);
   const uint8_t* isq = gb + kOffIsq;
   const uint32_t bar = base + kOffBar;
-  auto nfull = [&](int k) { return bar + 8u * k; };          // 0, 1
-  auto nfree = [&](int k) { return bar + 8u * (2 + k); };    // 2, 3
+  auto ffull = [&](int k) { return bar + 8u * (0 + k); };    // 0, 1 (F buffer k)
+  auto ffree = [&](int k) { return bar + 8u * (2 + k); };    // 2, 3
   auto afull = [&](int k) { return bar + 8u * (4 + k); };    // 4, 5
   auto afree = [&](int k) { return bar + 8u * (6 + k); };    // 6, 7
   auto d1full = [&](int k) { return bar + 8u * (8 + k); };   // 8, 9
@@ -133,16 +183,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t efull = bar + 8u * 16, edone = bar + 8u * 17;
   const uint32_t pfull = bar + 8u * 18, pfree = bar + 8u * 19;
   const uint32_t never = bar + 8u * 20, drain = bar + 8u * 21;
+  auto tfull = [&](int k) { return bar + 8u * (22 + k); };   // 22, 23, 24 (T buffer k)
+  auto tfree = [&](int k) { return bar + 8u * (25 + k); };   // 25, 26, 27
+  const uint32_t zbar = bar + 8u * 28;  // builders: an R^T buffer is cleared for a new box
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int R = g.R, RF = g.R_F, S = g.S;
   if (tid == 0) {
     s_abort = 0;
+    for (int k = 0; k < 3; ++k) {
+      mbar_init(tfull(k), 1);
+      mbar_init(tfree(k), 1);
+    }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(nfull(k), 1);
-      mbar_init(nfree(k), 1);
+      mbar_init(ffull(k), 1);
+      mbar_init(ffree(k), 1);
       mbar_init(afull(k), kBldWarps);
       mbar_init(afree(k), 1);
       mbar_init(d1full(k), 1);
@@ -156,6 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(pfree, 1);
     mbar_init(never, 1);
     mbar_init(drain, 1);
+    mbar_init(zbar, kBldWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -165,14 +222,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int v = tid; v <= RF * RF; v += kThreads) {
+  for (int v = tid; v <= g.rf_max * g.rf_max; v += kThreads) {
     int h = (int)sqrtf((float)v);
     while (h * h > v) --h;
     while ((h + 1) * (h + 1) <= v) ++h;
     gb[kOffIsq + v] = (uint8_t)h;
   }
-  // R^T operands start all zero (builders only ever write the band), and so do the U
-  // operands (the epilogue writes every K index of the band it reads)
+  // R^T operands start all zero (builders only ever write the band of the current box and
+  // clear a buffer when a new box starts using it), and so do the U operands (the epilogue
+  // writes every K index of the band it reads)
   for (uint32_t o = 16u * tid; o < 4 * kPl128; o += 16u * kThreads) {
     *reinterpret_cast<uint4*>(gb + kOffA + o) = make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(gb + kOffU + o) = make_uint4(0u, 0u, 0u, 0u);
@@ -183,117 +241,154 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // the band [zs, ze) of y, y' and z in 16-aligned K steps
-  const int zs = (R - RF) & ~15, ze0 = (R + RF + 16) & ~15, ze = ze0 < kG ? ze0 : kG;
   const long long u0 = (long long)blockIdx.x * g.units / gridDim.x;
   const long long u1 = (long long)(blockIdx.x + 1) * g.units / gridDim.x;
+  // the band [zs, ze) of y, y' and z of box X in 16-aligned K steps
+  auto band_lo = [](const SBox& X) { return (X.R - X.RF) & ~15; };
+  auto band_hi = [](const SBox& X) {
+    const int e = (X.R + X.RF + 16) & ~15;
+    return e < kG ? e : kG;
+  };
 
   if (warp == kProdWarp) {
     if (lane == 0) {
-      // ---------------- TMA producer: T_s (and F_s) hi + lo into node buffer (unit & 1)
-      const uint32_t bytes = kPeriodic ? 4 * kPl64 : 2 * kPl64;
+      // ---------------- TMA producer: T_s hi + lo into T buffer (unit % 3), F_s hi + lo
+      // (periodic) into F buffer (unit & 1)
+      BoxCursor<kBatch> C;
+      if (u0 < u1) C.init(g, u0);
       uint32_t n = 0;
       for (long long u = u0; u < u1 && !s_abort; ++u, ++n) {
-        const int s = (int)(u % S), k = (int)(n & 1u);
-        if (!mbar_wait(nfree(k), ((n >> 1) & 1u) ^ 1u, g.err, 41, &s_abort)) {
+        C.advance(g, u);
+        const int s = (int)((u - C.X.unit0) % C.X.S), kt = (int)(n % 3u), kf = (int)(n & 1u);
+        const int row = (int)(C.X.fr0 / kG) + s * kG;
+        if (!mbar_wait(tfree(kt), ((n / 3u) & 1u) ^ 1u, g.err, 41, &s_abort)) {
           s_abort = 1;
           break;
         }
-        const uint32_t dst = base + kOffNode + k * 4 * kPl64;
-        mbar_expect_tx(nfull(k), bytes);
-        tma_load_2d(dst, &mTh, 0, s * kG, nfull(k));
-        tma_load_2d(dst + kPl64, &mTl, 0, s * kG, nfull(k));
+        const uint32_t dt = base + kOffT + kt * 2 * kPl64;
+        mbar_expect_tx(tfull(kt), 2 * kPl64);
+        tma_load_2d(dt, &mTh, 0, row, tfull(kt));
+        tma_load_2d(dt + kPl64, &mTl, 0, row, tfull(kt));
         if (kPeriodic) {
-          tma_load_2d(dst + 2 * kPl64, &mFh, 0, s * kG, nfull(k));
-          tma_load_2d(dst + 3 * kPl64, &mFl, 0, s * kG, nfull(k));
+          if (!mbar_wait(ffree(kf), ((n >> 1) & 1u) ^ 1u, g.err, 41, &s_abort)) {
+            s_abort = 1;
+            break;
+          }
+          const uint32_t df = base + kOffF + kf * 2 * kPl64;
+          mbar_expect_tx(ffull(kf), 2 * kPl64);
+          tma_load_2d(df, &mFh, 0, row, ffull(kf));
+          tma_load_2d(df + kPl64, &mFl, 0, row, ffull(kf));
         }
       }
-      for (uint32_t m = n > 2 ? n - 2 : 0; m < n; ++m)
-        mbar_wait(nfull(m & 1u), (m >> 1) & 1u, g.err, 42, nullptr, 100000000ull);
+      // copies still in flight land before the CTA leaves
+      for (uint32_t m = n > 3 ? n - 3 : 0; m < n; ++m)
+        mbar_wait(tfull(m % 3u), (m / 3u) & 1u, g.err, 42, nullptr, 100000000ull);
+      if (kPeriodic)
+        for (uint32_t m = n > 2 ? n - 2 : 0; m < n; ++m)
+          mbar_wait(ffull(m & 1u), (m >> 1) & 1u, g.err, 42, nullptr, 100000000ull);
     }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer (the whole warp; every wait result made warp-uniform)
     auto all = [](bool v) { return __all_sync(0xffffffffu, v); };
-    const uint32_t N2 = (uint32_t)((g.Mg + 15) & ~15);
     constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
-    const uint32_t idesc1 = idesc0 | ((N2 >> 3) << 17);              // A, B K-major
-    const uint32_t idesc2 = idesc0 | (1u << 15) | ((N2 >> 3) << 17);  // A MN-major
     if (g.stall_test && !all(mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull))) s_abort = 1;
-    const int ms = zs >> 4, me = ze >> 4;
-    const int nh = (RF + 16) >> 4;  // K steps of h in the A term
     const uint64_t dP = sdesc(base + kOffP);
-    auto mma1 = [&](uint32_t i) {
+    // K steps and N of the box of each MMA (unit i's box for MMA1, i - 1's for MMA2)
+    struct Geo {
+      int ms, me, nh;
+      uint32_t idesc1, idesc2;
+    };
+    auto geo = [&](const SBox& X) {
+      Geo q;
+      q.ms = band_lo(X) >> 4;
+      q.me = band_hi(X) >> 4;
+      q.nh = (X.RF + 16) >> 4;  // K steps of h in the A term
+      const uint32_t N2 = (uint32_t)((X.Mg + 15) & ~15);
+      q.idesc1 = idesc0 | ((N2 >> 3) << 17);              // A, B K-major
+      q.idesc2 = idesc0 | (1u << 15) | ((N2 >> 3) << 17);  // A MN-major
+      return q;
+    };
+    auto mma1 = [&](uint32_t i, const Geo& q) {
       const uint32_t k = i & 1u, d = tmem + 64u * k;
-      const uint32_t nb = base + kOffNode + k * 4 * kPl64;
-      const uint64_t dA = sdesc(base + kOffA + k * 2 * kPl128), dT = sdesc(nb);
+      const uint64_t dA = sdesc(base + kOffA + k * 2 * kPl128);
+      const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
 #pragma unroll 1
-      for (int m = ms; m < me; ++m)
-        mma_x3_w(d, dA + 2u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, idesc1, m > ms ? 1u : 0u);
+      for (int m = q.ms; m < q.me; ++m)
+        mma_x3_w(d, dA + 2u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, q.idesc1,
+                 m > q.ms ? 1u : 0u);
       if constexpr (kPeriodic) {
-        const uint64_t dF = sdesc(nb + 2 * kPl64);
+        const uint64_t dF = sdesc(base + kOffF + k * 2 * kPl64);
 #pragma unroll 1
-        for (int m = 0; m < nh; ++m) mma_x2_ss_w(d, dP + 2u * m, dF + 2u * m, kPl64 >> 4, idesc1, 1u);
+        for (int m = 0; m < q.nh; ++m)
+          mma_x2_ss_w(d, dP + 2u * m, dF + 2u * m, kPl64 >> 4, q.idesc1, 1u);
       }
     };
-    auto mma2 = [&](uint32_t i, bool first) {
+    auto mma2 = [&](uint32_t i, bool first, const Geo& q) {
       const uint32_t k = i & 1u;
       const uint64_t dU = sdesc_mn(base + kOffU + k * 2 * kPl128);
-      const uint64_t dT = sdesc(base + kOffNode + k * 4 * kPl64);
+      const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
 #pragma unroll 1
-      for (int m = ms; m < me; ++m)
-        mma_x3_w(tmem + 128u, dU + 128u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, idesc2,
-                 (first && m == ms) ? 0u : 1u);
+      for (int m = q.ms; m < q.me; ++m)
+        mma_x3_w(tmem + 128u, dU + 128u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, q.idesc2,
+                 (first && m == q.ms) ? 0u : 1u);
     };
     bool ok = all(!s_abort);
     uint32_t pc = 0, segc = 0;
-    long long prev = -1;  // unit of the MMA2 still to issue
-    bool prev_first = false, prev_last = false;
+    BoxCursor<kBatch> C;
+    if (u0 < u1) C.init(g, u0);
+    Geo q = geo(C.X), qp = q;  // geometry of unit i and of unit i - 1
+    bool have_prev = false, prev_first = false, prev_last = false;
     uint32_t i = 0;
     for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      const bool first = u == u0 || u % S == 0;
-      const bool last = u + 1 == u1 || (u + 1) % S == 0;
+      if (C.advance(g, u)) q = geo(C.X);
+      const long long loc = u - C.X.unit0;
+      const bool first = u == u0 || loc % C.X.S == 0;
+      const bool last = u + 1 == u1 || (loc + 1) % C.X.S == 0;
       // MMA1(i)
-      ok = all(mbar_wait(nfull(i & 1u), (i >> 1) & 1u, g.err, 43, &s_abort) &&
+      ok = all(mbar_wait(tfull(i % 3u), (i / 3u) & 1u, g.err, 43, &s_abort) &&
+               (!kPeriodic || mbar_wait(ffull(i & 1u), (i >> 1) & 1u, g.err, 43, &s_abort)) &&
                mbar_wait(afull(i & 1u), (i >> 1) & 1u, g.err, 44, &s_abort) &&
                (!first || !kPeriodic || mbar_wait(pfull, pc & 1u, g.err, 45, &s_abort)) &&
                (i < 2 || mbar_wait(d1free(i & 1u), ((i >> 1) & 1u) ^ 1u, g.err, 46, &s_abort)));
       if (!ok) break;
       if (first) ++pc;
       tc_fence_after();
-      mma1(i);
+      mma1(i, q);
       mma_commit_w(afree(i & 1u));
+      if (kPeriodic) mma_commit_w(ffree(i & 1u));
       mma_commit_w(d1full(i & 1u));
       if (last && kPeriodic) mma_commit_w(pfree);
       // MMA2(i - 1)
-      if (prev >= 0) {
+      if (have_prev) {
         const uint32_t ip = i - 1;
         ok = all(mbar_wait(ufull(ip & 1u), (ip >> 1) & 1u, g.err, 47, &s_abort) &&
                  (!prev_first || segc == 0 ||
                   mbar_wait(edone, (segc - 1) & 1u, g.err, 48, &s_abort)));
         if (!ok) break;
         tc_fence_after();
-        mma2(ip, prev_first);
+        mma2(ip, prev_first, qp);
         mma_commit_w(ufree(ip & 1u));
-        mma_commit_w(nfree(ip & 1u));
+        mma_commit_w(tfree(ip % 3u));
         if (prev_last) {
           mma_commit_w(efull);
           ++segc;
         }
       }
-      prev = u;
+      have_prev = true;
       prev_first = first;
       prev_last = last;
+      qp = q;
     }
-    if (ok && prev >= 0) {
+    if (ok && have_prev) {
       const uint32_t ip = i - 1;
       ok = all(mbar_wait(ufull(ip & 1u), (ip >> 1) & 1u, g.err, 47, &s_abort) &&
                (!prev_first || segc == 0 ||
                 mbar_wait(edone, (segc - 1) & 1u, g.err, 48, &s_abort)));
       if (ok) {
         tc_fence_after();
-        mma2(ip, prev_first);
+        mma2(ip, prev_first, qp);
         mma_commit_w(ufree(ip & 1u));
-        mma_commit_w(nfree(ip & 1u));
+        mma_commit_w(tfree(ip % 3u));
         mma_commit_w(efull);
         ++segc;
       }
@@ -305,48 +400,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- R^T and P builders (warps 8-10, 12-14)
     // R^T[(j, z)][y'] = F_s[x_j][h(y', z)]: rows z and 2R - z are equal, so a task forms one
     // 16-byte chunk (8 consecutive y') of a row z <= R and stores it into both mirror rows.
-    // The h values of a task never change; the row of F_s comes from two registers per lane
-    // (h < 32 and h >= 32; R_F <= 31, so only the first) by shuffles.
+    // The h values of a task are fixed for a box; the row of F_s comes from one register per
+    // lane (h = lane; R_F <= 31) by shuffles.
     const int bw = warp < kProdWarp ? warp - kEpiWarps : warp - kEpiWarps - 1;
     const int bt = 32 * bw + lane;
-    const int zlo = R - RF, nzh = RF + 1;
-    const int clo = (R - RF) >> 3, nc = ((R + RF) >> 3) - clo + 1;
-    const int tasks = 2 * nzh * nc;  // <= 2 x 32 x 8 = 512 < 3 x 192
-    constexpr int kMaxTasks = 3;
+    constexpr int kMaxTasks = 3;  // 2 (2 R_F + 1 rows, halved by the mirror) 8 chunks <= 576
     uint32_t hb[kMaxTasks][2];
+    int zlo = 0, nzh = 0, clo = 0, nc = 0, tasks = 0;
+    auto setup = [&](const SBox& X) {
+      zlo = X.R - X.RF;
+      nzh = X.RF + 1;
+      clo = (X.R - X.RF) >> 3;
+      nc = ((X.R + X.RF) >> 3) - clo + 1;
+      tasks = 2 * nzh * nc;
 #pragma unroll
-    for (int k = 0; k < kMaxTasks; ++k) {
-      const int t = bt + k * kBldThreads;
-      hb[k][0] = hb[k][1] = 0xffffffffu;
-      if (t < tasks) {
-        const int tt = t % (nzh * nc);
-        const int z = zlo + tt / nc, c = clo + tt % nc, dz = z - R;
+      for (int k = 0; k < kMaxTasks; ++k) {
+        const int t = bt + k * kBldThreads;
+        hb[k][0] = hb[k][1] = 0xffffffffu;
+        if (t < tasks) {
+          const int tt = t % (nzh * nc);
+          const int z = zlo + tt / nc, c = clo + tt % nc, dz = z - X.R;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int dy = 8 * c + e - R;
-          const int q = RF * RF - dy * dy - dz * dz;
-          const uint32_t h = q >= 0 ? (uint32_t)isq[q] : 0xffu;
-          hb[k][e >> 2] = (hb[k][e >> 2] & ~(0xffu << (8 * (e & 3)))) | (h << (8 * (e & 3)));
+          for (int e = 0; e < 8; ++e) {
+            const int dy = 8 * c + e - X.R;
+            const int q = X.RF * X.RF - dy * dy - dz * dz;
+            const uint32_t h = q >= 0 ? (uint32_t)isq[q] : 0xffu;
+            hb[k][e >> 2] = (hb[k][e >> 2] & ~(0xffu << (8 * (e & 3)))) | (h << (8 * (e & 3)));
+          }
         }
       }
-    }
-    auto frow = [&](long long u, int j) {
-      return g.FR + ((long long)(u % S) * kG + 2 * (u / S) + j) * kHMax;
     };
-    // F rows of the next unit, loaded a unit ahead (row x_j: lane l holds h = l)
+    BoxCursor<kBatch> C, Cn;  // the box of this unit and of the next (F rows loaded ahead)
+    if (u0 < u1) {
+      C.init(g, u0);
+      Cn.init(g, u0);
+      setup(C.X);
+    }
+    auto frow = [&](const SBox& X, long long u, int j) {
+      const long long loc = u - X.unit0;
+      return g.FR + X.fr0 + ((loc % X.S) * kG + 2 * (loc / X.S) + j) * kHMax;
+    };
     uint32_t nf0 = 0, nf1 = 0;
     if (u0 < u1) {
-      nf0 = __ldg(frow(u0, 0) + lane);
-      nf1 = __ldg(frow(u0, 1) + lane);
+      nf0 = __ldg(frow(C.X, u0, 0) + lane);
+      nf1 = __ldg(frow(C.X, u0, 1) + lane);
     }
-    uint32_t pc = 0, i = 0;
+    int abox[2] = {0, 0};  // the box each R^T buffer was last built for (zero at start)
+    if (kBatch && u0 < u1) abox[0] = abox[1] = C.b;
+    uint32_t pc = 0, i = 0, zc = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      const bool first = u == u0 || u % S == 0;
+      if (C.advance(g, u)) setup(C.X);
+      const long long loc = u - C.X.unit0;
+      const bool first = u == u0 || loc % C.X.S == 0;
       const uint32_t f0 = nf0, f1 = nf1;
       if (u + 1 < u1) {
-        nf0 = __ldg(frow(u + 1, 0) + lane);
-        nf1 = __ldg(frow(u + 1, 1) + lane);
+        Cn.advance(g, u + 1);
+        nf0 = __ldg(frow(Cn.X, u + 1, 0) + lane);
+        nf1 = __ldg(frow(Cn.X, u + 1, 1) + lane);
       }
       if (kPeriodic && first) {
         // P_j[z][h] = [h(x_j, z) = h] for the pair of u: row r = 64 j + z, one thread a row
@@ -354,8 +465,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         if (bt < 128) {
           const int j = bt >> 6, z = bt & 63;
-          const int dx = (int)(2 * (u / S) + j) - R, dz = z - R;
-          const int q = RF * RF - dx * dx - dz * dz;
+          const int dx = (int)(2 * (loc / C.X.S) + j) - C.X.R, dz = z - C.X.R;
+          const int q = C.X.RF * C.X.RF - dx * dx - dz * dz;
           const int h = q >= 0 ? (int)isq[q] : -1;
           uint8_t* row = gb + kOffP + bt * 128;
 #pragma unroll
@@ -377,6 +488,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       ok = mbar_wait(afree(i & 1u), ((i >> 1) & 1u) ^ 1u, g.err, 52, &s_abort);
       if (!ok) break;
       uint8_t* A = gb + kOffA + (i & 1u) * 2 * kPl128;
+      if (kBatch && abox[i & 1u] != C.b) {
+        // a new box in this buffer: clear what the previous box's band left, and let no
+        // builder write its chunks before every builder has finished clearing
+        for (uint32_t o = 16u * bt; o < 2 * kPl128; o += 16u * kBldThreads)
+          *reinterpret_cast<uint4*>(A + o) = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(zbar);
+        ok = mbar_wait(zbar, zc & 1u, g.err, 53, &s_abort);
+        ++zc;
+        if (!ok) break;
+        abox[i & 1u] = C.b;
+      }
 #pragma unroll
       for (int k = 0; k < kMaxTasks; ++k) {
         const int t = bt + k * kBldThreads;
@@ -403,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           lo.y = __byte_perm(v[2], v[3], 0x7632);
           lo.z = __byte_perm(v[4], v[5], 0x7632);
           lo.w = __byte_perm(v[6], v[7], 0x7632);
-          const int r = 64 * j + z, rm = 64 * j + 2 * R - z;
+          const int r = 64 * j + z, rm = 64 * j + 2 * C.X.R - z;
           const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((c & 7) ^ (r & 7)) << 4);
           *reinterpret_cast<uint4*>(A + off) = hi;
           *reinterpret_cast<uint4*>(A + off + kPl128) = lo;
@@ -424,12 +547,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quad = warp & 3, half = warp >> 2;
     const int j = quad >> 1, zr = 32 * (quad & 1) + lane;  // D1 row (j, z = zr)
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
-    const bool in_band = zr >= zs && zr < ze;
+    BoxCursor<kBatch> C;
+    if (u0 < u1) C.init(g, u0);
+    bool in_band = zr >= band_lo(C.X) && zr < band_hi(C.X);
     uint32_t i = 0, segc = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      const bool last = u + 1 == u1 || (u + 1) % S == 0;
-      const float ws = g.w[(int)(u % S)];
+      if (C.advance(g, u)) in_band = zr >= band_lo(C.X) && zr < band_hi(C.X);
+      const long long loc = u - C.X.unit0;
+      const bool last = u + 1 == u1 || (loc + 1) % C.X.S == 0;
+      const float ws = g.w[C.X.w0 + loc % C.X.S];
       ok = mbar_wait(d1full(i & 1u), (i >> 1) & 1u, g.err, 61, &s_abort);
       if (!ok) break;
       tc_fence_after();
@@ -469,11 +596,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       ok = mbar_wait(efull, segc & 1u, g.err, 63, &s_abort);
       if (!ok) break;
       tc_fence_after();
-      const long long p = u / S;
-      const int kseg = (int)blockIdx.x - owner_cta(p * S, g.units, gridDim.x);
+      const long long p = loc / C.X.S;
+      const int kseg =
+          (int)blockIdx.x - owner_cta(C.X.unit0 + p * C.X.S, g.units, gridDim.x);
       tmem_ld32(tmem + lane_off + 128u + 32u * half, v);
       float4* o = reinterpret_cast<float4*>(
-          g.part + ((p * g.maxseg + kseg) * 128 + 32 * quad + lane) * (long long)kG + 32 * half);
+          g.part + C.X.part0 + ((p * C.X.maxseg + kseg) * 128 + 32 * quad + lane) * (long long)kG +
+          32 * half);
 #pragma unroll
       for (int e = 0; e < 8; ++e)
         o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
@@ -556,46 +685,54 @@ __device__ __forceinline__ int isqrt_int(int v) {
 }
 
 // one warp per grid row (x, y), two z per lane: partials of the pair in order, + Dbar term,
-// eps on the basis sphere; FP64 sum of the row's eps over the Fermi sphere
+// eps on the basis sphere; FP64 sum of the row's eps over the Fermi sphere.  The last block
+// to finish (ticket) adds the row sums in index order into E_x (deterministic whichever
+// block is last) and resets the ticket for the next call.
 __global__ void __launch_bounds__(256)
     k_tcs_finalize(const float* part, const float* FB, int R, int RF, int S, int units, int grid,
-                   int maxseg, int periodic, double pref, float* eps, double* row_ex) {
+                   int maxseg, int periodic, double pref, float* eps, double* row_ex,
+                   unsigned* ticket, double* Ex, const int* err, int* status) {
   const int Mg = 2 * R + 1;
   const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (y >= Mg) return;  // whole warps
-  const int p = x >> 1, j = x & 1;
-  const int c0 = owner_cta((long long)p * S, units, grid);
-  const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
-  const int dx = x - R, dy = y - R;
-  const int qb = RF * RF - dx * dx - dy * dy;
-  const float* fb = (periodic && qb >= 0) ? FB + isqrt_int(qb) * kG : nullptr;
-  const float* pp = part + ((long long)p * maxseg * 128 + 64 * j + y) * kG;
-  double acc = 0.0;
+  if (y < Mg) {
+    const int p = x >> 1, j = x & 1;
+    const int c0 = owner_cta((long long)p * S, units, grid);
+    const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
+    const int dx = x - R, dy = y - R;
+    const int qb = RF * RF - dx * dx - dy * dy;
+    const float* fb = (periodic && qb >= 0) ? FB + isqrt_int(qb) * kG : nullptr;
+    const float* pp = part + ((long long)p * maxseg * 128 + 64 * j + y) * kG;
+    double acc = 0.0;
 #pragma unroll
-  for (int k2 = 0; k2 < 2; ++k2) {
-    const int z = lane + 32 * k2;
-    if (z >= Mg) continue;
-    float sum = 0.0f;
-    for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 128 * kG + z);
-    if (fb) sum += __ldg(fb + z);
-    const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
-    const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
-    eps[((long long)x * Mg + y) * Mg + z] = v;
-    if (m <= RF * RF) acc += (double)v;
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int z = lane + 32 * k2;
+      if (z >= Mg) continue;
+      float sum = 0.0f;
+      for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 128 * kG + z);
+      if (fb) sum += __ldg(fb + z);
+      const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
+      const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
+      eps[((long long)x * Mg + y) * Mg + z] = v;
+      if (m <= RF * RF) acc += (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
-}
-
-__global__ void __launch_bounds__(1024)
-    k_tcs_ex(const double* row_ex, int n, double* Ex, const int* err, int* status) {
-  __shared__ double red[1024];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += 1024) acc += row_ex[i];
-  red[threadIdx.x] = acc;
+  __shared__ bool s_last;
+  __shared__ double red[256];
+  __threadfence();
   __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
+  if (threadIdx.x == 0)
+    s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double a = 0.0;
+  for (int i = threadIdx.x; i < Mg * Mg; i += 256) a += __ldcg(row_ex + i);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
@@ -603,7 +740,73 @@ __global__ void __launch_bounds__(1024)
     Ex[0] = 0.5 * red[0];
     Ex[1] = red[0];
     if (status) *status = *err;
+    *ticket = 0u;
   }
+}
+
+// batches: one block per slab (box, x), eight warps over the rows y, two z per lane; the
+// block's FP64 sum of eps over the Fermi sphere (rows in order, then warps in order), and the
+// last block of a box (ticket) adds its slab sums in order into the box's E_x
+struct FBox {
+  int R, RF, Mg, S, maxseg, slab0;
+  long long unit0, part0, eps_off;
+  double pref;
+};
+
+__global__ void __launch_bounds__(256)
+    k_tcsb_finalize(const FBox* __restrict__ boxes, const int* __restrict__ slab_box,
+                    const float* part, const float* FB, int units, int grid, float* eps,
+                    double* slab_ex, unsigned* ticket, double* Ex) {
+  const int gx = blockIdx.x, b = slab_box[gx];
+  const FBox X = boxes[b];
+  const int x = gx - X.slab0, Mg = X.Mg, R = X.R, RF = X.RF;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = x >> 1, j = x & 1;
+  const int c0 = owner_cta(X.unit0 + (long long)p * X.S, units, grid);
+  const int nseg = owner_cta(X.unit0 + (long long)(p + 1) * X.S - 1, units, grid) - c0 + 1;
+  const int dx = x - R;
+  double wacc = 0.0;
+  for (int y = warp; y < Mg; y += 8) {
+    const int dy = y - R;
+    const int qb = RF * RF - dx * dx - dy * dy;
+    const float* fb = qb >= 0 ? FB + (long long)b * kG * kHMax + isqrt_int(qb) * kG : nullptr;
+    const float* pp = part + X.part0 + ((long long)p * X.maxseg * 128 + 64 * j + y) * kG;
+    double acc = 0.0;
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int z = lane + 32 * k2;
+      if (z >= Mg) continue;
+      float sum = 0.0f;
+      for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 128 * kG + z);
+      if (fb) sum += __ldg(fb + z);
+      const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
+      const float v = m <= R * R ? (float)(-X.pref * (double)sum) : 0.0f;
+      eps[X.eps_off + ((long long)x * Mg + y) * Mg + z] = v;
+      if (m <= RF * RF) acc += (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    wacc += acc;
+  }
+  __shared__ double s_w[8];
+  __shared__ bool s_last;
+  if (lane == 0) s_w[warp] = wacc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += s_w[k];
+    slab_ex[gx] = t;
+    __threadfence();
+    s_last = atomicAdd(ticket + b, 1u) == (unsigned)(Mg - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int k = 0; k < Mg; ++k) tot += __ldcg(slab_ex + X.slab0 + k);
+  Ex[2 * b] = 0.5 * tot;
+  Ex[2 * b + 1] = tot;
+  ticket[b] = 0u;
 }
 
 int sm_count() {
@@ -617,6 +820,30 @@ int sm_count() {
   return n;
 }
 
+cc_status set_smem_attrs() {
+  static bool done = false;
+  if (done) return CC_OK;
+  CC_CUDA(cudaFuncSetAttribute(k_tcs<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemBytes));
+  CC_CUDA(cudaFuncSetAttribute(k_tcs<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemBytes));
+  CC_CUDA(cudaFuncSetAttribute(k_tcs<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemBytes));
+  done = true;
+  return CC_OK;
+}
+
+// the largest number of CTAs that one slab pair's units are spread over
+int max_segments(long long unit0, int pairs, int S, int units, int grid) {
+  int m = 1;
+  for (int p = 0; p < pairs; ++p) {
+    const int c0 = owner_cta(unit0 + (long long)p * S, units, grid);
+    const int c1 = owner_cta(unit0 + (long long)(p + 1) * S - 1, units, grid);
+    m = std::max(m, c1 - c0 + 1);
+  }
+  return m;
+}
+
 }  // namespace
 
 struct TcSmallWs {
@@ -628,6 +855,7 @@ struct TcSmallWs {
   float* part = nullptr;
   double* row_ex = nullptr;
   float* w32 = nullptr;
+  unsigned* ticket = nullptr;
   alignas(64) unsigned char map_th[128], map_tl[128], map_fh[128], map_fl[128];
   std::vector<void*> allocs;
 };
@@ -644,16 +872,13 @@ void tc_small_free(void* p) {
 cc_status tc_small_alloc(cc_tables t, void** out) {
   *out = nullptr;
   if (!tc_small_supported(t)) return CC_OK;
+  CC_TRY(set_smem_attrs());
   TcSmallWs* w = new (std::nothrow) TcSmallWs();
   if (!w) return CC_ERR_ALLOC;
   const int S = t->S_eff, pairs = (t->Mg + 1) / 2;
   w->units = pairs * S;
   w->grid = std::min(sm_count(), w->units);
-  for (int p = 0; p < pairs; ++p) {
-    const int c0 = owner_cta((long long)p * S, w->units, w->grid);
-    const int c1 = owner_cta((long long)(p + 1) * S - 1, w->units, w->grid);
-    w->maxseg = std::max(w->maxseg, c1 - c0 + 1);
-  }
+  w->maxseg = max_segments(0, pairs, S, w->units, w->grid);
   auto alloc = [&](void** p, size_t bytes) -> cc_status {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -673,7 +898,8 @@ cc_status tc_small_alloc(cc_tables t, void** out) {
       (st = alloc((void**)&w->FB, sizeof(float) * kG * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->part, sizeof(float) * 128 * kG * pairs * w->maxseg)) != CC_OK ||
       (st = alloc((void**)&w->row_ex, sizeof(double) * kG * kG)) != CC_OK ||
-      (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK) {
+      (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK ||
+      (st = alloc((void**)&w->ticket, sizeof(unsigned))) != CC_OK) {
     tc_small_free(w);
     return st;
   }
@@ -692,6 +918,7 @@ cc_status tc_small_alloc(cc_tables t, void** out) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpy(w->w32, w32.data(), sizeof(float) * S, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(w->ticket, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     set_last_error("small-grid tensor-core planes", e);
     tc_small_free(w);
@@ -716,38 +943,181 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
     w->RF_built = R_F;
   }
   Args a{};
-  a.R = R;
-  a.R_F = R_F;
-  a.Mg = Mg;
-  a.S = S;
-  a.periodic = periodic;
+  a.boxes = nullptr;
+  a.b0 = SBox{R, R_F, Mg, S, 0, 0, 0, 0, w->maxseg, 0};
+  a.nbox = 1;
   a.units = w->units;
-  a.maxseg = w->maxseg;
+  a.rf_max = R_F;
   a.FR = w->FR;
   a.w = w->w32;
   a.part = w->part;
   a.err = err;
   a.stall_test = stall_test;
-  static bool attr = false;
-  if (!attr) {
-    CC_CUDA(cudaFuncSetAttribute(k_tcs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes));
-    CC_CUDA(cudaFuncSetAttribute(k_tcs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes));
-    attr = true;
-  }
   const CUtensorMap& th = *reinterpret_cast<const CUtensorMap*>(w->map_th);
   const CUtensorMap& tl = *reinterpret_cast<const CUtensorMap*>(w->map_tl);
   const CUtensorMap& fh = *reinterpret_cast<const CUtensorMap*>(w->map_fh);
   const CUtensorMap& fl = *reinterpret_cast<const CUtensorMap*>(w->map_fl);
   if (periodic)
-    k_tcs<true><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+    k_tcs<true, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   else
-    k_tcs<false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
-  k_tcs_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, w->FB, R, R_F, S, w->units,
-                                                         w->grid, w->maxseg, periodic, t->pref,
-                                                         eps, w->row_ex);
-  k_tcs_ex<<<1, 1024, 0, st>>>(w->row_ex, Mg * Mg, Ex, err, err + 1);
+    k_tcs<false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  k_tcs_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
+      w->part, w->FB, R, R_F, S, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
+      w->row_ex, w->ticket, Ex, err, err + 1);
+  CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+// ---------------------------------------------------------------- batches of boxes
+struct TcSmallBatch {
+  int nbox = 0, units = 0, grid = 0, rf_max = 0, slabs = 0;
+  SBox* boxes = nullptr;
+  FBox* fboxes = nullptr;
+  int* slab_box = nullptr;
+  uint32_t* FR = nullptr;
+  void* F[2] = {nullptr, nullptr};
+  void* T[2] = {nullptr, nullptr};
+  float* FB = nullptr;
+  float* part = nullptr;
+  double* slab_ex = nullptr;
+  float* w = nullptr;
+  unsigned* ticket = nullptr;
+  alignas(64) unsigned char map_th[128], map_tl[128], map_fh[128], map_fl[128];
+  std::vector<void*> allocs;
+};
+
+bool tc_small_batch_supported(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F) {
+  for (size_t b = 0; b < tabs.size(); ++b)
+    if (tabs[b]->Mg > kG || R_F[b] > 31 || tabs[b]->p.kernel != CC_KERNEL_PERIODIC) return false;
+  return !tabs.empty();
+}
+
+void tc_small_batch_free(void* p) {
+  TcSmallBatch* m = reinterpret_cast<TcSmallBatch*>(p);
+  if (!m) return;
+  for (void* a : m->allocs) cudaFree(a);
+  delete m;
+}
+
+cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
+                                const std::vector<long long>& eps_off, void** out) {
+  *out = nullptr;
+  if (!tc_small_batch_supported(tabs, R_F)) return CC_ERR_NOTSUPP;
+  CC_TRY(set_smem_attrs());
+  TcSmallBatch* m = new (std::nothrow) TcSmallBatch();
+  if (!m) return CC_ERR_ALLOC;
+  const int nb = (int)tabs.size();
+  m->nbox = nb;
+  std::vector<SBox> bx(nb);
+  std::vector<FBox> fb(nb);
+  std::vector<int> slab_box;
+  long long units = 0, nodes = 0;
+  for (int b = 0; b < nb; ++b) {
+    const cc_tables t = tabs[b];
+    const int pairs = (t->Mg + 1) / 2;
+    bx[b] = SBox{t->p.R, R_F[b], t->Mg, t->S_eff, units, nodes * kG * kG, nodes, 0, 1, 0};
+    units += (long long)pairs * t->S_eff;
+    nodes += t->S_eff;
+    m->rf_max = std::max(m->rf_max, R_F[b]);
+  }
+  m->units = (int)units;
+  m->grid = (int)std::min<long long>(sm_count(), units);
+  long long part = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int pairs = (bx[b].Mg + 1) / 2;
+    bx[b].maxseg = max_segments(bx[b].unit0, pairs, bx[b].S, m->units, m->grid);
+    bx[b].part0 = part;
+    part += (long long)pairs * bx[b].maxseg * 128 * kG;
+    fb[b] = FBox{bx[b].R, bx[b].RF, bx[b].Mg, bx[b].S, bx[b].maxseg, m->slabs, bx[b].unit0,
+                 bx[b].part0, eps_off[b], tabs[b]->pref};
+    for (int x = 0; x < bx[b].Mg; ++x) slab_box.push_back(b);
+    m->slabs += bx[b].Mg;
+  }
+  auto alloc = [&](void** p, size_t bytes) -> cc_status {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      set_last_error("cudaMalloc(small-grid tensor-core batch)", e);
+      return CC_ERR_ALLOC;
+    }
+    m->allocs.push_back(*p);
+    return CC_OK;
+  };
+  const size_t plane = sizeof(__nv_bfloat16) * (size_t)nodes * kG * kG;
+  cc_status st = CC_OK;
+  if ((st = alloc((void**)&m->boxes, sizeof(SBox) * nb)) != CC_OK ||
+      (st = alloc((void**)&m->fboxes, sizeof(FBox) * nb)) != CC_OK ||
+      (st = alloc((void**)&m->slab_box, sizeof(int) * m->slabs)) != CC_OK ||
+      (st = alloc((void**)&m->FR, sizeof(uint32_t) * (size_t)nodes * kG * kHMax)) != CC_OK ||
+      (st = alloc(&m->F[0], plane)) != CC_OK || (st = alloc(&m->F[1], plane)) != CC_OK ||
+      (st = alloc(&m->T[0], plane)) != CC_OK || (st = alloc(&m->T[1], plane)) != CC_OK ||
+      (st = alloc((void**)&m->FB, sizeof(float) * nb * kG * kHMax)) != CC_OK ||
+      (st = alloc((void**)&m->part, sizeof(float) * part)) != CC_OK ||
+      (st = alloc((void**)&m->slab_ex, sizeof(double) * m->slabs)) != CC_OK ||
+      (st = alloc((void**)&m->w, sizeof(float) * nodes)) != CC_OK ||
+      (st = alloc((void**)&m->ticket, sizeof(unsigned) * nb)) != CC_OK) {
+    tc_small_batch_free(m);
+    return st;
+  }
+  const long long rows = nodes * kG;
+  if ((st = tc_make_map_bf16(m->map_th, m->T[0], rows, kG, kG)) != CC_OK ||
+      (st = tc_make_map_bf16(m->map_tl, m->T[1], rows, kG, kG)) != CC_OK ||
+      (st = tc_make_map_bf16(m->map_fh, m->F[0], rows, kG, kG)) != CC_OK ||
+      (st = tc_make_map_bf16(m->map_fl, m->F[1], rows, kG, kG)) != CC_OK) {
+    tc_small_batch_free(m);
+    return st;
+  }
+  std::vector<float> w(nodes);
+  for (int b = 0; b < nb; ++b) {
+    const cc_tables t = tabs[b];
+    const long long o = bx[b].fr0;
+    k_tcs_prep<<<(t->S_eff * kG + 127) / 128, 128>>>(t->d.Tm64, t->S_eff, t->Mg, t->p.R, R_F[b], 1,
+                                                      m->FR + o, (__nv_bfloat16*)m->F[0] + o,
+                                                      (__nv_bfloat16*)m->F[1] + o);
+    k_tcs_tplanes<<<128, 256>>>(t->d.Tm64, t->S_eff, t->Mg, (__nv_bfloat16*)m->T[0] + o,
+                                (__nv_bfloat16*)m->T[1] + o);
+    k_tcs_dbar<<<1, kG>>>(t->d.Dbar64, t->Mg, t->p.R, R_F[b], m->FB + (long long)b * kG * kHMax);
+    for (int i = 0; i < t->S_eff; ++i) w[bx[b].w0 + i] = (float)t->w[t->kept_idx[i]];
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->boxes, bx.data(), sizeof(SBox) * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->fboxes, fb.data(), sizeof(FBox) * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->slab_box, slab_box.data(), sizeof(int) * m->slabs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->w, w.data(), sizeof(float) * nodes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->ticket, 0, sizeof(unsigned) * nb);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_last_error("small-grid tensor-core batch planes", e);
+    tc_small_batch_free(m);
+    return CC_ERR_CUDA;
+  }
+  *out = m;
+  return CC_OK;
+}
+
+cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStream_t st) {
+  TcSmallBatch* m = reinterpret_cast<TcSmallBatch*>(p);
+  if (!m) return CC_ERR_NOTSUPP;
+  Args a{};
+  a.boxes = m->boxes;
+  a.nbox = m->nbox;
+  a.units = m->units;
+  a.rf_max = m->rf_max;
+  a.FR = m->FR;
+  a.w = m->w;
+  a.part = m->part;
+  a.err = err;
+  a.stall_test = 0;
+  const CUtensorMap& th = *reinterpret_cast<const CUtensorMap*>(m->map_th);
+  const CUtensorMap& tl = *reinterpret_cast<const CUtensorMap*>(m->map_tl);
+  const CUtensorMap& fh = *reinterpret_cast<const CUtensorMap*>(m->map_fh);
+  const CUtensorMap& fl = *reinterpret_cast<const CUtensorMap*>(m->map_fl);
+  k_tcs<true, true><<<m->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  k_tcsb_finalize<<<m->slabs, 256, 0, st>>>(m->fboxes, m->slab_box, m->part, m->FB, m->units,
+                                            m->grid, eps, m->slab_ex, m->ticket, Ex);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

@@ -878,7 +878,8 @@ struct MxBatchImpl {
   std::vector<long long*> t123[3], t4;
   std::vector<int> n123, n4;
   std::vector<void*> allocs;
-  void* slab = nullptr;  // the batch through the fused slab kernel (tcslab.cu)
+  void* slab = nullptr;   // the batch through the fused slab kernel (tcslab.cu)
+  void* small = nullptr;  // the batch through the small-grid kernel (tcsmall.cu)
 };
 
 __global__ void k_mxb_occ(int nbox, const int* R, const int* RF, __nv_bfloat16* O,
@@ -954,6 +955,7 @@ void mixed_batch_free(void* p) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return;
   tc_slab_batch_free(m->slab);
+  tc_small_batch_free(m->small);
   for (void* q : m->allocs) cudaFree(q);
   delete m;
 }
@@ -1066,6 +1068,9 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
   if (s == CC_OK)
     s = tc_slab_batch_create(tabs, R_F, eps_off, P.TT[0], P.TT[1], rows_x1, off_x1, Np,
                              &m->slab);
+  // and through the small-grid kernel (every grid side <= 64)
+  if (s == CC_OK && tc_small_batch_supported(tabs, R_F))
+    s = tc_small_batch_create(tabs, R_F, eps_off, &m->small);
   if (s != CC_OK) {
     mixed_batch_free(m);
     return s;
@@ -1077,7 +1082,11 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
 cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return CC_ERR_NOTSUPP;
-  if (m->slab && g_mixed_variant != 1) return tc_slab_batch_run(m->slab, m->err, eps, Ex, st);
+  const int variant = __atomic_load_n(&g_mixed_variant, __ATOMIC_ACQUIRE);
+  if (m->small && (variant == 0 || variant == 3))
+    return tc_small_batch_run(m->small, m->err, eps, Ex, st);
+  if (variant == 3) return CC_ERR_NOTSUPP;
+  if (m->slab && variant != 1) return tc_slab_batch_run(m->slab, m->err, eps, Ex, st);
   constexpr int Np = 64;
   using E = __nv_bfloat16;
   const long long NN = (long long)Np * Np;
