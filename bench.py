@@ -367,13 +367,20 @@ MP_CONFIGS = {"precision": (31, 40.0, 96, 20), "large": (63, 60.0, 128, 40)}
 
 
 def tc_slab_executed_flop(R, R_F, Mg, S_eff, periodic=True):
-    """Flop the tensor-core slab kernel issues for one exchange call: per (slab pair, node)
-    unit and slab, MMA1 (3 x 128 x B x B), MMA2 (3 x 128 x B x N2) and, when the A term runs
-    on the tensor cores (periodic, band B <= 96), 2 x 128 x B x 16 nh; B = the band rounded
-    out to 16-column pieces, N2 = the grid side rounded up to 16, nh = ceil((R_F + 1) / 16)."""
-    B = ((R + R_F + 16) & ~15) - ((R - R_F) & ~15)
+    """Flop the tensor-core exchange issues for one call.  Grid sides up to 64 (the small-grid
+    kernel, two slabs per 128-row MMA): per (slab pair, node) unit, MMA1 and MMA2 of
+    3 x 2 x 128 x N2 x 16 per K step over the band, plus the A term 2 x 2 x 128 x N2 x 16 per
+    h step (periodic).  Larger grids (the 128-row slab kernel): per unit and slab, MMA1
+    (3 x 128 x B x B), MMA2 (3 x 128 x B x N2) and, when the A term runs on the tensor cores
+    (periodic, band B <= 96), 2 x 128 x B x 16 nh.  B = the band rounded out to 16-column
+    pieces, N2 = the grid side rounded up to 16, nh = ceil((R_F + 1) / 16)."""
     N2 = (Mg + 15) & ~15
     nh = (R_F + 16) >> 4
+    if Mg <= 64:
+        steps = (min(64, (R + R_F + 16) & ~15) - ((R - R_F) & ~15)) // 16
+        per_unit = 2 * 128 * N2 * 16 * (6 * steps + (2 * nh if periodic else 0))
+        return per_unit * ((Mg + 1) // 2) * S_eff
+    B = ((R + R_F + 16) & ~15) - ((R - R_F) & ~15)
     per_slab = 2 * 128 * (3 * B * B + 3 * B * N2 + (2 * B * 16 * nh if periodic and B <= 96 else 0))
     return per_slab * 2 * ((Mg + 1) // 2) * S_eff
 
@@ -408,6 +415,8 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
         Ex = torch.empty(2, dtype=torch.float64, device=dev)
         p = "fp32" if prec == "fp32_dense" else prec
         cc.lib().cc_set_simt_variant(1 if prec == "fp32_dense" else 0)
+        if prec == "fp32_dense":   # the chain at its autotuned tiles
+            out["fp32_dense_tiles"] = cc.autotune_gemm(t, R_F, precision="fp32", reps=2)
         try:
             n = max(2, reps // 4) if prec == "fp32_dense" else reps
             for _ in range(2):
@@ -482,6 +491,7 @@ def mixed_vs_fp32(mp, large, batched_sec, general):
     if batched_sec:
         out["batch256_ms"] = {k: _sig(batched_sec[k]["ms_per_batch"]) for k in ("fp32", "bf16x3", "fp64")
                               if k in batched_sec}
+        out["batch256_bf16x3_frac_exec"] = _sig(batched_sec["bf16x3"].get("executed_frac_of_peak"), 3)
     if large:
         out["cfg5_1e9_lookups"] = {k: {"ms": _sig(v["ms"]), "hbm_frac": _sig(v["hbm_frac"], 3)}
                                    for k, v in large.items() if isinstance(v, dict)}
@@ -508,7 +518,7 @@ def batched(reps=10):
     for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64), ("bf16x3", torch.float32)):
         eps = torch.empty(int(B.offsets[-1]), dtype=dt, device=dev)
         Ex = torch.empty((B.nbox, 2), dtype=torch.float64, device=dev)
-        choice = B.tune(eps, Ex, reps=3) if prec != "bf16x3" else None
+        choice = B.tune(eps, Ex, reps=3, precision=prec)
         B.exchange(eps, Ex, precision=prec)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -523,6 +533,19 @@ def batched(reps=10):
                      "pair_evals_per_s": pairs / (ms * 1e-3), "tuned": choice,
                      "work_items": B.n_items}
     out["pair_evals_per_batch"] = pairs
+    peak, peak_kind = _bf16_peak()
+    infos = [cc.build_tables("periodic", R=b["R"], L=b["L"], S=b["S"]) for b in boxes]
+    ex = sum(tc_slab_executed_flop(b["R"], b["R_F"], 2 * b["R"] + 1, t.info["S_eff"])
+             for b, t in zip(boxes, infos))
+    useful = sum(6.0 * (2 * b["R"] + 1) ** 4 * t.info["S_eff"] for b, t in zip(boxes, infos))
+    for t in infos:
+        t.free()
+    ms = out["bf16x3"]["ms_per_batch"]
+    out["bf16x3"]["executed_tflops"] = ex / (ms * 1e-3) / 1e12
+    out["bf16x3"]["useful_tflops"] = useful / (ms * 1e-3) / 1e12
+    out["bf16x3"]["executed_frac_of_peak"] = out["bf16x3"]["executed_tflops"] / peak
+    out["bf16x3"]["useful_frac_of_peak"] = out["bf16x3"]["useful_tflops"] / peak
+    out["bf16x3"]["kernel"] = "small-grid tensor-core kernel, every box in one launch"
     B.free()
     return out
 

@@ -281,12 +281,26 @@ cc_status cc_set_mixed_variant(int variant);
  * grids always take the fused per-node kernel.  CC_ERR_ARG for any other value. */
 cc_status cc_set_simt_variant(int variant);
 
-/* Tile shapes of the SIMT mode products (plain FP32 / FP64 exchange path), chosen by the
- * project's autotuner: small_tile for the Mg x Mg batched products, large_tile for the
- * products with an Mg^2-long side, each 0 = 64x64, 1 = 32x32, 2 = 64x32 outputs per CTA;
- * threshold = grid side up to which 32x32 tiles are always used (< 0 keeps it).
- * Process-wide setting; not part of the paper (a tuning knob of this implementation). */
+/* Tile shapes of the SIMT mode products of the dense GEMM chain (plain FP32 / FP64 exchange
+ * path where it takes the chain): small_tile for the Mg x Mg batched products, large_tile
+ * for the products with an Mg^2-long side, each 0 = 64x64, 1 = 32x32, 2 = 64x32 outputs per
+ * CTA; threshold = grid side up to which 32x32 tiles are used (< 0 keeps it).  Process-wide
+ * default; a choice measured by cc_autotune_gemm for a grid side takes precedence.  Not part
+ * of the paper (a tuning knob of this implementation). */
 cc_status cc_set_gemm_tiles(int precision, int small_tile, int large_tile, int threshold);
+
+/* Autotuner of those tiles (not part of the paper): runs the dense chain of the handle's mode
+ * products (FP32 or FP64, Fermi radius R_F) with each of the 9 (small, large) tile pairs,
+ * `reps` timed calls each (CUDA events on `stream`, median), and keeps the fastest pair for
+ * this grid side and precision, process-wide.  choice_host[2] (or NULL) receives it, *ms_host
+ * (or NULL) its time.  Synchronous; allocates a scratch output.  CC_ERR_ARG / CC_ERR_RANGE
+ * for bad arguments. */
+cc_status cc_autotune_gemm(cc_tables t, int precision, int R_F, int reps, int* choice_host,
+                           float* ms_host, void* stream);
+
+/* The tile pair cc_autotune_gemm measured for a grid side Mg (0 <= Mg < 256) and precision,
+ * or -1, -1 when none has been measured in this process. */
+cc_status cc_gemm_tiles_tuned(int precision, int Mg, int* small_tile, int* large_tile);
 
 /* ---- batched engine: many independent boxes in one persistent, graph-captured launch.
  * Box i has its own cutoff, side, node count and mesh (p, any kernel; defaults as in
@@ -312,10 +326,12 @@ cc_status cc_batch_info(cc_batch b, int* nbox, long long* eps_offsets_host, int*
 /* Exchange sums of all boxes: eps_dev (double for CC_PREC_FP64, float for CC_PREC_FP32
  * and CC_PREC_BF16X3) holds every box's grid at its offset, Ex_dev[2 i], Ex_dev[2 i + 1] =
  * E_x^sigma and total of box i.  Stream ordered; calls on one batch must not overlap.
- * CC_PREC_BF16X3 (periodic boxes only) runs the tensor-core chain for all boxes at once,
- * a few launches per round of 4 nodes per box, all in the captured graph; its first call
- * builds the bf16 planes and buffers (synchronous, allocates), later calls allocate
- * nothing. */
+ * CC_PREC_BF16X3 (periodic boxes only) runs every box through one launch of the
+ * small-grid tensor-core kernel (two slabs per 128-row MMA; work units (box, slab pair,
+ * node) cut among one CTA per SM) and one finalising launch, both in the captured graph
+ * (cc_set_mixed_variant selects the 128-row slab kernel or the step chain instead); its
+ * first call builds the bf16 planes and buffers (synchronous, allocates), later calls
+ * allocate nothing. */
 cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex_dev,
                             void* stream);
 
@@ -324,10 +340,14 @@ cc_status cc_batch_exchange(cc_batch b, int precision, void* eps_dev, double* Ex
  * group), in proportion to each box's cost.  Drops captured graphs. */
 cc_status cc_batch_set_plan(cc_batch b, int ctas_per_sm, int oversub);
 
-/* Autotuner: times every launch shape (CTAs per SM in {2, 4, 8}, oversubscription in
- * {1, 2, 4}) with CUDA events, median of `reps` replays, keeps the fastest.
- * choice_host[2] receives it, *ms_host its time.  Writes eps_dev / Ex_dev (valid sums)
- * while timing.  Synchronous. */
+/* Autotuner.  CC_PREC_FP32 / CC_PREC_FP64 (the SIMT engine): times every launch shape (CTAs
+ * per SM in {2, 4, 8}, oversubscription in {1, 2, 4}) and keeps the fastest; choice_host[2]
+ * = (CTAs per SM, oversubscription).  CC_PREC_BF16X3 (the tensor-core engine): times every
+ * work decomposition, box order (0 as given, 1 by decreasing cost) x cut of the unit
+ * sequence among the CTAs (0 equal unit counts, 1 equal estimated cost), and keeps the
+ * fastest; choice_host[2] = (order, cut).  CUDA events, median of `reps` runs each;
+ * *ms_host receives the best time.  Writes eps_dev / Ex_dev (valid sums) while timing and
+ * drops the batch's captured graphs.  Synchronous. */
 cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, double* Ex_dev, int reps,
                         int* choice_host, float* ms_host, void* stream);
 

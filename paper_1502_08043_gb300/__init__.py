@@ -80,6 +80,8 @@ SIGNATURES = {
     "cc_pair_matrix": (_I, [_P, _I64, _I64, _I, _I, _P, _P]),
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
     "cc_set_gemm_tiles": (_I, [_I, _I, _I, _I]),
+    "cc_autotune_gemm": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "cc_gemm_tiles_tuned": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "cc_mixed_status": (_I, [_P, _P, _I]),
     "cc_exchange_sums_noalloc": (_I, [_P, _I, _P, _P, _P]),
     "cc_test_stall_next_mixed": (_I, []),
@@ -340,6 +342,29 @@ def mixed_status(tables: Tables, clear=True) -> int:
     return code.value
 
 
+TILES = {0: "64x64", 1: "32x32", 2: "64x32"}
+
+
+def autotune_gemm(tables: Tables, R_F, precision="fp32", reps=3, stream=None):
+    """cc_autotune_gemm: time the dense SIMT chain with every tile pair, keep the fastest
+    for this grid side and precision; returns {"small": .., "large": .., "ms": ..}."""
+    choice = np.zeros(2, dtype=np.int32)
+    ms = ctypes.c_float(0.0)
+    st = _stream(stream)
+    _check("cc_autotune_gemm", lib().cc_autotune_gemm(
+        tables.handle, PRECISIONS[precision], int(R_F), int(reps), choice.ctypes.data,
+        ctypes.byref(ms), st))
+    return {"small": TILES[int(choice[0])], "large": TILES[int(choice[1])], "ms": ms.value}
+
+
+def gemm_tiles_tuned(precision, Mg):
+    """The measured tile pair for a grid side (cc_gemm_tiles_tuned), or None."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check("cc_gemm_tiles_tuned", lib().cc_gemm_tiles_tuned(PRECISIONS[precision], int(Mg),
+                                                            ctypes.byref(a), ctypes.byref(b)))
+    return None if a.value < 0 else {"small": TILES[a.value], "large": TILES[b.value]}
+
+
 def set_gemm_tiles(precision, small_tile, large_tile, threshold=-1):
     _check("cc_set_gemm_tiles", lib().cc_set_gemm_tiles(PRECISIONS[precision], small_tile,
                                                         large_tile, threshold))
@@ -399,12 +424,19 @@ class Batch:
     def set_plan(self, ctas_per_sm=4, oversub=2):
         _check("cc_batch_set_plan", lib().cc_batch_set_plan(self.handle, ctas_per_sm, oversub))
 
-    def tune(self, eps, Ex, reps=5, stream=None):
+    def tune(self, eps, Ex, reps=5, precision=None, stream=None):
+        """cc_batch_tune.  SIMT engine (FP32 / FP64 by the dtype of eps): launch shape;
+        precision="bf16x3": the tensor-core engine's work decomposition."""
+        prec = PRECISIONS[precision] if precision else _prec_of(eps)
         choice = np.zeros(2, dtype=np.int32)
         ms = ctypes.c_float()
         _check("cc_batch_tune", lib().cc_batch_tune(
-            self.handle, _prec_of(eps), _ptr(eps), _ptr(Ex), int(reps), choice.ctypes.data,
+            self.handle, prec, _ptr(eps), _ptr(Ex), int(reps), choice.ctypes.data,
             ctypes.byref(ms), _stream(stream, eps)))
+        if prec == PRECISIONS["bf16x3"]:
+            return {"order": ["as given", "by decreasing cost"][int(choice[0])],
+                    "cut": ["equal units", "equal estimated cost"][int(choice[1])],
+                    "ms": ms.value}
         n = ctypes.c_int()
         items = ctypes.c_int()
         lib().cc_batch_info(self.handle, ctypes.byref(n), None, ctypes.byref(items), None)

@@ -352,6 +352,16 @@ extern "C" cc_status cc_batch_tune(cc_batch b, int precision, void* eps_dev, dou
                                    int reps, int* choice_host, float* ms_host, void* stream) {
   if (!b || !eps_dev || !Ex_dev || reps < 1) return CC_ERR_ARG;
   cudaStream_t st = as_stream(stream);
+  if (precision == CC_PREC_BF16X3) {
+    // the tensor-core form: order of the boxes and cut of the unit sequence among the CTAs
+    if (!b->mixed) CC_TRY(cc_batch_exchange(b, precision, eps_dev, Ex_dev, stream));
+    CC_CUDA(cudaStreamSynchronize(st));
+    batch_drop_graphs(b);  // captured launches hold the old plan's arguments
+    CC_TRY(mixed_batch_tune(b->mixed, (float*)eps_dev, Ex_dev, reps, choice_host, ms_host, st));
+    batch_drop_graphs(b);
+    return CC_OK;
+  }
+  if (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) return CC_ERR_NOTSUPP;
   const int cps[] = {2, 4, 8};
   const int ovs[] = {1, 2, 4};
   float best = 1e30f;

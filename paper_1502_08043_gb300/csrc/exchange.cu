@@ -19,6 +19,9 @@
 // Then eps = -pref E on the basis sphere, E_x^sigma = 1/2 sum_{k in F} eps(k) in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace cc {
@@ -264,14 +267,20 @@ void workspace_free(cc_tables t) {
   w.part = nullptr;
 }
 
-// ---------------------------------------------------------------- autotuned tile choice
-// Tile per GEMM class, by grid side: 32x32 tiles for Mg <= 40, 64x64 above.  The
-// autotuner (cc_autotune_gemm) replaces these defaults with measured choices.
+// ---------------------------------------------------------------- tile choice
+// Tile per GEMM class: a choice measured by cc_autotune_gemm for this (grid side,
+// precision) when there is one; otherwise the process-wide setting (cc_set_gemm_tiles):
+// 32x32 tiles for grid sides up to the threshold (40), above it 32x32 for the Mg x Mg
+// products and 64x64 for the products with an Mg^2-long side.
 static int g_tile_small[2] = {kTile32, kTile32};   // [fp32, fp64] the Mg x Mg products
 static int g_tile_large[2] = {kTile64, kTile64};   // the Mg^2-long products
 static int g_tile_threshold = 40;
+// measured choices: [precision][grid side] -> small_tile + 3 * large_tile + 1 (0 = none)
+static unsigned char g_tuned[2][256] = {};
 
 static int tile_for(int Mg, bool long_dim, bool fp64) {
+  const int tc = (Mg >= 0 && Mg < 256) ? __atomic_load_n(&g_tuned[fp64][Mg], __ATOMIC_ACQUIRE) : 0;
+  if (tc) return long_dim ? (tc - 1) / 3 : (tc - 1) % 3;
   if (Mg <= g_tile_threshold) return kTile32;
   return long_dim ? g_tile_large[fp64] : g_tile_small[fp64];
 }
@@ -379,6 +388,82 @@ extern "C" cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void*
 extern "C" cc_status cc_set_simt_variant(int variant) {
   if (variant < 0 || variant > 1) return CC_ERR_ARG;
   __atomic_store_n(&g_simt_variant, variant, __ATOMIC_RELEASE);
+  return CC_OK;
+}
+
+// Autotuner of the SIMT GEMM tiles: times the dense chain of mode products of this handle
+// with every (small, large) tile pair and keeps the fastest for this grid side and precision.
+extern "C" cc_status cc_autotune_gemm(cc_tables t, int precision, int R_F, int reps,
+                                      int* choice_host, float* ms_host, void* stream) {
+  if (!t || (precision != CC_PREC_FP32 && precision != CC_PREC_FP64) || reps < 1) return CC_ERR_ARG;
+  if (R_F < 1 || R_F > t->p.R) return CC_ERR_RANGE;
+  if (t->Mg >= 256) return CC_ERR_RANGE;
+  cudaStream_t st = as_stream(stream);
+  const bool f64 = precision == CC_PREC_FP64;
+  const size_t G3 = (size_t)t->Mg * t->Mg * t->Mg;
+  void* eps = nullptr;
+  double* Ex = nullptr;
+  if (cudaMalloc(&eps, G3 * (f64 ? 8 : 4)) != cudaSuccess ||
+      cudaMalloc((void**)&Ex, 2 * sizeof(double)) != cudaSuccess) {
+    cudaFree(eps);
+    return CC_ERR_ALLOC;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = -1.0f;
+  int bs = 0, bl = 0;
+  cc_status s = CC_OK;
+  for (int ts = 0; ts < 3 && s == CC_OK; ++ts)
+    for (int tl = 0; tl < 3 && s == CC_OK; ++tl) {
+      __atomic_store_n(&g_tuned[f64][t->Mg], (unsigned char)(ts + 3 * tl + 1), __ATOMIC_RELEASE);
+      auto run = [&]() {
+        return f64 ? exchange_simt<double>(t, R_F, (double*)eps, Ex, st)
+                   : exchange_simt<float>(t, R_F, (float*)eps, Ex, st);
+      };
+      s = run();  // warm-up
+      if (s != CC_OK) break;
+      std::vector<float> ms(reps);
+      for (int r = 0; r < reps && s == CC_OK; ++r) {
+        cudaEventRecord(e0, st);
+        s = run();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = CC_ERR_CUDA;
+        cudaEventElapsedTime(&ms[r], e0, e1);
+      }
+      if (s != CC_OK) break;
+      std::sort(ms.begin(), ms.end());
+      const float med = ms[reps / 2];
+      if (best < 0.0f || med < best) {
+        best = med;
+        bs = ts;
+        bl = tl;
+      }
+    }
+  __atomic_store_n(&g_tuned[f64][t->Mg], (unsigned char)(s == CC_OK ? bs + 3 * bl + 1 : 0),
+                   __ATOMIC_RELEASE);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(eps);
+  cudaFree(Ex);
+  if (s != CC_OK) return s;
+  if (choice_host) {
+    choice_host[0] = bs;
+    choice_host[1] = bl;
+  }
+  if (ms_host) *ms_host = best;
+  return CC_OK;
+}
+
+// The measured tile choice for a grid side and precision: small_tile, large_tile, or -1, -1
+// when none has been measured in this process.
+extern "C" cc_status cc_gemm_tiles_tuned(int precision, int Mg, int* small_tile, int* large_tile) {
+  if ((precision != CC_PREC_FP32 && precision != CC_PREC_FP64) || !small_tile || !large_tile)
+    return CC_ERR_ARG;
+  if (Mg < 0 || Mg >= 256) return CC_ERR_RANGE;
+  const int tc = __atomic_load_n(&g_tuned[precision == CC_PREC_FP64][Mg], __ATOMIC_ACQUIRE);
+  *small_tile = tc ? (tc - 1) % 3 : -1;
+  *large_tile = tc ? (tc - 1) / 3 : -1;
   return CC_OK;
 }
 

@@ -116,6 +116,8 @@ void workspace_free(cc_tables t);
 cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
                              const std::vector<long long>& eps_off, void** out);
 cc_status mixed_batch_run(void* mb, float* eps, double* Ex, cudaStream_t st);
+cc_status mixed_batch_tune(void* mb, float* eps, double* Ex, int reps, int* choice, float* ms,
+                           cudaStream_t st);
 void mixed_batch_free(void* mb);
 cc_status mixed_workspace_alloc(cc_tables t);
 void mixed_workspace_free(cc_tables t);
@@ -140,6 +142,8 @@ bool tc_small_batch_supported(const std::vector<cc_tables>& tabs, const std::vec
 cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
                                 const std::vector<long long>& eps_off, void** out);
 cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStream_t st);
+cc_status tc_small_batch_tune(void* p, int* err, float* eps, double* Ex, int reps, int* choice,
+                              float* ms, cudaStream_t st);
 void tc_small_batch_free(void* p);
 // simtslab.cu (plain FP32 exchange by the slab algorithm, grid side 50..127)
 bool simt_slab_supported(cc_tables t);

@@ -83,6 +83,7 @@ struct SBox {
 struct Args {
   const SBox* boxes;  // batches: nbox entries; single boxes: nullptr (b0 is used)
   SBox b0;
+  const long long* cta0;  // batches: first unit of CTA c at cta0[c] (grid + 1 entries)
   int nbox, units, rf_max;
   const uint32_t* FR;  // [nodes][64][64] F_s[a][h] as bf16 hi (low half) | lo (high half)
   const float* w;      // [nodes]
@@ -96,6 +97,18 @@ __host__ __device__ inline int owner_cta(long long u, int units, int grid) {
   while (c + 1 < grid && (long long)(c + 1) * units / grid <= u) ++c;
   while (c > 0 && (long long)c * units / grid > u) --c;
   return c;
+}
+
+// the CTA that owns unit u: an equal split of the units, or the table of CTA starts
+__host__ __device__ inline int owner_of(long long u, const long long* cta0, int units, int grid) {
+  if (!cta0) return owner_cta(u, units, grid);
+  int lo = 0, hi = grid - 1;  // last c with cta0[c] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta0[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // the box of a role's current unit; batches walk the table forward as units increase
@@ -241,8 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const long long u0 = (long long)blockIdx.x * g.units / gridDim.x;
-  const long long u1 = (long long)(blockIdx.x + 1) * g.units / gridDim.x;
+  const long long u0 =
+      g.cta0 ? g.cta0[blockIdx.x] : (long long)blockIdx.x * g.units / gridDim.x;
+  const long long u1 =
+      g.cta0 ? g.cta0[blockIdx.x + 1] : (long long)(blockIdx.x + 1) * g.units / gridDim.x;
   // the band [zs, ze) of y, y' and z of box X in 16-aligned K steps
   auto band_lo = [](const SBox& X) { return (X.R - X.RF) & ~15; };
   auto band_hi = [](const SBox& X) {
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const long long p = loc / C.X.S;
       const int kseg =
-          (int)blockIdx.x - owner_cta(C.X.unit0 + p * C.X.S, g.units, gridDim.x);
+          (int)blockIdx.x - owner_of(C.X.unit0 + p * C.X.S, g.cta0, g.units, gridDim.x);
       tmem_ld32(tmem + lane_off + 128u + 32u * half, v);
       float4* o = reinterpret_cast<float4*>(
           g.part + C.X.part0 + ((p * C.X.maxseg + kseg) * 128 + 32 * quad + lane) * (long long)kG +
@@ -755,15 +770,15 @@ struct FBox {
 
 __global__ void __launch_bounds__(256)
     k_tcsb_finalize(const FBox* __restrict__ boxes, const int* __restrict__ slab_box,
-                    const float* part, const float* FB, int units, int grid, float* eps,
-                    double* slab_ex, unsigned* ticket, double* Ex) {
+                    const long long* cta0, const float* part, const float* FB, int units,
+                    int grid, float* eps, double* slab_ex, unsigned* ticket, double* Ex) {
   const int gx = blockIdx.x, b = slab_box[gx];
   const FBox X = boxes[b];
   const int x = gx - X.slab0, Mg = X.Mg, R = X.R, RF = X.RF;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = x >> 1, j = x & 1;
-  const int c0 = owner_cta(X.unit0 + (long long)p * X.S, units, grid);
-  const int nseg = owner_cta(X.unit0 + (long long)(p + 1) * X.S - 1, units, grid) - c0 + 1;
+  const int c0 = owner_of(X.unit0 + (long long)p * X.S, cta0, units, grid);
+  const int nseg = owner_of(X.unit0 + (long long)(p + 1) * X.S - 1, cta0, units, grid) - c0 + 1;
   const int dx = x - R;
   double wacc = 0.0;
   for (int y = warp; y < Mg; y += 8) {
@@ -834,11 +849,12 @@ cc_status set_smem_attrs() {
 }
 
 // the largest number of CTAs that one slab pair's units are spread over
-int max_segments(long long unit0, int pairs, int S, int units, int grid) {
+int max_segments(long long unit0, int pairs, int S, int units, int grid,
+                 const long long* cta0 = nullptr) {
   int m = 1;
   for (int p = 0; p < pairs; ++p) {
-    const int c0 = owner_cta(unit0 + (long long)p * S, units, grid);
-    const int c1 = owner_cta(unit0 + (long long)(p + 1) * S - 1, units, grid);
+    const int c0 = owner_of(unit0 + (long long)p * S, cta0, units, grid);
+    const int c1 = owner_of(unit0 + (long long)(p + 1) * S - 1, cta0, units, grid);
     m = std::max(m, c1 - c0 + 1);
   }
   return m;
@@ -945,6 +961,7 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
   Args a{};
   a.boxes = nullptr;
   a.b0 = SBox{R, R_F, Mg, S, 0, 0, 0, 0, w->maxseg, 0};
+  a.cta0 = nullptr;
   a.nbox = 1;
   a.units = w->units;
   a.rf_max = R_F;
@@ -969,16 +986,29 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
 }
 
 // ---------------------------------------------------------------- batches of boxes
+// The work decomposition of a batch is tunable (cc_batch_tune): the order of the boxes in
+// the unit sequence (as given, or by decreasing cost) and how the sequence is cut among the
+// CTAs (equal unit counts, or equal estimated cost: per unit a fixed latency of about
+// kUnitFixed cycles plus the MMA time, 48 cycles per 128 x 16 x N2 / 64 operand step).
+constexpr double kUnitFixed = 2400.0;
+
 struct TcSmallBatch {
   int nbox = 0, units = 0, grid = 0, rf_max = 0, slabs = 0;
+  int order = 0, split = 0;  // the current plan (see above)
+  std::vector<cc_tables> tabs;
+  std::vector<int> R_F;
+  std::vector<long long> eps_off;
+  std::vector<long long> node0;  // first node of box b in the concatenated planes
   SBox* boxes = nullptr;
   FBox* fboxes = nullptr;
   int* slab_box = nullptr;
+  long long* cta0 = nullptr;
   uint32_t* FR = nullptr;
   void* F[2] = {nullptr, nullptr};
   void* T[2] = {nullptr, nullptr};
   float* FB = nullptr;
   float* part = nullptr;
+  size_t part_cap = 0;
   double* slab_ex = nullptr;
   float* w = nullptr;
   unsigned* ticket = nullptr;
@@ -996,7 +1026,99 @@ void tc_small_batch_free(void* p) {
   TcSmallBatch* m = reinterpret_cast<TcSmallBatch*>(p);
   if (!m) return;
   for (void* a : m->allocs) cudaFree(a);
+  cudaFree(m->part);
   delete m;
+}
+
+static double unit_cost(int R, int RF, int Mg) {
+  const int steps = (std::min(kG, (R + RF + 16) & ~15) - ((R - RF) & ~15)) / 16;
+  const int nh = (RF + 16) >> 4, N2 = (Mg + 15) & ~15;
+  return kUnitFixed + 48.0 * (6 * steps + 2 * nh) * N2 / 64.0;
+}
+
+// unit sequence, CTA cuts, partial layout and finaliser tables for (order, split)
+static cc_status small_batch_plan(TcSmallBatch* m, int order, int split) {
+  const int nb = m->nbox;
+  std::vector<int> seq(nb);
+  for (int b = 0; b < nb; ++b) seq[b] = b;
+  auto cost_of = [&](int b) {
+    const cc_tables t = m->tabs[b];
+    return unit_cost(t->p.R, m->R_F[b], t->Mg) * ((t->Mg + 1) / 2) * t->S_eff;
+  };
+  if (order == 1)
+    std::stable_sort(seq.begin(), seq.end(), [&](int a, int b) { return cost_of(a) > cost_of(b); });
+  std::vector<SBox> bx(nb);  // in unit order
+  std::vector<FBox> fb(nb);  // by box index
+  std::vector<double> ucost;
+  long long units = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int b = seq[k];
+    const cc_tables t = m->tabs[b];
+    const int pairs = (t->Mg + 1) / 2;
+    bx[k] = SBox{t->p.R, m->R_F[b], t->Mg, t->S_eff, units, m->node0[b] * kG * kG,
+                 m->node0[b], 0, 1, 0};
+    units += (long long)pairs * t->S_eff;
+    if (split == 1) ucost.push_back(unit_cost(t->p.R, m->R_F[b], t->Mg));
+  }
+  const int grid = (int)std::min<long long>(sm_count(), units);
+  std::vector<long long> cuts(grid + 1);
+  if (split == 1) {  // equal estimated cost per CTA
+    double total = 0.0;
+    for (int k = 0; k < nb; ++k) total += ucost[k] * (double)((bx[k].Mg + 1) / 2) * bx[k].S;
+    double acc = 0.0;
+    int c = 1;
+    cuts[0] = 0;
+    for (int k = 0; k < nb && c < grid; ++k) {
+      const long long n = (long long)((bx[k].Mg + 1) / 2) * bx[k].S;
+      for (long long i = 0; i < n && c < grid; ++i) {
+        acc += ucost[k];
+        if (acc >= total * c / grid) cuts[c++] = bx[k].unit0 + i + 1;
+      }
+    }
+    for (; c < grid; ++c) cuts[c] = units;
+    cuts[grid] = units;
+    for (int c2 = 1; c2 <= grid; ++c2) cuts[c2] = std::max(cuts[c2], cuts[c2 - 1]);
+  } else {
+    for (int c = 0; c <= grid; ++c) cuts[c] = (long long)c * units / grid;
+  }
+  long long part = 0;
+  int slab = 0;
+  std::vector<int> slab_box(m->slabs);
+  std::vector<int> slab0(nb);
+  for (int b = 0, sl = 0; b < nb; ++b) {
+    slab0[b] = sl;
+    for (int x = 0; x < m->tabs[b]->Mg; ++x) slab_box[sl++] = b;
+  }
+  for (int k = 0; k < nb; ++k) {
+    const int b = seq[k];
+    const int pairs = (bx[k].Mg + 1) / 2;
+    bx[k].maxseg = max_segments(bx[k].unit0, pairs, bx[k].S, (int)units, grid, cuts.data());
+    bx[k].part0 = part;
+    part += (long long)pairs * bx[k].maxseg * 128 * kG;
+    fb[b] = FBox{bx[k].R, bx[k].RF, bx[k].Mg, bx[k].S, bx[k].maxseg, slab0[b], bx[k].unit0,
+                 bx[k].part0, m->eps_off[b], m->tabs[b]->pref};
+  }
+  (void)slab;
+  const size_t pbytes = sizeof(float) * (size_t)part;
+  if (pbytes > m->part_cap) {
+    cudaFree(m->part);
+    m->part = nullptr;
+    m->part_cap = 0;
+    if (cudaMalloc((void**)&m->part, pbytes) != cudaSuccess) {
+      set_last_error("cudaMalloc(small-grid batch partials)", cudaErrorMemoryAllocation);
+      return CC_ERR_ALLOC;
+    }
+    m->part_cap = pbytes;
+  }
+  m->units = (int)units;
+  m->grid = grid;
+  m->order = order;
+  m->split = split;
+  CC_CUDA(cudaMemcpy(m->boxes, bx.data(), sizeof(SBox) * nb, cudaMemcpyHostToDevice));
+  CC_CUDA(cudaMemcpy(m->fboxes, fb.data(), sizeof(FBox) * nb, cudaMemcpyHostToDevice));
+  CC_CUDA(cudaMemcpy(m->slab_box, slab_box.data(), sizeof(int) * m->slabs, cudaMemcpyHostToDevice));
+  CC_CUDA(cudaMemcpy(m->cta0, cuts.data(), sizeof(long long) * (grid + 1), cudaMemcpyHostToDevice));
+  return CC_OK;
 }
 
 cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
@@ -1008,30 +1130,15 @@ cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::v
   if (!m) return CC_ERR_ALLOC;
   const int nb = (int)tabs.size();
   m->nbox = nb;
-  std::vector<SBox> bx(nb);
-  std::vector<FBox> fb(nb);
-  std::vector<int> slab_box;
-  long long units = 0, nodes = 0;
+  m->tabs = tabs;
+  m->R_F = R_F;
+  m->eps_off = eps_off;
+  long long nodes = 0;
   for (int b = 0; b < nb; ++b) {
-    const cc_tables t = tabs[b];
-    const int pairs = (t->Mg + 1) / 2;
-    bx[b] = SBox{t->p.R, R_F[b], t->Mg, t->S_eff, units, nodes * kG * kG, nodes, 0, 1, 0};
-    units += (long long)pairs * t->S_eff;
-    nodes += t->S_eff;
+    m->node0.push_back(nodes);
+    nodes += tabs[b]->S_eff;
+    m->slabs += tabs[b]->Mg;
     m->rf_max = std::max(m->rf_max, R_F[b]);
-  }
-  m->units = (int)units;
-  m->grid = (int)std::min<long long>(sm_count(), units);
-  long long part = 0;
-  for (int b = 0; b < nb; ++b) {
-    const int pairs = (bx[b].Mg + 1) / 2;
-    bx[b].maxseg = max_segments(bx[b].unit0, pairs, bx[b].S, m->units, m->grid);
-    bx[b].part0 = part;
-    part += (long long)pairs * bx[b].maxseg * 128 * kG;
-    fb[b] = FBox{bx[b].R, bx[b].RF, bx[b].Mg, bx[b].S, bx[b].maxseg, m->slabs, bx[b].unit0,
-                 bx[b].part0, eps_off[b], tabs[b]->pref};
-    for (int x = 0; x < bx[b].Mg; ++x) slab_box.push_back(b);
-    m->slabs += bx[b].Mg;
   }
   auto alloc = [&](void** p, size_t bytes) -> cc_status {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -1047,11 +1154,11 @@ cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::v
   if ((st = alloc((void**)&m->boxes, sizeof(SBox) * nb)) != CC_OK ||
       (st = alloc((void**)&m->fboxes, sizeof(FBox) * nb)) != CC_OK ||
       (st = alloc((void**)&m->slab_box, sizeof(int) * m->slabs)) != CC_OK ||
+      (st = alloc((void**)&m->cta0, sizeof(long long) * (sm_count() + 1))) != CC_OK ||
       (st = alloc((void**)&m->FR, sizeof(uint32_t) * (size_t)nodes * kG * kHMax)) != CC_OK ||
       (st = alloc(&m->F[0], plane)) != CC_OK || (st = alloc(&m->F[1], plane)) != CC_OK ||
       (st = alloc(&m->T[0], plane)) != CC_OK || (st = alloc(&m->T[1], plane)) != CC_OK ||
       (st = alloc((void**)&m->FB, sizeof(float) * nb * kG * kHMax)) != CC_OK ||
-      (st = alloc((void**)&m->part, sizeof(float) * part)) != CC_OK ||
       (st = alloc((void**)&m->slab_ex, sizeof(double) * m->slabs)) != CC_OK ||
       (st = alloc((void**)&m->w, sizeof(float) * nodes)) != CC_OK ||
       (st = alloc((void**)&m->ticket, sizeof(unsigned) * nb)) != CC_OK) {
@@ -1069,22 +1176,16 @@ cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::v
   std::vector<float> w(nodes);
   for (int b = 0; b < nb; ++b) {
     const cc_tables t = tabs[b];
-    const long long o = bx[b].fr0;
+    const long long o = m->node0[b] * kG * kG;
     k_tcs_prep<<<(t->S_eff * kG + 127) / 128, 128>>>(t->d.Tm64, t->S_eff, t->Mg, t->p.R, R_F[b], 1,
                                                       m->FR + o, (__nv_bfloat16*)m->F[0] + o,
                                                       (__nv_bfloat16*)m->F[1] + o);
     k_tcs_tplanes<<<128, 256>>>(t->d.Tm64, t->S_eff, t->Mg, (__nv_bfloat16*)m->T[0] + o,
                                 (__nv_bfloat16*)m->T[1] + o);
     k_tcs_dbar<<<1, kG>>>(t->d.Dbar64, t->Mg, t->p.R, R_F[b], m->FB + (long long)b * kG * kHMax);
-    for (int i = 0; i < t->S_eff; ++i) w[bx[b].w0 + i] = (float)t->w[t->kept_idx[i]];
+    for (int i = 0; i < t->S_eff; ++i) w[m->node0[b] + i] = (float)t->w[t->kept_idx[i]];
   }
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->boxes, bx.data(), sizeof(SBox) * nb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->fboxes, fb.data(), sizeof(FBox) * nb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->slab_box, slab_box.data(), sizeof(int) * m->slabs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(m->w, w.data(), sizeof(float) * nodes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->ticket, 0, sizeof(unsigned) * nb);
@@ -1093,6 +1194,10 @@ cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::v
     set_last_error("small-grid tensor-core batch planes", e);
     tc_small_batch_free(m);
     return CC_ERR_CUDA;
+  }
+  if ((st = small_batch_plan(m, 0, 0)) != CC_OK) {
+    tc_small_batch_free(m);
+    return st;
   }
   *out = m;
   return CC_OK;
@@ -1103,6 +1208,7 @@ cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStre
   if (!m) return CC_ERR_NOTSUPP;
   Args a{};
   a.boxes = m->boxes;
+  a.cta0 = m->cta0;
   a.nbox = m->nbox;
   a.units = m->units;
   a.rf_max = m->rf_max;
@@ -1116,9 +1222,54 @@ cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStre
   const CUtensorMap& fh = *reinterpret_cast<const CUtensorMap*>(m->map_fh);
   const CUtensorMap& fl = *reinterpret_cast<const CUtensorMap*>(m->map_fl);
   k_tcs<true, true><<<m->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
-  k_tcsb_finalize<<<m->slabs, 256, 0, st>>>(m->fboxes, m->slab_box, m->part, m->FB, m->units,
-                                            m->grid, eps, m->slab_ex, m->ticket, Ex);
+  k_tcsb_finalize<<<m->slabs, 256, 0, st>>>(m->fboxes, m->slab_box, m->cta0, m->part, m->FB,
+                                            m->units, m->grid, eps, m->slab_ex, m->ticket, Ex);
   CC_CUDA(cudaGetLastError());
+  return CC_OK;
+}
+
+// Times every (order, split) plan with CUDA events (median of reps runs) and keeps the
+// fastest.  choice[0] = order (0 as given, 1 by decreasing cost), choice[1] = split (0 equal
+// units, 1 equal estimated cost).  Writes valid sums into eps / Ex while timing.
+cc_status tc_small_batch_tune(void* p, int* err, float* eps, double* Ex, int reps,
+                              int* choice, float* ms_out, cudaStream_t st) {
+  TcSmallBatch* m = reinterpret_cast<TcSmallBatch*>(p);
+  if (!m || reps < 1) return CC_ERR_ARG;
+  cudaEvent_t e0, e1;
+  CC_CUDA(cudaEventCreate(&e0));
+  CC_CUDA(cudaEventCreate(&e1));
+  float best = -1.0f;
+  int bo = 0, bs = 0;
+  cc_status s = CC_OK;
+  for (int order = 0; order < 2 && s == CC_OK; ++order)
+    for (int split = 0; split < 2 && s == CC_OK; ++split) {
+      if ((s = small_batch_plan(m, order, split)) != CC_OK) break;
+      if ((s = tc_small_batch_run(m, err, eps, Ex, st)) != CC_OK) break;
+      std::vector<float> t(reps);
+      for (int r = 0; r < reps && s == CC_OK; ++r) {
+        cudaEventRecord(e0, st);
+        s = tc_small_batch_run(m, err, eps, Ex, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = CC_ERR_CUDA;
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      if (s != CC_OK) break;
+      std::sort(t.begin(), t.end());
+      if (best < 0.0f || t[reps / 2] < best) {
+        best = t[reps / 2];
+        bo = order;
+        bs = split;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == CC_OK) s = small_batch_plan(m, bo, bs);
+  if (s != CC_OK) return s;
+  if (choice) {
+    choice[0] = bo;
+    choice[1] = bs;
+  }
+  if (ms_out) *ms_out = best;
   return CC_OK;
 }
 

@@ -1079,6 +1079,13 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
   return CC_OK;
 }
 
+cc_status mixed_batch_tune(void* p, float* eps, double* Ex, int reps, int* choice, float* ms,
+                           cudaStream_t st) {
+  MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
+  if (!m || !m->small) return CC_ERR_NOTSUPP;
+  return tc_small_batch_tune(m->small, m->err, eps, Ex, reps, choice, ms, st);
+}
+
 cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return CC_ERR_NOTSUPP;

@@ -155,3 +155,32 @@ def test_exchange_errors(dev):
             cc.exchange_sums(t, R_F, eps, Ex)
         assert e.value.status == 2
     t.free()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_gemm_tile_autotuner(dev, prec):
+    """The SIMT GEMM tile autotuner: times the dense chain with every tile pair and keeps the
+    fastest for the grid side; every tile pair sums each output in the same order (16-wide K
+    tiles, Kahan across them), so the results are bit-identical before and after tuning."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    R, R_F, L, S = 27, 12, 25.0, 40
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    Mg = t.info["Mg"]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    assert cc.lib().cc_set_simt_variant(1) == 0   # the dense chain (grid side 55 > 49)
+    try:
+        e0 = torch.empty(Mg ** 3, dtype=dt, device=dev)
+        x0 = torch.zeros(2, dtype=torch.float64, device=dev)
+        cc.exchange_sums(t, R_F, e0, x0, precision=prec)
+        choice = cc.autotune_gemm(t, R_F, precision=prec, reps=2)
+        assert choice["small"] in cc.TILES.values() and choice["large"] in cc.TILES.values()
+        assert cc.gemm_tiles_tuned(prec, Mg) == {"small": choice["small"], "large": choice["large"]}
+        e1 = torch.empty_like(e0)
+        x1 = torch.zeros_like(x0)
+        cc.exchange_sums(t, R_F, e1, x1, precision=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(e0, e1) and torch.equal(x0, x1)
+    finally:
+        assert cc.lib().cc_set_simt_variant(0) == 0
+    t.free()
