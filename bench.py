@@ -351,10 +351,13 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0 and world == 1:
         # last on the line: the metric's mixed-vs-FP32 comparison in compact form
-        line["mixed_vs_fp32"] = mixed_vs_fp32(line.get("mode_products"),
-                                              line.get("large_lookups"),
-                                              line.get("batched"),
-                                              line.get("general_lookups"))
+        try:
+            line["mixed_vs_fp32"] = mixed_vs_fp32(line.get("mode_products"),
+                                                  line.get("large_lookups"),
+                                                  line.get("batched"),
+                                                  line.get("general_lookups"))
+        except (KeyError, TypeError, ValueError) as e:   # never lose the line to a summary
+            line["mixed_vs_fp32"] = {"error": f"summary not formed: {e!r}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     t.free()
@@ -435,6 +438,27 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
         res[prec] = (ms, eps.cpu().numpy().astype(np.float64), float(Ex[0].item()))
         out[prec + "_ms"] = ms
         out[prec + "_useful_tflops"] = 6.0 * Mg ** 4 * S_eff / (ms * 1e-3) / 1e12
+    # the same tensor-core product without the lo-plane correction (hi * hi only)
+    cc.lib().cc_set_mixed_terms(1)
+    try:
+        eps = torch.empty(Mg ** 3, dtype=torch.float32, device=dev)
+        Ex = torch.empty(2, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            cc.exchange_sums(t, R_F, eps, Ex, precision="bf16x3")
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            cc.exchange_sums(t, R_F, eps, Ex, precision="bf16x3")
+        b.record(st)
+        torch.cuda.synchronize()
+        res["bf16x1"] = (a.elapsed_time(b) / reps, eps.cpu().numpy().astype(np.float64),
+                         float(Ex[0].item()))
+        out["bf16x1_ms"] = res["bf16x1"][0]
+        out["bf16x1_note"] = "bf16 hi * hi products only (no lo-plane correction)"
+    finally:
+        cc.lib().cc_set_mixed_terms(3)
     out["fp32_executed_tflops"] = simt_slab_flop(R_F, Mg, S_eff) / (res["fp32"][0] * 1e-3) / 1e12
     ex = tc_slab_executed_flop(R, R_F, Mg, S_eff)
     for prec in ("bf16x3", "fp16x3") if with_fp16 else ("bf16x3",):
@@ -460,7 +484,7 @@ def mode_products(name, reps=10, oracle_sample=200, with_fp16=True):
         ref = ox.eps_separable(R, R_F, L, aa[keep], ww[keep], k_idx=idx)
         k = ob.basis(R)[idx] + R
         flat = (k[:, 0] * Mg + k[:, 1]) * Mg + k[:, 2]
-        for prec in precs:
+        for prec in precs + ["bf16x1"]:
             got = res[prec][1][flat]
             out[prec + "_max_rel_err_vs_oracle"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
         out["oracle_sample"] = f"{len(idx)} seeded basis functions of {Nb}"
@@ -484,7 +508,7 @@ def mixed_vs_fp32(mp, large, batched_sec, general):
             "bf16x3_frac_exec": _sig(m.get("bf16x3_executed_frac_of_peak"), 3),
             "fp32_exec_tflops": _sig(m.get("fp32_executed_tflops"), 3),
             "err": {k: _sig(m.get(k + "_max_rel_err_vs_oracle"), 2)
-                    for k in ("fp32", "bf16x3", "fp16x3")},
+                    for k in ("fp32", "bf16x3", "fp16x3", "bf16x1")},
             "x_bf16x3_vs_fp32": _sig(m.get("speedup_bf16x3_vs_fp32"), 3),
             "x_bf16x3_vs_fp32_dense": _sig(m.get("speedup_bf16x3_vs_fp32_dense"), 3),
         }
@@ -493,8 +517,13 @@ def mixed_vs_fp32(mp, large, batched_sec, general):
                               if k in batched_sec}
         out["batch256_bf16x3_frac_exec"] = _sig(batched_sec["bf16x3"].get("executed_frac_of_peak"), 3)
     if large:
-        out["cfg5_1e9_lookups"] = {k: {"ms": _sig(v["ms"]), "hbm_frac": _sig(v["hbm_frac"], 3)}
-                                   for k, v in large.items() if isinstance(v, dict)}
+        out["cfg5_1e9_lookups"] = {k: {"ms": _sig(v.get("ms")), "hbm_frac": _sig(v.get("hbm_frac"), 3)}
+                                   for k, v in large.items() if isinstance(v, dict) and "hbm_frac" in v}
+        tuned = large.get("vec_separable_mesh_for_1e-8")
+        if tuned:
+            out["cfg5_separable_mesh_for_1e-8"] = {
+                "ms": _sig(tuned["ms"]), "S_eff": tuned["S_eff"],
+                "x_vs_128_node_mesh": _sig(tuned["speedup_vs_128_node_mesh"], 3)}
     if general:
         out["general_box_lookups"] = {"integrals_per_s": _sig(general["fp32"]["integrals_per_s"]),
                                       "fp64_integrals_per_s": _sig(general["fp64"]["integrals_per_s"])}
@@ -675,6 +704,24 @@ def large_lookups(n=1_000_000_000, reps=3):
             gbs = 20.0 * n / (ms * 1e-3) / 1e9
             out[f"{fmt}_{lookup}"] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3),
                                       "hbm_GBps": gbs, "hbm_frac": gbs / peak}
+    # the separable lookup on tables built for a stated method error (1e-8): the tuned mesh
+    # with the fewest nodes instead of the 128-node workload mesh
+    tt = cc.build_tables_for_error("periodic", R=63, L=60.0, target=1e-8)
+    cc.reconstruct_integrals(tt, vecs, vals, lookup="separable")
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(reps):
+        cc.reconstruct_integrals(tt, vecs, vals, lookup="separable")
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out["vec_separable_mesh_for_1e-8"] = {
+        "ms": ms, "integrals_per_s": n / (ms * 1e-3), "S": tt.info["S"],
+        "S_eff": tt.info["S_eff"], "alpha_c": tt.info["alpha_c"], "ratio": tt.info["ratio"],
+        "speedup_vs_128_node_mesh": out["vec_separable"]["ms"] / ms}
+    tt.free()
     del q, vals, vecs
     t.free()
     torch.cuda.empty_cache()

@@ -79,15 +79,17 @@ typedef enum {
  *   R         basis cutoff |n|^2 <= R^2, 1 <= R <= 127.  Tables cover Delta = 0..2R.
  *   L         box side (bohr), > 0.
  *   S         total number of quadrature nodes, 2 <= S <= 1024.
- *   n_sub     interval [0, alpha_c] is split at alpha_c 5^-n_sub, ..., alpha_c/5
+ *   n_sub     interval [0, alpha_c] is split at alpha_c ratio^-n_sub, ..., alpha_c/ratio
  *             (n_sub + 1 Gauss-Legendre sub-intervals; 0 = one interval, the paper's
- *             Mesh 1; 7 = the paper's Mesh 2).  < 0 selects the default rule.
+ *             Mesh 1; 7 with ratio 5 = the paper's Mesh 2).  < 0 selects the default rule.
  *   q_tail    Gauss-Legendre points in t = alpha^{-1/2} on (0, alpha_c^{-1/2}] (Eq. 11);
  *             < 0 selects the default rule.
  *   alpha_c   split point (Sec. II fixes alpha_c = 1).  PERIODIC: in index units
  *             a = alpha (2 pi / L)^2; BOX: in bohr^2.  <= 0 selects 1.
  *   prune_tol PERIODIC only: drop node s when w_s exp(-a_s) < prune_tol / (12 R^2);
  *             0 keeps all nodes.  Negative selects 1e-9.  Ignored for BOX.
+ *   ratio     sub-interval ratio of the split of [0, alpha_c] (the paper's Mesh 2: 5);
+ *             <= 1 selects 5.
  * Default rule: (S, R) = (32, 4) -> (2, 10); (64, 13) -> (3, 21); (96, 31) -> (4, 29);
  * (128, 63) -> (5, 34); otherwise a search: with r = max(1, floor(log5(12 R^2)) - 1),
  * n_sub in {r, r + 1} and q_tail in 3 .. max(3, round(0.45 S)) (S - q_tail >= n_sub + 1),
@@ -106,6 +108,7 @@ typedef struct {
   int q_tail;
   double alpha_c;
   double prune_tol;
+  double ratio;
 } cc_table_params;
 
 typedef struct cc_tables_s* cc_tables;
@@ -119,6 +122,7 @@ typedef struct {
   int m_max;          /* collapsed table covers m = 0..m_max = 4 R^2 */
   size_t device_bytes; /* device memory held by the handle (tables + workspace) */
   size_t table_bytes;  /* of which the FP32 lookup tables (the stored compression) */
+  double ratio;        /* sub-interval ratio of the mesh */
   int general_codes;   /* BOX: entries per node of the two-index tables, (2R + 1)^2; 0 for
                           PERIODIC (Sec. III counts 4 N^{2/3} per node for N planewaves) */
   size_t general_table_bytes; /* BOX: FP32 two-index lookup tables, general_codes x S_eff
@@ -180,6 +184,25 @@ cc_status cc_default_mesh(int S, int R, int* n_sub, int* q_tail);
 cc_status cc_mesh_for_error(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
                             double* err);
 
+/* Mesh tuning for a stated method error (host only, no GPU; not a rule of the paper, which
+ * fixes alpha_c = 1 and leaves "the value of alpha_c which allows for the most efficient
+ * numerical integration" and more than two intervals open, Sec. II).  Searches the
+ * sub-interval ratio in {3, 4, 5, 6, 8}, alpha_c in {0.5, 1, 2} (periodic index units) and
+ * the default rule's n_sub (computed from the ratio) and q_tail ranges, for node counts from
+ * 0.8 to 1 times the count cc_mesh_for_error returns for the same target: the fewest nodes
+ * whose best candidate has the periodic-kernel error (as in cc_mesh_for_error) of at most
+ * target; ties as in the default rule.  Writes the mesh (S, n_sub, q_tail, alpha_c, ratio)
+ * and, if err is not NULL, its error.  Errors as cc_mesh_for_error. */
+cc_status cc_mesh_tune(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
+                       double* alpha_c, double* ratio, double* err);
+
+/* Build tables (as cc_build_tables, default pruning) on the mesh cc_mesh_tune picks for a
+ * stated periodic-kernel method error: the fewest nodes, so the separable lookups and the
+ * mode products do the least work for that accuracy.  The box kernel uses the same mesh.
+ * Errors as cc_mesh_tune and cc_build_tables. */
+cc_status cc_build_tables_for_error(int kernel, int R, double L, double target, int S_max,
+                                    void* stream, cc_tables* out);
+
 /* Basis of cutoff R (Sec. II Eq. 1 with |n|^2 <= R^2) in canonical order.  Writes the
  * count to *Nb; if vec_host is not NULL it must hold 4 * Nb int8 and receives
  * (n_x, n_y, n_z, 0) per function.  1 <= R <= 127. */
@@ -235,13 +258,18 @@ cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, d
  * cannot call cudaMalloc at the point where they need the sums: code running under a
  * framework's caching allocator that owns the device memory, or latency-critical loops
  * where cudaMalloc's implicit device synchronisation would stall other streams.
- * Computes exactly what cc_exchange_sums computes with CC_PREC_FP32 (eps float[Mg^3],
- * Ex_dev[2]), reading the handle's tables, but keeps all scratch in one fixed 16 MiB
- * device array inside the library (held by every GPU that loads the library until the
- * process exits) and calls no cudaMalloc, cudaFree or allocating library routine.
- * Limit: R <= 31 (grid side 63); larger handles get CC_ERR_RANGE.
+ * Computes the same sums as cc_exchange_sums with CC_PREC_FP32 (eps float[Mg^3], Ex_dev[2]),
+ * within that call's FP32 tolerance, by the plain chain of SIMT mode products over the
+ * handle's tables (cc_exchange_sums may take another FP32 form with another summation
+ * order, so the two agree to rounding, not bit for bit), but keeps all scratch in one fixed
+ * 16 MiB device array inside the library (held by every GPU that loads the library until
+ * the process exits) and calls no cudaMalloc, cudaFree or allocating library routine.
+ * Limit: R <= 31 (grid side 63); larger handles get CC_ERR_RANGE.  The handle's device
+ * must be the current device (CC_ERR_ARG otherwise).
  * The first call on a device looks up that device's address of the array
- * (cudaGetSymbolAddress, device current); make that first call before any stream
+ * (cudaGetSymbolAddress, device current) and caches it for the rest of the process: the
+ * cache assumes the device's primary context lives as long as the process (after a
+ * cudaDeviceReset the cached address is stale).  Make that first call before any stream
  * capture.  Every call shares the array and leaves the last call's contents in it:
  * calls that overlap on the GPU (any device-side overlap, on any stream, from any
  * thread) race and must be ordered by the caller. */
@@ -264,12 +292,23 @@ cc_status cc_mixed_status(cc_tables t, int* code_host, int clear);
 cc_status cc_test_stall_next_mixed(void);
 
 /* Which form the tensor-core exchange (bf16x3, fp16x3) takes (not part of the paper; a
- * diagnostic and tuning switch of this implementation, process-wide): 0 = automatic (the
- * fused slab kernel), 1 = the step chain of five batched GEMM launches, 2 = the fused slab
- * kernel.  Both cover every grid side up to 127; batches (bf16x3) likewise take the batched
- * form of the slab kernel or, on 1, the chain.  The setting is read when a batch's graph is
+ * diagnostic and tuning switch of this implementation, process-wide): 0 = automatic, 1 = the
+ * step chain of five batched GEMM launches, 2 = the 128-row fused slab kernel (every grid
+ * side up to 127), 3 = the small-grid kernel (bf16x3, grid sides up to 64, two slabs per
+ * 128-row MMA; CC_ERR_NOTSUPP for larger grids).  Automatic takes the small-grid kernel for
+ * bf16x3 grids up to 64 and the 128-row kernel otherwise (fp16x3: always the 128-row
+ * kernel); batches (bf16x3) take the batched small-grid kernel on 0 and 3, the batched
+ * 128-row kernel on 2, the chain on 1.  The setting is read when a batch's graph is
  * captured.  CC_ERR_ARG for any other value. */
 cc_status cc_set_mixed_variant(int variant);
+
+/* Split products per mode product in the single-box bf16x3 tensor-core exchange (through
+ * the slab kernels; not part of the paper, a diagnostic of this implementation,
+ * process-wide): 3 (the default) = hi*hi + hi*lo + lo*hi, where the lo planes carry the
+ * rounding residual of every 16-bit operand and correct the product; 1 = hi*hi only, the
+ * uncorrected bf16 product, to state what the correction buys (its error is a few 1e-4
+ * relative).  fp16x3, batches and the step chain always use 3.  CC_ERR_ARG otherwise. */
+cc_status cc_set_mixed_terms(int terms);
 
 /* Which form the plain FP32 exchange (cc_exchange_sums with CC_PREC_FP32) takes at grid
  * sides 50..127 (not part of the paper; a diagnostic and comparison switch of this

@@ -34,11 +34,12 @@ def gauss_legendre(q: int, a: float, b: float):
     return 0.5 * (b - a) * x + 0.5 * (b + a), 0.5 * (b - a) * w
 
 
-def interval1_edges(n_sub: int, alpha_c: float = 1.0):
-    """Edges of the sub-intervals of [0, alpha_c]: 0, alpha_c 5^-n_sub, ..., alpha_c/5, alpha_c."""
+def interval1_edges(n_sub: int, alpha_c: float = 1.0, ratio: float = 5.0):
+    """Edges of the sub-intervals of [0, alpha_c]: 0, alpha_c ratio^-n_sub, ...,
+    alpha_c/ratio, alpha_c (the paper's Mesh 2: ratio 5)."""
     if n_sub == 0:
         return [0.0, alpha_c]
-    return [0.0] + [alpha_c * 5.0 ** (-k) for k in range(n_sub, 0, -1)] + [alpha_c]
+    return [0.0] + [alpha_c * ratio ** (-k) for k in range(n_sub, 0, -1)] + [alpha_c]
 
 
 def interval1_counts(S: int, n_sub: int, q_tail: int):
@@ -49,14 +50,14 @@ def interval1_counts(S: int, n_sub: int, q_tail: int):
     return [n // k + (1 if i < n % k else 0) for i in range(k)]
 
 
-def laplace_mesh(S: int, n_sub: int, q_tail: int, alpha_c: float = 1.0):
+def laplace_mesh(S: int, n_sub: int, q_tail: int, alpha_c: float = 1.0, ratio: float = 5.0):
     """Nodes and weights with int_0^inf F(alpha) d alpha ~= sum_s w_s F(alpha_s).
 
     Returns (alpha[S], w[S], part[S]); part is 0 on interval 1 ([0, alpha_c]) and 1 on the
     tail.  Order: sub-intervals ascending, nodes ascending inside each, then the tail
     in ascending t.
     """
-    edges = interval1_edges(n_sub, alpha_c)
+    edges = interval1_edges(n_sub, alpha_c, ratio)
     counts = interval1_counts(S, n_sub, q_tail)
     al, wl, pl = [], [], []
     for i, q in enumerate(counts):
@@ -93,10 +94,11 @@ def tune_points(R: int):
     return np.unique(np.array([1 + (top * k ** 3) // 857375 for k in range(96)], dtype=np.int64))
 
 
-def mesh_error(S: int, n_sub: int, q_tail: int, R: int) -> float:
+def mesh_error(S: int, n_sub: int, q_tail: int, R: int, alpha_c: float = 1.0,
+               ratio: float = 5.0) -> float:
     """max_m |sum_s w_s exp(-a_s m) - 1/m| * m over tune_points(R) (relative error of the
     node sum of 1/m; the Laplace form of the periodic kernel in index units)."""
-    a, w, _ = laplace_mesh(S, n_sub, q_tail)
+    a, w, _ = laplace_mesh(S, n_sub, q_tail, alpha_c, ratio)
     m = tune_points(R).astype(np.float64)
     return float(np.max(np.abs(np.exp(-np.outer(m, a)) @ w - 1.0 / m) * m))
 
@@ -142,6 +144,44 @@ def mesh_for_error(R: int, target: float, S_max: int):
         if e <= target:
             return S, n_sub, q_tail, e
     return None
+
+
+TUNE_RATIOS = (3.0, 4.0, 5.0, 6.0, 8.0)
+TUNE_ALPHAS = (0.5, 1.0, 2.0)
+
+
+def mesh_tune(R: int, target: float, S_max: int):
+    """The fewest nodes over a wider mesh family that reach mesh_error <= target (Sec. II:
+    the split point alpha_c and the sub-intervals decide how many nodes the accuracy needs;
+    the paper fixes alpha_c = 1 and leaves a better choice open).  Candidates: sub-interval
+    ratio in TUNE_RATIOS, alpha_c in TUNE_ALPHAS, n_sub in {r, r + 1} with
+    r = max(1, floor(log_ratio(12 R^2)) - 1), q_tail in 3 .. max(3, round(0.45 S)) with
+    S - q_tail >= n_sub + 1, for S from max(2, floor(0.8 S_d)) to S_d, S_d the count of
+    mesh_for_error.  The first S whose best candidate (smallest error floored at 1e-10,
+    replaced only when smaller by more than 0.1 %, visited ratio, alpha_c, n_sub, q_tail
+    ascending) reaches the target wins.  Returns (S, n_sub, q_tail, alpha_c, ratio, error)
+    or None."""
+    d = mesh_for_error(R, target, S_max)
+    if d is None:
+        return None
+    Sd = d[0]
+    m = 12.0 * R * R
+    for S in range(max(2, int(0.8 * Sd)), Sd + 1):
+        best = None
+        for ratio in TUNE_RATIOS:
+            r = max(1, int(np.floor(np.log(m) / np.log(ratio))) - 1)
+            for ac in TUNE_ALPHAS:
+                for n_sub in (r, r + 1):
+                    for q_tail in range(3, max(3, int(np.rint(0.45 * S))) + 1):
+                        if S - q_tail < n_sub + 1:
+                            continue
+                        raw = mesh_error(S, n_sub, q_tail, R, ac, ratio)
+                        e = max(raw, 1e-10)
+                        if best is None or e < best[0] * (1.0 - 1e-3):
+                            best = (e, raw, n_sub, q_tail, ac, ratio)
+        if best is not None and best[1] <= target:
+            return S, best[2], best[3], best[4], best[5], best[1]
+    return d[0], d[1], d[2], 1.0, 5.0, d[3]
 
 
 def prune_periodic(alpha_idx, w, R: int, tol: float):

@@ -42,7 +42,8 @@ class CoulombError(RuntimeError):
 class TableParams(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("R", ctypes.c_int), ("L", ctypes.c_double),
                 ("S", ctypes.c_int), ("n_sub", ctypes.c_int), ("q_tail", ctypes.c_int),
-                ("alpha_c", ctypes.c_double), ("prune_tol", ctypes.c_double)]
+                ("alpha_c", ctypes.c_double), ("prune_tol", ctypes.c_double),
+                ("ratio", ctypes.c_double)]
 
 
 class TablesInfo(ctypes.Structure):
@@ -51,7 +52,8 @@ class TablesInfo(ctypes.Structure):
                 ("alpha_c", ctypes.c_double), ("prune_tol", ctypes.c_double),
                 ("S_eff", ctypes.c_int), ("Nb", ctypes.c_int), ("Mg", ctypes.c_int),
                 ("m_max", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
-                ("table_bytes", ctypes.c_size_t), ("general_codes", ctypes.c_int),
+                ("table_bytes", ctypes.c_size_t), ("ratio", ctypes.c_double),
+                ("general_codes", ctypes.c_int),
                 ("general_table_bytes", ctypes.c_size_t)]
 
 
@@ -76,6 +78,11 @@ SIGNATURES = {
     "cc_default_mesh": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "cc_mesh_for_error": (_I, [_I, ctypes.c_double, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "cc_mesh_tune": (_I, [_I, ctypes.c_double, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "cc_build_tables_for_error": (_I, [_I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
+                                       ctypes.POINTER(_P)]),
     "cc_reconstruct_integrals": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P, _P]),
     "cc_pair_matrix": (_I, [_P, _I64, _I64, _I, _I, _P, _P]),
     "cc_exchange_sums": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -87,6 +94,7 @@ SIGNATURES = {
     "cc_test_stall_next_mixed": (_I, []),
     "cc_set_mixed_variant": (_I, [_I]),
     "cc_set_simt_variant": (_I, [_I]),
+    "cc_set_mixed_terms": (_I, [_I]),
     "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
     "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),
     "cc_batch_exchange": (_I, [_P, _I, _P, _P, _P]),
@@ -209,10 +217,11 @@ class Tables:
 
 
 def build_tables(kernel="periodic", R=4, L=10.0, S=32, n_sub=-1, q_tail=-1, alpha_c=1.0,
-                 prune_tol=-1.0, stream=None) -> Tables:
+                 prune_tol=-1.0, ratio=5.0, stream=None) -> Tables:
     """cc_build_tables: nodes, weights and tables on the current CUDA device (FP64)."""
     p = TableParams(KERNELS[kernel] if isinstance(kernel, str) else int(kernel), int(R),
-                    float(L), int(S), int(n_sub), int(q_tail), float(alpha_c), float(prune_tol))
+                    float(L), int(S), int(n_sub), int(q_tail), float(alpha_c), float(prune_tol),
+                    float(ratio))
     h = ctypes.c_void_p()
     _check("cc_build_tables", lib().cc_build_tables(ctypes.byref(p), _stream(stream),
                                                     ctypes.byref(h)))
@@ -246,6 +255,28 @@ def mesh_for_error(R: int, target: float, S_max: int = 1024):
                                                         ctypes.byref(S), ctypes.byref(n),
                                                         ctypes.byref(q), ctypes.byref(e)))
     return S.value, n.value, q.value, e.value
+
+
+def mesh_tune(R: int, target: float, S_max: int = 1024):
+    """cc_mesh_tune: (S, n_sub, q_tail, alpha_c, ratio, error) of the fewest nodes over the
+    tuned mesh family that reach the stated method error."""
+    S, n, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    a, r, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check("cc_mesh_tune", lib().cc_mesh_tune(int(R), float(target), int(S_max), ctypes.byref(S),
+                                              ctypes.byref(n), ctypes.byref(q), ctypes.byref(a),
+                                              ctypes.byref(r), ctypes.byref(e)))
+    return S.value, n.value, q.value, a.value, r.value, e.value
+
+
+def build_tables_for_error(kernel="periodic", R=4, L=10.0, target=1e-6, S_max=1024,
+                           stream=None) -> Tables:
+    """cc_build_tables_for_error: tables on the tuned mesh with the fewest nodes for a stated
+    periodic-kernel method error."""
+    h = ctypes.c_void_p()
+    _check("cc_build_tables_for_error", lib().cc_build_tables_for_error(
+        KERNELS[kernel] if isinstance(kernel, str) else int(kernel), int(R), float(L),
+        float(target), int(S_max), _stream(stream), ctypes.byref(h)))
+    return Tables(h.value)
 
 
 def basis(R: int) -> np.ndarray:
@@ -382,7 +413,7 @@ class Batch:
             arr[i].p = TableParams(KERNELS[k] if isinstance(k, str) else int(k), int(b["R"]),
                                    float(b["L"]), int(b["S"]), int(b.get("n_sub", -1)),
                                    int(b.get("q_tail", -1)), float(b.get("alpha_c", 1.0)),
-                                   float(b.get("prune_tol", -1.0)))
+                                   float(b.get("prune_tol", -1.0)), float(b.get("ratio", 5.0)))
             arr[i].R_F = int(b["R_F"])
         h = ctypes.c_void_p()
         _check("cc_batch_create", lib().cc_batch_create(arr, len(boxes), _stream(stream),

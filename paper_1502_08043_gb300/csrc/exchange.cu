@@ -503,10 +503,12 @@ static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up once per device (with
-// that device current) and cached.
-static cc_status noalloc_scratch(void** out) {
+// that device current) and cached for the process (one primary context per device).  The
+// handle's tables must live on that same device.
+static cc_status noalloc_scratch(cc_tables t, void** out) {
   int dev = 0;
   CC_CUDA(cudaGetDevice(&dev));
+  if (dev != t->device) return CC_ERR_ARG;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return CC_ERR_RANGE;
   void* p = __atomic_load_n(&g_noalloc_ptr[dev], __ATOMIC_ACQUIRE);
   if (!p) {
@@ -524,7 +526,7 @@ extern "C" cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_d
   if (t->p.R > kNoAllocMaxR) return CC_ERR_RANGE;
   if (R_F < 1 || R_F > t->p.R) return CC_ERR_RANGE;
   void* base = nullptr;
-  CC_TRY(noalloc_scratch(&base));
+  CC_TRY(noalloc_scratch(t, &base));
   // layout: occ | E | part (each start 256-byte aligned) | P[chunk][Mg^3] | Q[chunk][Mg^3]
   const size_t G3 = (size_t)t->Mg * t->Mg * t->Mg;
   const size_t tensor = G3 * sizeof(float);

@@ -131,13 +131,13 @@ cc_status tc_slab_alloc(cc_tables t, void** out);
 void tc_slab_free(void* ws);
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
                       int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
-                      bool half);
+                      bool half, int x1 = 0);
 // tcsmall.cu (tensor-core exchange, bf16x3, grid side up to 64: two slabs per 128-row MMA)
 bool tc_small_supported(cc_tables t);
 cc_status tc_small_alloc(cc_tables t, void** out);
 void tc_small_free(void* ws);
 cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F, float* eps,
-                       double* Ex, cudaStream_t st);
+                       double* Ex, cudaStream_t st, int x1 = 0);
 bool tc_small_batch_supported(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F);
 cc_status tc_small_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
                                 const std::vector<long long>& eps_off, void** out);

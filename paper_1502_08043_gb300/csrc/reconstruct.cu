@@ -353,23 +353,28 @@ __global__ void __launch_bounds__(256) k_gen(Src src, int64_t n, const T* __rest
 }
 
 // ---------------------------------------------------------------- collapsed kernel
-template <typename T, typename Src>
+// kRep copies of the table V_m in shared memory, copy c holding entry m at word kRep m + c,
+// and lane l reading copy l % kRep: a warp's gathers of V_m then conflict at most
+// 32 / kRep ways (kRep = 16: lanes l and l + 16 share a copy), instead of landing on random
+// banks.  kRep = 1 is the plain table.
+template <typename T, typename Src, int kRep>
 __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __restrict__ gVm,
                                              int m_max, T* __restrict__ out,
                                              unsigned long long* counters, int basis_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* Vm = reinterpret_cast<T*>(smem);
-  for (int i = threadIdx.x; i <= m_max; i += blockDim.x) Vm[i] = gVm[i];
+  for (int i = threadIdx.x; i < (m_max + 1) * kRep; i += blockDim.x) Vm[i] = gVm[i / kRep];
   if (basis_smem > 0) {
-    const size_t off = ((size_t)(m_max + 1) * sizeof(T) + 15) & ~(size_t)15;
+    const size_t off = ((size_t)(m_max + 1) * kRep * sizeof(T) + 15) & ~(size_t)15;
     char4* sb = reinterpret_cast<char4*>(smem + off);
     for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
     src.basis = sb;
   }
   __syncthreads();
+  const T* Vl = Vm + (threadIdx.x & (kRep - 1));  // this lane's copy
   unsigned c0 = 0, c1 = 0, c2 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = 8;  // 8 x 16 B streaming loads in flight per thread before any use
+  constexpr int U = 8;  // 8 streaming loads in flight per thread before any use
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + (U - 1) * stride < n; i += U * stride) {
     int4 v[U];
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
       c0 += f[u] == kNonCons;
       c1 += f[u] == kQZero;
       c2 += f[u] == kRange;
-      __stcs(out + i + u * stride, f[u] ? T(0) : Vm[m[u]]);
+      __stcs(out + i + u * stride, f[u] ? T(0) : Vl[m[u] * kRep]);
     }
   }
   for (; i < n; i += stride) {
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __rest
     c0 += f == kNonCons;
     c1 += f == kQZero;
     c2 += f == kRange;
-    __stcs(out + i, f ? T(0) : Vm[__dp4a(qa, qa, 0u)]);
+    __stcs(out + i, f ? T(0) : Vl[__dp4a(qa, qa, 0u) * kRep]);
   }
   c0 = __reduce_add_sync(kFull, c0);
   c1 = __reduce_add_sync(kFull, c1);
@@ -525,12 +530,17 @@ static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned lo
   const T* Vm;
   if constexpr (sizeof(T) == 4) Vm = reinterpret_cast<const T*>(t->d.Vm32);
   else Vm = reinterpret_cast<const T*>(t->d.Vm64);
-  const size_t tb = (((size_t)(t->m_max + 1) * sizeof(T)) + 15) & ~(size_t)15;
-  if (tb > kSmemCap) return CC_ERR_RANGE;
+  const size_t tb1 = (((size_t)(t->m_max + 1) * sizeof(T)) + 15) & ~(size_t)15;
+  if (tb1 > kSmemCap) return CC_ERR_RANGE;
+  // the replicated table when it and the basis fit in 96 KB (two 512-thread blocks per SM)
+  constexpr int kRep = 16;
+  const size_t tbr = (((size_t)(t->m_max + 1) * kRep * sizeof(T)) + 15) & ~(size_t)15;
+  const bool rep = tbr + (uses_basis ? (size_t)t->Nb * 4 : 0) <= 96 * 1024;
+  const size_t tb = rep ? tbr : tb1;
   int basis_smem = 0;
-  if (uses_basis && tb + (size_t)t->Nb * 4 <= 48 * 1024) basis_smem = t->Nb;
+  if (uses_basis && tb + (size_t)t->Nb * 4 <= (rep ? 96 * 1024 : 48 * 1024)) basis_smem = t->Nb;
   const size_t smem = tb + (size_t)basis_smem * 4;
-  auto kern = k_col<T, Src>;
+  auto kern = rep ? k_col<T, Src, kRep> : k_col<T, Src, 1>;
   int blocks = 0;
   CC_TRY(grid_for(kern, 512, smem, (n + 7) / 8, &blocks));
   kern<<<blocks, 512, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);

@@ -5,7 +5,8 @@
 // (0, alpha_c^{-1/2}]; d alpha = -2 t^{-3} dt, so a Gauss-Legendre point (t, w_t) becomes
 // the node alpha = 1/t^2 with weight 2 w_t / t^3 (the printed Eq. 13 weight is garbled).
 // Eq. 12 and the Table I discussion: Gauss-Legendre on [0, alpha_c], optionally split
-// geometrically at alpha_c 5^-k.  Eq. 14: one node sum over both intervals.
+// geometrically at alpha_c rho^-k (the paper's Mesh 2: rho = 5).  Eq. 14: one node sum over
+// both intervals.
 // Sec. III: for planewaves the per-axis tables depend on one index difference only.
 //
 // Gauss-Legendre points: Newton iteration on the three-term Legendre recurrence
@@ -237,14 +238,15 @@ __global__ void k_dbar(const double* WDm64, int S_eff, int Mg, double* D64, floa
 
 // ---------------------------------------------------------------- host helpers
 // Host copy of the node set of a mesh (same construction as k_mesh_nodes).
-static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, std::vector<double>& a,
-                      std::vector<double>& w);
+static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, double ratio,
+                      std::vector<double>& a, std::vector<double>& w);
 
 // max_m |sum_s w_s exp(-a_s m) - 1/m| m over m_k = 1 + floor((12R^2 - 1) k^3 / 95^3),
 // k = 0..95: the relative error of the node sum of 1/m (periodic kernel, index units)
-static double mesh_error(int S, int n_sub, int q_tail, int R) {
+static double mesh_error(int S, int n_sub, int q_tail, int R, double alpha_c = 1.0,
+                         double ratio = 5.0) {
   std::vector<double> a, w;
-  host_mesh(S, n_sub, q_tail, 1.0, a, w);
+  host_mesh(S, n_sub, q_tail, alpha_c, ratio, a, w);
   const long long top = 12LL * R * R - 1;
   long long prev = -1;
   double worst = 0.0;
@@ -314,6 +316,8 @@ cc_status resolve_params(const cc_table_params* in, cc_table_params* out) {
   if (p.n_sub > 30) return CC_ERR_RANGE;
   if (p.q_tail < 0 || p.q_tail >= p.S) return CC_ERR_ARG;
   if (!(p.alpha_c > 0.0)) p.alpha_c = 1.0;
+  if (!(p.ratio > 1.0)) p.ratio = 5.0;
+  if (!std::isfinite(p.alpha_c) || !std::isfinite(p.ratio)) return CC_ERR_ARG;
   if (p.prune_tol < 0.0) p.prune_tol = 1e-9;
   if (p.kernel == CC_KERNEL_BOX) p.prune_tol = 0.0;
   if (p.S - p.q_tail < p.n_sub + 1) return CC_ERR_ARG;  // every sub-interval gets a point
@@ -339,7 +343,7 @@ static std::vector<NodeSpec> node_specs(const cc_table_params& p) {
   std::vector<NodeSpec> out;
   std::vector<double> edges;
   edges.push_back(0.0);
-  for (int k = p.n_sub; k >= 1; --k) edges.push_back(p.alpha_c * pow(5.0, -k));
+  for (int k = p.n_sub; k >= 1; --k) edges.push_back(p.alpha_c * pow(p.ratio, -k));
   edges.push_back(p.alpha_c);
   const int n1 = p.S - p.q_tail, ns = p.n_sub + 1;
   for (int i = 0; i < ns; ++i) {
@@ -350,13 +354,14 @@ static std::vector<NodeSpec> node_specs(const cc_table_params& p) {
   return out;
 }
 
-static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, std::vector<double>& a,
-                      std::vector<double>& w) {
+static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, double ratio,
+                      std::vector<double>& a, std::vector<double>& w) {
   cc_table_params p{};
   p.S = S;
   p.n_sub = n_sub;
   p.q_tail = q_tail;
   p.alpha_c = alpha_c;
+  p.ratio = ratio;
   std::vector<NodeSpec> spec = node_specs(p);
   a.resize(spec.size());
   w.resize(spec.size());
@@ -599,7 +604,7 @@ cc_status build_tables_internal(const cc_table_params* params, cudaStream_t st, 
 // little-endian: "CCTB" u32 version | params | S, S_eff | alpha[S] w[S] part[S] kept[S] |
 // T64[S_eff][Dmax+1] | u64 FNV-1a of everything before it
 static const uint32_t kMagic = 0x42544343u;  // "CCTB"
-static const uint32_t kVersion = 1;
+static const uint32_t kVersion = 2;  // 2: parameters carry the sub-interval ratio
 
 static uint64_t fnv1a(const std::vector<uint8_t>& b) {
   uint64_t h = 1469598103934665603ull;
@@ -678,6 +683,100 @@ cc_status cc_mesh_for_error(int R, double target, int S_max, int* S, int* n_sub,
   return CC_ERR_RANGE;
 }
 
+// Mesh tuning for a stated periodic-kernel error (Sec. II: the split point alpha_c and the
+// sub-intervals decide how many nodes the accuracy needs).  Candidates: sub-interval ratio
+// rho in {3, 4, 5, 6, 8}, alpha_c in {0.5, 1, 2} (index units), n_sub = max(1,
+// floor(log_rho(12 R^2)) - 1) (from the smallest split edge alpha_c rho^-n_sub near
+// 1 / (12 R^2)) and the next one, q_tail in 3 .. max(3, round(0.45 S)) with
+// S - q_tail >= n_sub + 1; node counts S from max(2, floor(0.8 S_d)) up to S_d, where S_d is
+// cc_mesh_for_error's count for the same target (which the default rho = 5, alpha_c = 1
+// mesh reaches).  The first S whose best candidate reaches the target wins; within an S the
+// smallest error wins (errors floored at 1e-10, a candidate replaces the best only when
+// smaller by more than 0.1 %, visiting rho, alpha_c, n_sub, q_tail ascending).
+static const double kTuneRatios[] = {3.0, 4.0, 5.0, 6.0, 8.0};
+static const double kTuneAlphas[] = {0.5, 1.0, 2.0};
+
+static bool mesh_tune(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
+                      double* alpha_c, double* ratio, double* err) {
+  int Sd = -1, nd = -1, qd = -1;
+  for (int s = 2; s <= S_max; ++s) {
+    int n = -1, q = -1;
+    default_mesh(s, R, &n, &q);
+    if (mesh_error(s, n, q, R) <= target) {
+      Sd = s;
+      nd = n;
+      qd = q;
+      break;
+    }
+  }
+  if (Sd < 0) return false;
+  const double m = 12.0 * R * R;
+  for (int s = std::max(2, (int)(0.8 * Sd)); s <= Sd; ++s) {
+    double best = -1.0, bestraw = 0.0;
+    int bn = -1, bq = -1;
+    double ba = 1.0, br = 5.0;
+    for (double rho : kTuneRatios)
+      for (double ac : kTuneAlphas) {
+        const int r = std::max(1, (int)floor(log(m) / log(rho)) - 1);
+        for (int n = r; n <= r + 1; ++n)
+          for (int q = 3; q <= std::max(3, (int)lrint(0.45 * s)); ++q) {
+            if (s - q < n + 1) continue;
+            const double raw = mesh_error(s, n, q, R, ac, rho);
+            const double e = std::max(raw, 1e-10);
+            if (best < 0 || e < best * (1.0 - 1e-3)) {
+              best = e;
+              bestraw = raw;
+              bn = n;
+              bq = q;
+              ba = ac;
+              br = rho;
+            }
+          }
+      }
+    if (bn >= 0 && bestraw <= target) {
+      *S = s;
+      *n_sub = bn;
+      *q_tail = bq;
+      *alpha_c = ba;
+      *ratio = br;
+      *err = bestraw;
+      return true;
+    }
+  }
+  // S_d itself with the default mesh reaches the target
+  *S = Sd;
+  *n_sub = nd;
+  *q_tail = qd;
+  *alpha_c = 1.0;
+  *ratio = 5.0;
+  *err = mesh_error(Sd, nd, qd, R);
+  return true;
+}
+
+cc_status cc_mesh_tune(int R, double target, int S_max, int* S, int* n_sub, int* q_tail,
+                       double* alpha_c, double* ratio, double* err) {
+  if (!S || !n_sub || !q_tail || !alpha_c || !ratio || !(target > 0.0) || !std::isfinite(target))
+    return CC_ERR_ARG;
+  if (R < 1 || R > kMaxR || S_max < 2 || S_max > kMaxS) return CC_ERR_RANGE;
+  double e = 0.0;
+  if (!mesh_tune(R, target, S_max, S, n_sub, q_tail, alpha_c, ratio, &e)) return CC_ERR_RANGE;
+  if (err) *err = e;
+  return CC_OK;
+}
+
+cc_status cc_build_tables_for_error(int kernel, int R, double L, double target, int S_max,
+                                    void* stream, cc_tables* out) {
+  if (!out) return CC_ERR_ARG;
+  cc_table_params p{};
+  p.kernel = kernel;
+  p.R = R;
+  p.L = L;
+  p.prune_tol = -1.0;
+  double e = 0.0;
+  CC_TRY(cc_mesh_tune(R, target, S_max, &p.S, &p.n_sub, &p.q_tail, &p.alpha_c, &p.ratio, &e));
+  return build_tables_internal(&p, as_stream(stream), true, out);
+}
+
 cc_status cc_basis(int R, int* Nb, int8_t* vec_host) {
   if (!Nb) return CC_ERR_ARG;
   if (R < 1 || R > kMaxR) return CC_ERR_RANGE;
@@ -701,6 +800,7 @@ cc_status cc_tables_info(cc_tables t, cc_tables_info_t* info) {
   info->q_tail = t->p.q_tail;
   info->L = t->p.L;
   info->alpha_c = t->p.alpha_c;
+  info->ratio = t->p.ratio;
   info->prune_tol = t->p.prune_tol;
   info->S_eff = t->S_eff;
   info->Nb = t->Nb;

@@ -128,7 +128,8 @@ __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uin
   }
 }
 
-template <bool kHalf, bool kMmaA>
+// kX1: hi * hi products only (no lo-plane correction; a diagnostic, bf16)
+template <bool kHalf, bool kMmaA, bool kX1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_slab(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
               Args g) {
@@ -253,13 +254,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           constexpr uint64_t kPl = kPlane >> 4;
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           const uint32_t acc = m > ms ? 1u : 0u;
-          mma_x3_w(d, dT + o, dR + o, kPl, kPl, idesc1, acc);
+          if constexpr (kX1) mma_x1_w(d, dT + o, dR + o, idesc1, acc);
+          else mma_x3_w(d, dT + o, dR + o, kPl, kPl, idesc1, acc);
         }
         if constexpr (kMmaA) {
 #pragma unroll
           for (int m = 0; m < 4; ++m)
-            if (m < nh)
-              mma_x2_ts_w(d, tmem + kFhi + 8u * m, tmem + kFlo + 8u * m, dP + 2u * m, idesc1);
+            if (m < nh) {
+              if constexpr (kX1) mma_x1_ts_w(d, tmem + kFhi + 8u * m, dP + 2u * m, idesc1, 1u);
+              else mma_x2_ts_w(d, tmem + kFhi + 8u * m, tmem + kFlo + 8u * m, dP + 2u * m,
+                               idesc1);
+            }
         }
       };
       auto mma2 = [&](uint32_t tb, int j, bool first) {
@@ -273,7 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t o = (uint64_t)((m >> 2) * 2 * (kPlane >> 4) + 2 * (m & 3));
           // U piece of z = 16 m ..: columns 16 (m - zs / 16) .., 8 hi then 8 lo
           const uint32_t aH = a0 + (uint32_t)(16 * m);
-          mma_x3_ts_w(d, aH, dT + o, kPl, idesc2, (first && m == ms) ? 0u : 1u);
+          if constexpr (kX1) mma_x1_ts_w(d, aH, dT + o, idesc2, (first && m == ms) ? 0u : 1u);
+          else mma_x3_ts_w(d, aH, dT + o, kPl, idesc2, (first && m == ms) ? 0u : 1u);
         }
       };
       bool ok = all(!s_abort);
@@ -944,7 +950,7 @@ void tc_slab_free(void* p) {
 
 cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map_lo, int* err,
                       int stall_test, int R_F, float* eps, double* Ex, cudaStream_t st,
-                      bool half) {
+                      bool half, int x1) {
   TcSlabWs* w = reinterpret_cast<TcSlabWs*>(ws);
   if (!w || !tc_slab_supported(t) || R_F > 63) return CC_ERR_NOTSUPP;
   const int S = t->S_eff, Mg = t->Mg, R = t->p.R;
@@ -989,38 +995,39 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
   const uint32_t smem = slab_smem_bytes(R_F);
   static uint32_t attr = 0;
   if (attr < smem) {
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)slab_smem_bytes(63)));
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)slab_smem_bytes(63)));
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)slab_smem_bytes(63)));
-    CC_CUDA(cudaFuncSetAttribute(k_tc_slab<true, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)slab_smem_bytes(63)));
+    const void* ks[] = {(const void*)k_tc_slab<false, false, false>,
+                        (const void*)k_tc_slab<false, true, false>,
+                        (const void*)k_tc_slab<true, false, false>,
+                        (const void*)k_tc_slab<true, true, false>,
+                        (const void*)k_tc_slab<false, false, true>,
+                        (const void*)k_tc_slab<false, true, true>};
+    for (const void* k : ks)
+      CC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)slab_smem_bytes(63)));
     attr = slab_smem_bytes(63);
   }
   // the A term on the tensor cores where the band leaves tensor memory free for F_s
   const bool mma_a = periodic && ((R + R_F + 16) & ~15) - ((R - R_F) & ~15) <= kMmaABand;
-  if (half) {
+  if (half) {  // fp16x3 (the hi * hi diagnostic is a bf16 one)
     const CUtensorMap& mh = *reinterpret_cast<const CUtensorMap*>(w->map16_hi);
     const CUtensorMap& ml = *reinterpret_cast<const CUtensorMap*>(w->map16_lo);
     if (mma_a)
-      k_tc_slab<true, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+      k_tc_slab<true, true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
     else
-      k_tc_slab<true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+      k_tc_slab<true, false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   } else {
     const CUtensorMap& mh =
         *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_hi : map_hi);
     const CUtensorMap& ml =
         *reinterpret_cast<const CUtensorMap*>(w->T128[0] ? (const void*)w->map_lo : map_lo);
-    if (mma_a)
-      k_tc_slab<false, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    if (mma_a && x1)
+      k_tc_slab<false, true, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    else if (mma_a)
+      k_tc_slab<false, true, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+    else if (x1)
+      k_tc_slab<false, false, true><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
     else
-      k_tc_slab<false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
+      k_tc_slab<false, false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   }
   k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, half ? w->FB16 : w->FB,
                                                              R, R_F, S,

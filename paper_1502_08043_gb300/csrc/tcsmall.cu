@@ -174,7 +174,8 @@ __device__ __forceinline__ void mma_x2_ss_w(uint32_t tmem_d, uint64_t a, uint64_
       : "memory");
 }
 
-template <bool kPeriodic, bool kBatch>
+// kX1: hi * hi products only (no lo-plane correction; a diagnostic of single boxes)
+template <bool kPeriodic, bool kBatch, bool kX1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tcs(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
           const __grid_constant__ CUtensorMap mFh, const __grid_constant__ CUtensorMap mFl,
@@ -328,14 +329,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t dA = sdesc(base + kOffA + k * 2 * kPl128);
       const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
 #pragma unroll 1
-      for (int m = q.ms; m < q.me; ++m)
-        mma_x3_w(d, dA + 2u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, q.idesc1,
-                 m > q.ms ? 1u : 0u);
+      for (int m = q.ms; m < q.me; ++m) {
+        if constexpr (kX1) mma_x1_w(d, dA + 2u * m, dT + 2u * m, q.idesc1, m > q.ms ? 1u : 0u);
+        else mma_x3_w(d, dA + 2u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, q.idesc1,
+                      m > q.ms ? 1u : 0u);
+      }
       if constexpr (kPeriodic) {
         const uint64_t dF = sdesc(base + kOffF + k * 2 * kPl64);
 #pragma unroll 1
-        for (int m = 0; m < q.nh; ++m)
-          mma_x2_ss_w(d, dP + 2u * m, dF + 2u * m, kPl64 >> 4, q.idesc1, 1u);
+        for (int m = 0; m < q.nh; ++m) {
+          if constexpr (kX1) mma_x1_w(d, dP + 2u * m, dF + 2u * m, q.idesc1, 1u);
+          else mma_x2_ss_w(d, dP + 2u * m, dF + 2u * m, kPl64 >> 4, q.idesc1, 1u);
+        }
       }
     };
     auto mma2 = [&](uint32_t i, bool first, const Geo& q) {
@@ -343,9 +348,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t dU = sdesc_mn(base + kOffU + k * 2 * kPl128);
       const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
 #pragma unroll 1
-      for (int m = q.ms; m < q.me; ++m)
-        mma_x3_w(tmem + 128u, dU + 128u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4, q.idesc2,
-                 (first && m == q.ms) ? 0u : 1u);
+      for (int m = q.ms; m < q.me; ++m) {
+        const uint32_t acc = (first && m == q.ms) ? 0u : 1u;
+        if constexpr (kX1) mma_x1_w(tmem + 128u, dU + 128u * m, dT + 2u * m, q.idesc2, acc);
+        else mma_x3_w(tmem + 128u, dU + 128u * m, dT + 2u * m, kPl128 >> 4, kPl64 >> 4,
+                      q.idesc2, acc);
+      }
     };
     bool ok = all(!s_abort);
     uint32_t pc = 0, segc = 0;
@@ -838,12 +846,11 @@ int sm_count() {
 cc_status set_smem_attrs() {
   static bool done = false;
   if (done) return CC_OK;
-  CC_CUDA(cudaFuncSetAttribute(k_tcs<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemBytes));
-  CC_CUDA(cudaFuncSetAttribute(k_tcs<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemBytes));
-  CC_CUDA(cudaFuncSetAttribute(k_tcs<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemBytes));
+  const void* ks[] = {(const void*)k_tcs<true, false, false>, (const void*)k_tcs<false, false, false>,
+                      (const void*)k_tcs<true, false, true>, (const void*)k_tcs<false, false, true>,
+                      (const void*)k_tcs<true, true, false>};
+  for (const void* k : ks)
+    CC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   done = true;
   return CC_OK;
 }
@@ -945,7 +952,7 @@ cc_status tc_small_alloc(cc_tables t, void** out) {
 }
 
 cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F, float* eps,
-                       double* Ex, cudaStream_t st) {
+                       double* Ex, cudaStream_t st, int x1) {
   TcSmallWs* w = reinterpret_cast<TcSmallWs*>(ws);
   if (!w || !tc_small_supported(t) || R_F > 31) return CC_ERR_NOTSUPP;
   const int S = t->S_eff, Mg = t->Mg, R = t->p.R;
@@ -974,10 +981,14 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
   const CUtensorMap& tl = *reinterpret_cast<const CUtensorMap*>(w->map_tl);
   const CUtensorMap& fh = *reinterpret_cast<const CUtensorMap*>(w->map_fh);
   const CUtensorMap& fl = *reinterpret_cast<const CUtensorMap*>(w->map_fl);
-  if (periodic)
-    k_tcs<true, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  if (periodic && x1)
+    k_tcs<true, false, true><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  else if (periodic)
+    k_tcs<true, false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  else if (x1)
+    k_tcs<false, false, true><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   else
-    k_tcs<false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+    k_tcs<false, false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   k_tcs_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
       w->part, w->FB, R, R_F, S, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
       w->row_ex, w->ticket, Ex, err, err + 1);
@@ -1221,7 +1232,7 @@ cc_status tc_small_batch_run(void* p, int* err, float* eps, double* Ex, cudaStre
   const CUtensorMap& tl = *reinterpret_cast<const CUtensorMap*>(m->map_tl);
   const CUtensorMap& fh = *reinterpret_cast<const CUtensorMap*>(m->map_fh);
   const CUtensorMap& fl = *reinterpret_cast<const CUtensorMap*>(m->map_fl);
-  k_tcs<true, true><<<m->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
+  k_tcs<true, true, false><<<m->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   k_tcsb_finalize<<<m->slabs, 256, 0, st>>>(m->fboxes, m->slab_box, m->cta0, m->part, m->FB,
                                             m->units, m->grid, eps, m->slab_ex, m->ticket, Ex);
   CC_CUDA(cudaGetLastError());

@@ -702,6 +702,7 @@ static int tc_sm_count() {
 static int g_stall_next = 0;
 // 0: automatic, 1: step chain, 2: fused slab kernel, 3: small-grid kernel (bf16x3)
 static int g_mixed_variant = 0;
+static int g_mixed_terms = 3;  // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only (slab kernels)
 
 template <int NP, typename E>
 static cc_status launch_tc(const CUtensorMap& A, const CUtensorMap& Alo, const CUtensorMap& B,
@@ -812,7 +813,8 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
   if (precision == CC_PREC_FP16X3) {
     if (w->slab && g_mixed_variant != 1) {
       const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
-      return tc_slab_run(t, w->slab, nullptr, nullptr, w->err, stall, R_F, eps, Ex, st, true);
+      return tc_slab_run(t, w->slab, nullptr, nullptr, w->err, stall, R_F, eps, Ex, st, true,
+                         __atomic_load_n(&g_mixed_terms, __ATOMIC_ACQUIRE) == 1);
     }
     if (g_mixed_variant == 2) return CC_ERR_NOTSUPP;
     if (w->Np == 64) return run_mixed<64, __half>(t, w, w->hf, R_F, eps, Ex, st);
@@ -821,13 +823,14 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
   const int variant = __atomic_load_n(&g_mixed_variant, __ATOMIC_ACQUIRE);
   if (w->small && (variant == 0 || variant == 3)) {
     const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
-    return tc_small_run(t, w->small, w->err, stall, R_F, eps, Ex, st);
+    return tc_small_run(t, w->small, w->err, stall, R_F, eps, Ex, st,
+                        __atomic_load_n(&g_mixed_terms, __ATOMIC_ACQUIRE) == 1);
   }
   if (variant == 3) return CC_ERR_NOTSUPP;
   if (w->slab && variant != 1) {
     const int stall = __atomic_exchange_n(&g_stall_next, 0, __ATOMIC_ACQ_REL);
     return tc_slab_run(t, w->slab, &w->bf.mTT[0], &w->bf.mTT[1], w->err, stall, R_F, eps, Ex,
-                       st, false);
+                       st, false, __atomic_load_n(&g_mixed_terms, __ATOMIC_ACQUIRE) == 1);
   }
   if (variant == 2) return CC_ERR_NOTSUPP;
   if (w->Np == 64) return run_mixed<64, __nv_bfloat16>(t, w, w->bf, R_F, eps, Ex, st);
@@ -841,6 +844,12 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
 extern "C" cc_status cc_set_mixed_variant(int variant) {
   if (variant < 0 || variant > 3) return CC_ERR_ARG;
   __atomic_store_n(&cc::g_mixed_variant, variant, __ATOMIC_RELEASE);
+  return CC_OK;
+}
+
+extern "C" cc_status cc_set_mixed_terms(int terms) {
+  if (terms != 1 && terms != 3) return CC_ERR_ARG;
+  __atomic_store_n(&cc::g_mixed_terms, terms, __ATOMIC_RELEASE);
   return CC_OK;
 }
 

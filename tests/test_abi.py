@@ -92,3 +92,30 @@ def test_library_mesh_for_error_equals_oracle(lib):
         lib.mesh_for_error(4, 1e-30, 8)   # not reachable with 8 nodes
     with pytest.raises(lib.CoulombError):
         lib.mesh_for_error(4, -1.0, 8)
+
+
+def test_library_mesh_tune_equals_oracle(lib):
+    """Mesh tuning over the wider family (sub-interval ratio, alpha_c): library and oracle
+    pick the same mesh; it reaches the target with at most the default rule's node count,
+    and no candidate of the family with one node fewer in the searched range does."""
+    from oracle import quadrature as oq
+    for R, target in ((4, 1e-5), (13, 1e-7), (13, 1e-8)):
+        got = lib.mesh_tune(R, target, 200)
+        ref = oq.mesh_tune(R, target, 200)
+        assert ref is not None
+        assert got[:3] == ref[:3] and got[3:5] == ref[3:5], (R, target, got, ref)
+        # the two errors are the same quantity from two Gauss-Legendre constructions summed
+        # in different orders: they agree to FP64 rounding of sums of order 1
+        assert got[5] <= target and abs(got[5] - ref[5]) <= 1e-13
+        S_d = oq.mesh_for_error(R, target, 200)[0]
+        assert got[0] <= S_d
+        # the mesh itself: its error recomputed from the oracle's nodes
+        assert oq.mesh_error(got[0], got[1], got[2], R, got[3], got[4]) <= target
+    # ratio 5 and alpha_c 1 give the nodes of the paper's geometric split (Mesh 2 edges)
+    a1, w1, _ = oq.laplace_mesh(48, 7, 8)
+    a2, w2, _ = oq.laplace_mesh(48, 7, 8, 1.0, 5.0)
+    assert np.array_equal(a1, a2) and np.array_equal(w1, w2)
+    edges = oq.interval1_edges(3, 2.0, 4.0)
+    assert np.allclose(edges, [0.0, 2.0 / 64, 2.0 / 16, 2.0 / 4, 2.0], rtol=0, atol=0)
+    with pytest.raises(lib.CoulombError):
+        lib.mesh_tune(4, 1e-30, 8)

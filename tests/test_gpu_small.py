@@ -118,3 +118,26 @@ def test_small_kernel_rejects_large_grids(dev):
     finally:
         assert cc.lib().cc_set_mixed_variant(0) == 0
     t.free()
+
+
+@pytest.mark.parametrize("R,R_F,S", [(13, 8, 64), (33, 21, 64)])
+def test_lo_plane_correction(dev, R, R_F, S):
+    """What the split precision buys: with the lo planes (hi*hi + hi*lo + lo*hi) the
+    tensor-core exchange is within 1e-4 of the FP64 node sum; with hi*hi only (the plain
+    bf16 product) it is off by about the bf16 rounding, 2^-9 .. 2^-8 relative, and at least
+    ten times worse.  Grid side 27 runs the small-grid kernel, 67 the 128-row kernel."""
+    import paper_1502_08043_gb300 as cc
+    L = 30.0
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    a, w = oracle_nodes(R, S)
+    ref = ox.eps_separable_grid(R, R_F, L, a, w)
+    g3, _ = _run(t, R_F, dev, 0)
+    assert cc.lib().cc_set_mixed_terms(1) == 0
+    try:
+        g1, _ = _run(t, R_F, dev, 0)
+    finally:
+        assert cc.lib().cc_set_mixed_terms(3) == 0
+    e3, e1 = rel_err(g3, ref), rel_err(g1, ref)
+    assert e3 < TOL_MIXED and e1 > 10 * e3 and 1e-4 < e1 < 1e-2, (e3, e1)
+    assert cc.lib().cc_set_mixed_terms(2) == 1
+    t.free()

@@ -86,3 +86,37 @@ def test_parameter_errors(dev):
         with pytest.raises(cc.CoulombError) as e:
             cc.build_tables(**args)
         assert e.value.status == st, kw
+
+
+def test_build_tables_for_error():
+    """Tables built for a stated method error: the library's nodes are the oracle's tuned
+    mesh (mesh_tune), pruned as usual; separable lookups on them reproduce the exact kernel
+    1/(pi L |q|^2) to the stated error (plus FP32 rounding) on seeded conserving quadruples."""
+    import torch
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+    from gpu_common import need_gpu
+    from oracle import reconstruct as orc
+    dev = need_gpu()
+    R, L, target = 13, 20.0, 1e-8
+    t = cc.build_tables_for_error("periodic", R=R, L=L, target=target)
+    S, n_sub, q_tail, ac, ratio, err = oq.mesh_tune(R, target, 1024)
+    info = t.info
+    assert (info["S"], info["n_sub"], info["q_tail"]) == (S, n_sub, q_tail)
+    assert info["alpha_c"] == ac and info["ratio"] == ratio
+    a, w, part, kept = t.nodes()
+    ao, wo, _ = oq.laplace_mesh(S, n_sub, q_tail, ac, ratio)
+    assert np.allclose(a, ao, rtol=1e-13) and np.allclose(w, wo, rtol=1e-12)
+    assert np.array_equal(kept, oq.prune_periodic(ao, wo, R, 1e-9))
+    q = ci.quads(R, 0, 200000)
+    exact, _ = orc.reconstruct(q, R, L, "exact")
+    out = torch.empty(len(q), dtype=torch.float64, device=dev)
+    cc.reconstruct_integrals(t, torch.from_numpy(q).to(dev), out, lookup="separable")
+    got = out.cpu().numpy()
+    nz = exact != 0
+    assert np.max(np.abs(got[nz] - exact[nz]) / exact[nz]) < target + 1e-12
+    out32 = torch.empty(len(q), dtype=torch.float32, device=dev)
+    cc.reconstruct_integrals(t, torch.from_numpy(q).to(dev), out32, lookup="separable")
+    g32 = out32.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g32[nz] - exact[nz]) / exact[nz]) < target + 1e-6
+    t.free()

@@ -3,15 +3,17 @@
 It exists for callers that cannot call cudaMalloc where they need the exchange sums
 (code under a framework's caching allocator that owns the device memory, latency-
 critical loops that cannot afford cudaMalloc's implicit synchronisation).  It must give
-the same sums as the ordinary FP32 entry point cc_exchange_sums, call after call, while
-keeping its scratch in the library's fixed device array.  This file is collected last.
+the same sums as the ordinary FP32 entry point cc_exchange_sums, call after call, and the
+FP64 oracle's, while keeping its scratch in the library's fixed device array: the free
+device memory does not change across its calls.  This file is collected last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
-from gpu_common import TOL_FP32, need_gpu, rel_err
+from gpu_common import TOL_FP32, need_gpu, oracle_nodes, rel_err
+from oracle import exchange as ox
 
 pytestmark = pytest.mark.gpu
 
@@ -33,19 +35,27 @@ def test_noalloc_matches_existing_entry_point(R, L, S, R_F):
     dev = need_gpu()
     t = cc.build_tables("periodic", R=R, L=L, S=S)
     ref_eps, ref_Ex = _reference(cc, t, R_F, dev)
+    a, w = oracle_nodes(R, S)
+    oracle_eps = ox.eps_separable_grid(R, R_F, L, a, w).reshape(-1)
+    oracle_Ex = ox.Ex_separable_periodic(R_F, L, a, w, ox.difference_histogram(R_F, "fft"))
     Mg = t.info["Mg"]
-    for _ in range(2):   # two calls in a row through the C ABI
-        eps = torch.full((Mg ** 3,), float("nan"), dtype=torch.float32, device=dev)
-        Ex = torch.zeros(2, dtype=torch.float64, device=dev)
+    outs = [(torch.full((Mg ** 3,), float("nan"), dtype=torch.float32, device=dev),
+             torch.zeros(2, dtype=torch.float64, device=dev)) for _ in range(2)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for eps, Ex in outs:   # two calls in a row through the C ABI
         st = cc.lib().cc_exchange_sums_noalloc(
             t.handle, R_F, ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(Ex.data_ptr()),
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert st == 0
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info(dev)[0] == free0   # nothing allocated or freed
         got = eps.cpu().numpy().astype(np.float64)
         assert np.array_equal(got == 0, ref_eps == 0)
         assert rel_err(got, ref_eps) < TOL_FP32
         assert abs(Ex.cpu().numpy()[0] - ref_Ex[0]) < TOL_FP32 * abs(ref_Ex[0])
+        assert rel_err(got, oracle_eps) < TOL_FP32
+        assert abs(Ex.cpu().numpy()[0] - oracle_Ex) < TOL_FP32 * abs(oracle_Ex)
     t.free()
 
 
