@@ -684,13 +684,18 @@ def large_lookups(n=1_000_000_000, reps=3):
     ci.quads_device(63, 0, n, q)
     vals = torch.empty(n, dtype=torch.float32, device=dev)
     out = {"quadruples": n, "S_eff": t.info["S_eff"],
-           "note": "ids: every quadruple gathers 4 basis vectors from the 4.2 MB basis table "
-                   "(L2); vec: the quadruple carries its four int8x4 vectors"}
+           "note": "ids collapsed: the four ids decoded on chip from 128 KB of line hints in "
+                   "shared memory; ids separable and ids_l2gather: 4 basis vectors gathered "
+                   "from the 4.2 MB basis table (L2); vec: the quadruple carries its four "
+                   "int8x4 vectors"}
     peak, _ = _peaks()
     # the same quadruples in vector form (16 B each as well)
     vecs = torch.from_numpy(cc.basis(63)).to(dev)[q.long().view(-1)].view(n, 4, 4)
-    for fmt, qq in (("ids", q), ("vec", vecs)):
-        for lookup in ("collapsed", "separable"):
+    for fmt, qq, lookups in (("ids", q, ("collapsed", "separable")),
+                             ("ids_l2gather", q, ("collapsed",)),
+                             ("vec", vecs, ("collapsed", "separable"))):
+        cc.lib().cc_set_id_decode(0 if fmt == "ids_l2gather" else 1)
+        for lookup in lookups:
             cc.reconstruct_integrals(t, qq, vals, lookup=lookup)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -704,6 +709,7 @@ def large_lookups(n=1_000_000_000, reps=3):
             gbs = 20.0 * n / (ms * 1e-3) / 1e9
             out[f"{fmt}_{lookup}"] = {"ms": ms, "integrals_per_s": n / (ms * 1e-3),
                                       "hbm_GBps": gbs, "hbm_frac": gbs / peak}
+    cc.lib().cc_set_id_decode(1)
     # the separable lookup on tables built for a stated method error (1e-8): the tuned mesh
     # with the fewest nodes instead of the 128-node workload mesh
     tt = cc.build_tables_for_error("periodic", R=63, L=60.0, target=1e-8)
@@ -897,6 +903,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_CASES = {
+    "exchange_grid63": "bf16x3 exchange sums, |n| <= 31, R_F = 20, 96 nodes (3 calls)",
+    "exchange_grid127": "bf16x3 then FP32 exchange sums, |n| <= 63, R_F = 40, 128 nodes "
+                        "(2 calls each)",
+    "batch48": "bf16x3 exchange sums of the first 48 boxes of the batched workload (2 calls)",
+    "general2e6": "general box-kernel lookups, 9171 planewaves, 180 nodes, 2e6 uniform-id "
+                  "quadruples (3 calls)",
+    "col_ids16_2e7": "collapsed lookups of 2e7 uint16-id quadruples, |n| <= 13 (3 calls)",
+    "col_ids_1e8": "collapsed lookups of 1e8 int32-id quadruples, |n| <= 63, ids decoded on "
+                   "chip (3 calls)",
+}
+
+
+def profile_case(name):
+    """One small, fixed invocation of a hot-path kernel for an ncu capture (a few launches,
+    a few GB on the device at most); prints what ran.  No timing."""
+    import torch
+
+    import coulomb_inputs as ci
+    import paper_1502_08043_gb300 as cc
+    dev = torch.device("cuda:0")
+    if name == "exchange_grid63":
+        t = cc.build_tables("periodic", R=31, L=40.0, S=96)
+        eps = torch.empty(63 ** 3, dtype=torch.float32, device=dev)
+        Ex = torch.empty(2, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            cc.exchange_sums(t, 20, eps, Ex, precision="bf16x3")
+    elif name == "exchange_grid127":
+        t = cc.build_tables("periodic", R=63, L=60.0, S=128)
+        eps = torch.empty(127 ** 3, dtype=torch.float32, device=dev)
+        Ex = torch.empty(2, dtype=torch.float64, device=dev)
+        for prec in ("bf16x3", "fp32"):
+            for _ in range(2):
+                cc.exchange_sums(t, 40, eps, Ex, precision=prec)
+    elif name == "batch48":
+        B = cc.Batch(ci.box_params(48))
+        eps = torch.empty(int(B.offsets[-1]), dtype=torch.float32, device=dev)
+        Ex = torch.empty((B.nbox, 2), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            B.exchange(eps, Ex, precision="bf16x3")
+    elif name == "general2e6":
+        t = cc.build_tables("box", R=13, L=2.0, S=180, n_sub=0, q_tail=90)
+        n = 2_000_000
+        q = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        ci.quads_device(13, 0, n, q, stream=ci.STREAM_UNIFORM)
+        q16 = torch.where(q >= 32768, q - 65536, q).to(torch.int16)
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            cc.reconstruct_integrals(t, q16, out, lookup="general")
+    elif name in ("col_ids16_2e7", "col_ids_1e8"):
+        R, n = (13, 20_000_000) if name == "col_ids16_2e7" else (63, 100_000_000)
+        t = cc.build_tables("periodic", R=R, L=20.0 if R == 13 else 60.0,
+                            S=64 if R == 13 else 128)
+        q = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        ci.quads_device(R, 0, n, q)
+        if R == 13:
+            q = torch.where(q >= 32768, q - 65536, q).to(torch.int16)
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            cc.reconstruct_integrals(t, q, out, lookup="collapsed")
+    else:
+        raise SystemExit(f"unknown profile case {name!r}: one of {sorted(PROFILE_CASES)}")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "what": PROFILE_CASES[name]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -927,6 +999,9 @@ def main():
                     help="only run the general box-integral lookup section, print it")
     ap.add_argument("--replay-only", action="store_true",
                     help="only run the Table I / Fig. 1 replay through the GPU path, print it")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small fixed invocation of a hot-path kernel (for ncu), "
+                         "print what ran")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
@@ -934,6 +1009,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        profile_case(args.profile_case)
     elif args.mp_only:
         print(json.dumps({"mode_products": mode_products(args.mp_only, oracle_sample=0)}))
     elif args.replay_only:

@@ -234,6 +234,17 @@ cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n
                                    int lookup, int precision, void* out_dev,
                                    unsigned long long* counters_dev, void* stream);
 
+/* How the collapsed lookup finds the index vectors of ids (uint16 or int32) when the basis
+ * and the table do not fit in 48 KB of shared memory (R >= 15 in FP32, R >= 14 in FP64;
+ * not part of the paper, a comparison switch of this implementation, process-wide):
+ * 1 (the default) = decoded on chip from a table of one 32-bit hint per 32 ids staged in
+ * shared memory (the line (n_x, n_y) and place of the bucket's first id in the
+ * lexicographic basis order of Sec. III, and the next line's length; ids further on walk
+ * over whole lines), when table and hints fit in 200 KB (FP32 up to R = 63, FP64 up to
+ * R = 57); 0 = a gather from the basis table in global memory.  Results are identical.
+ * CC_ERR_ARG for any other value. */
+cc_status cc_set_id_decode(int on);
+
 /* Exchange-type pair integrals (ij|ji) = V(n_j - n_i) for basis rows
  * i = row0 .. row0 + nrows - 1 and every column j:  out_dev[nrows][Nb] (float or double
  * by precision), row major.  Diagonal of the PERIODIC kernel: 0 (q = 0 excluded). */
@@ -297,9 +308,9 @@ cc_status cc_test_stall_next_mixed(void);
  * side up to 127), 3 = the small-grid kernel (bf16x3, grid sides up to 64, two slabs per
  * 128-row MMA; CC_ERR_NOTSUPP for larger grids).  Automatic takes the small-grid kernel for
  * bf16x3 grids up to 64 and the 128-row kernel otherwise (fp16x3: always the 128-row
- * kernel); batches (bf16x3) take the batched small-grid kernel on 0 and 3, the batched
- * 128-row kernel on 2, the chain on 1.  The setting is read when a batch's graph is
- * captured.  CC_ERR_ARG for any other value. */
+ * kernel); batches (bf16x3, grid sides up to 49) take the batched small-grid kernel, or
+ * the chain on 1.  The setting is read when a batch's graph is captured.  CC_ERR_ARG for any
+ * other value. */
 cc_status cc_set_mixed_variant(int variant);
 
 /* Split products per mode product in the single-box bf16x3 tensor-core exchange (through

@@ -94,6 +94,7 @@ SIGNATURES = {
     "cc_test_stall_next_mixed": (_I, []),
     "cc_set_mixed_variant": (_I, [_I]),
     "cc_set_simt_variant": (_I, [_I]),
+    "cc_set_id_decode": (_I, [_I]),
     "cc_set_mixed_terms": (_I, [_I]),
     "cc_batch_create": (_I, [ctypes.POINTER(Box), _I, _P, ctypes.POINTER(_P)]),
     "cc_batch_info": (_I, [_P, _P, _P, _P, _P]),

@@ -23,8 +23,8 @@ LIB = os.path.join(HERE, "libcoulomb.so")
 GEN_SRC = os.path.join(ROOT, "coulomb_inputs", "gen.cu")
 GEN_LIB = os.path.join(ROOT, "coulomb_inputs", "libccgen.so")
 
-SOURCES = ["tables.cu", "reconstruct.cu", "exchange.cu", "umma.cu", "tcslab.cu", "tcslab_batch.cu",
-           "batched.cu", "simtslab.cu", "tcsmall.cu"]
+SOURCES = ["tables.cu", "reconstruct.cu", "exchange.cu", "umma.cu", "tcslab.cu", "batched.cu",
+           "simtslab.cu", "tcsmall.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -46,6 +46,7 @@ struct DevTables {
   double* Vm64 = nullptr;     // [m_max+1] collapsed pref sum_s w_s exp(-a_s m) (PERIODIC)
   float* Vm32 = nullptr;
   int8_t* basis = nullptr;    // [Nb][4]
+  uint32_t* idhint = nullptr; // [ceil(Nb / 64)] decode hints of the ids (make_id_hint)
   // dense Mg x Mg Toeplitz matrices for the mode products
   double* Tm64 = nullptr;     // [S_eff][Mg][Mg]  T_s[|a-b|]
   double* WDm64 = nullptr;    // [S_eff][Mg][Mg]  w_s D_s (D = T - I periodic, T box)
@@ -102,6 +103,15 @@ namespace cc {
 cc_status resolve_params(const cc_table_params* in, cc_table_params* out);
 void default_mesh(int S, int R, int* n_sub, int* q_tail);
 std::vector<int8_t> make_basis(int R);
+// Decode hints for basis ids in lexicographic (n_x, n_y, n_z) order, one per bucket of 32
+// ids; entry b describes id 32 b, the first id of bucket b, on its line (x, y) of
+// z = -z_max .. z_max, z_max = floor(sqrt(R^2 - x^2 - y^2)):
+//   bits 0-6  x + R,  bits 7-13  y + R,  bits 14-20  z + R of id 32 b,
+//   bits 21-25  min(z_max - z, 31)  (ids after id 32 b that are still on its line),
+//   bits 26-31  z_max of the next line when it is (x, y + 1), else 63 (also when that
+//               z_max is 63, which only costs a walk)
+constexpr int kIdHintShift = 5;
+std::vector<uint32_t> make_id_hint(int R);
 cc_status build_tables_internal(const cc_table_params* params, cudaStream_t st,
                                 bool workspaces, cc_tables* out);
 // batched.cu
@@ -150,12 +160,4 @@ bool simt_slab_supported(cc_tables t);
 cc_status simt_slab_alloc(cc_tables t, void** out);
 void simt_slab_free(void* ws);
 cc_status simt_slab_run(cc_tables t, void* ws, int R_F, float* eps, double* Ex, cudaStream_t st);
-// tcslab_batch.cu: a batch of boxes through the batched form of the slab kernel, over the
-// step chain's concatenated T planes ([rows][Np] bf16; box b's node 0 at row t_row0[b])
-cc_status tc_slab_batch_create(const std::vector<cc_tables>& tabs, const std::vector<int>& R_F,
-                               const std::vector<long long>& eps_off, void* tt_hi, void* tt_lo,
-                               long long tt_rows, const std::vector<long long>& t_row0, int Np,
-                               void** out);
-cc_status tc_slab_batch_run(void* p, int* err, float* eps, double* Ex, cudaStream_t st);
-void tc_slab_batch_free(void* p);
 }  // namespace cc

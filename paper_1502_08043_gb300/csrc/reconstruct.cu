@@ -47,6 +47,7 @@ __device__ __forceinline__ int classify(uint32_t a, uint32_t b, uint32_t c, uint
 }
 
 struct IdsSrc {
+  static constexpr bool kHint = false;
   const int4* q;
   const char4* basis;
   int Nb;
@@ -81,6 +82,7 @@ struct IdsSrc {
 
 // uint16 ids: 8 bytes per quadruple (basis of at most 65536 functions)
 struct Ids16Src {
+  static constexpr bool kHint = false;
   const uint2* q;
   const char4* basis;
   int Nb;
@@ -114,6 +116,7 @@ struct Ids16Src {
 };
 
 struct VecSrc {
+  static constexpr bool kHint = false;
   const int4* q;
   const char4* basis;  // unused
   int R2;
@@ -142,6 +145,96 @@ struct VecSrc {
     w[2] = (uint32_t)v.z;
     w[3] = (uint32_t)v.w;
     return in_sphere(w[0]) && in_sphere(w[1]) && in_sphere(w[2]) && in_sphere(w[3]);
+  }
+};
+
+// Ids of a basis too large for shared memory (|n| <= 63: 1047331 functions, 4.2 MB) are
+// decoded on chip from the hint of their bucket of 32 ids (make_id_hint), staged in shared
+// memory, instead of a random gather from the basis in L2.  The basis is the lexicographic
+// list of the lines (x, y) inside the sphere, line (x, y) holding the ids of
+// z = -z_max .. z_max, z_max = floor(sqrt(R^2 - x^2 - y^2)).  The hint places the bucket's
+// first id on its line and gives the next line's z_max; ids further on (about 0.2 % at
+// |n| <= 63) walk over whole lines, at most 31 of them.  The words carry every component
+// offset by +R (bytes 0 .. 126): the bookkeeping only takes differences of words, so the
+// offsets cancel.
+__device__ __forceinline__ int isqrt_small(int v) {  // floor(sqrt(v)), 0 <= v < 2^24
+  int h = v > 0 ? (int)((float)v * rsqrtf((float)v)) : 0;
+  if (h * h > v) --h;
+  if ((h + 1) * (h + 1) <= v) ++h;
+  return h;
+}
+
+__device__ __noinline__ uint32_t id_vector_walk(int R, int x, int y, int pos) {
+  // pos = place of the id counted from the first id of the line after (x, y)
+  for (int it = 0; it < 32; ++it) {
+    ++y;
+    int r2 = R * R - x * x - y * y;
+    if (r2 < 0) {  // past the plane's last line: first line of the next plane
+      ++x;
+      y = -isqrt_small(R * R - x * x);
+      r2 = R * R - x * x - y * y;
+    }
+    const int zm = isqrt_small(r2);
+    if (pos <= 2 * zm) return (uint32_t)(x + R) | (uint32_t)(y + R) << 8 |
+                              (uint32_t)(pos - zm + R) << 16;
+    pos -= 2 * zm + 1;
+  }
+  return 0u;  // not reached for ids below Nb
+}
+
+__device__ __forceinline__ uint32_t id_vector(const uint32_t* hint, int R, int id) {
+  const uint32_t e = hint[id >> kIdHintShift];
+  const int k = id & ((1 << kIdHintShift) - 1);
+  const int rest = (int)((e >> 21) & 31u), zm1 = (int)(e >> 26);
+  const int k1 = k - rest - 1;  // place on the next line (x, y + 1) when >= 0
+  const bool next = k1 >= 0;
+  if (next && (zm1 == 63 || k1 > 2 * zm1))
+    return id_vector_walk(R, (int)(e & 127u) - R, (int)((e >> 7) & 127u) - R, k1);
+  const uint32_t xy = (e & 127u) | ((e << 1) & 0x7f00u);  // bytes x + R, y + R
+  const uint32_t zR = next ? (uint32_t)(R - zm1 + k1) : ((e >> 14) & 127u) + (uint32_t)k;
+  return xy + (next ? 256u : 0u) + (zR << 16);
+}
+
+template <bool k16>  // uint16 ids (8 bytes per quadruple) or int32 ids (16 bytes)
+struct IdsDecSrc {
+  static constexpr bool kHint = true;
+  const void* q;
+  const uint32_t* hint;  // [nhint], moved to shared memory by the kernel
+  int Nb, R, nhint;
+  __device__ __forceinline__ int4 raw(int64_t i) const {
+    if constexpr (k16) {
+      const uint2 v = __ldcs(reinterpret_cast<const uint2*>(q) + i);
+      return make_int4((int)(v.x & 0xffffu), (int)(v.x >> 16), (int)(v.y & 0xffffu),
+                       (int)(v.y >> 16));
+    } else {
+      return ld_stream(reinterpret_cast<const int4*>(q) + i);
+    }
+  }
+  __device__ __forceinline__ bool in_range(const int4 v) const {
+    return (unsigned)v.x < (unsigned)Nb && (unsigned)v.y < (unsigned)Nb &&
+           (unsigned)v.z < (unsigned)Nb && (unsigned)v.w < (unsigned)Nb;
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int decode(int64_t i, uint32_t& qa) const {
+    return classify_raw<kPeriodic>(raw(i), qa);
+  }
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_raw(const int4 v, uint32_t& qa) const {
+    if (!in_range(v)) {
+      qa = 0;
+      return kRange;
+    }
+    return classify<kPeriodic>(id_vector(hint, R, v.x), id_vector(hint, R, v.y),
+                               id_vector(hint, R, v.z), id_vector(hint, R, v.w), qa);
+  }
+  __device__ __forceinline__ bool fetch(int64_t i, uint32_t w[4]) const {
+    const int4 v = raw(i);
+    if (!in_range(v)) return false;
+    w[0] = id_vector(hint, R, v.x);
+    w[1] = id_vector(hint, R, v.y);
+    w[2] = id_vector(hint, R, v.z);
+    w[3] = id_vector(hint, R, v.w);
+    return true;
   }
 };
 
@@ -357,15 +450,19 @@ __global__ void __launch_bounds__(256) k_gen(Src src, int64_t n, const T* __rest
 // and lane l reading copy l % kRep: a warp's gathers of V_m then conflict at most
 // 32 / kRep ways (kRep = 16: lanes l and l + 16 share a copy), instead of landing on random
 // banks.  kRep = 1 is the plain table.
-template <typename T, typename Src, int kRep>
-__global__ void __launch_bounds__(512) k_col(Src src, int64_t n, const T* __restrict__ gVm,
+template <typename T, typename Src, int kRep, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_col(Src src, int64_t n, const T* __restrict__ gVm,
                                              int m_max, T* __restrict__ out,
                                              unsigned long long* counters, int basis_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* Vm = reinterpret_cast<T*>(smem);
   for (int i = threadIdx.x; i < (m_max + 1) * kRep; i += blockDim.x) Vm[i] = gVm[i / kRep];
-  if (basis_smem > 0) {
-    const size_t off = ((size_t)(m_max + 1) * kRep * sizeof(T) + 15) & ~(size_t)15;
+  const size_t off = ((size_t)(m_max + 1) * kRep * sizeof(T) + 15) & ~(size_t)15;
+  if constexpr (Src::kHint) {
+    uint32_t* sh = reinterpret_cast<uint32_t*>(smem + off);
+    for (int i = threadIdx.x; i < src.nhint; i += blockDim.x) sh[i] = src.hint[i];
+    src.hint = sh;
+  } else if (basis_smem > 0) {
     char4* sb = reinterpret_cast<char4*>(smem + off);
     for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
     src.basis = sb;
@@ -524,6 +621,10 @@ static cc_status launch_gen(cc_tables t, Src src, int64_t n, T* out,
   return CC_OK;
 }
 
+// 1: int32 ids of bases too large for shared memory are decoded on chip (IdsDecSrc);
+// 0: gathered from the basis in global memory (L2)
+static int g_id_decode = 1;
+
 template <typename T, typename Src>
 static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned long long* counters,
                             cudaStream_t st, bool uses_basis) {
@@ -535,15 +636,20 @@ static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned lo
   // the replicated table when it and the basis fit in 96 KB (two 512-thread blocks per SM)
   constexpr int kRep = 16;
   const size_t tbr = (((size_t)(t->m_max + 1) * kRep * sizeof(T)) + 15) & ~(size_t)15;
-  const bool rep = tbr + (uses_basis ? (size_t)t->Nb * 4 : 0) <= 96 * 1024;
+  size_t staged = uses_basis ? (size_t)t->Nb * 4 : 0;
+  if constexpr (Src::kHint) staged = (size_t)src.nhint * 4;
+  const bool rep = tbr + staged <= 96 * 1024;
   const size_t tb = rep ? tbr : tb1;
   int basis_smem = 0;
   if (uses_basis && tb + (size_t)t->Nb * 4 <= (rep ? 96 * 1024 : 48 * 1024)) basis_smem = t->Nb;
-  const size_t smem = tb + (size_t)basis_smem * 4;
-  auto kern = rep ? k_col<T, Src, kRep> : k_col<T, Src, 1>;
+  size_t smem = tb + (size_t)basis_smem * 4;
+  if constexpr (Src::kHint) smem = tb + (size_t)src.nhint * 4;
+  // decoding sources hold one 1024-thread block per SM (the hints fill shared memory)
+  constexpr int kThreads = Src::kHint ? 1024 : 512;
+  auto kern = rep ? k_col<T, Src, kRep, kThreads> : k_col<T, Src, 1, kThreads>;
   int blocks = 0;
-  CC_TRY(grid_for(kern, 512, smem, (n + 7) / 8, &blocks));
-  kern<<<blocks, 512, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);
+  CC_TRY(grid_for(kern, kThreads, smem, (n + 7) / 8, &blocks));
+  kern<<<blocks, kThreads, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }
@@ -562,13 +668,24 @@ static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int fo
       return launch_gen<T>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
     return launch_gen<T>(t, VecSrc{q, nullptr, t->p.R * t->p.R}, n, out, counters, st);
   }
+  // collapsed lookups decode ids on chip when the basis cannot be staged but the hints can
+  const size_t tbc = (((size_t)(t->m_max + 1) * sizeof(T)) + 15) & ~(size_t)15;
+  const int nhint = (t->Nb + (1 << kIdHintShift) - 1) >> kIdHintShift;
+  const bool dec = tbc + (size_t)t->Nb * 4 > 48 * 1024 && tbc + (size_t)nhint * 4 <= kSmemCap &&
+                   __atomic_load_n(&g_id_decode, __ATOMIC_ACQUIRE);
   if (format == CC_QUAD_IDS_U16) {
+    if (lookup == CC_LOOKUP_COLLAPSED && dec)
+      return launch_col<T>(t, IdsDecSrc<true>{quads, t->d.idhint, t->Nb, t->p.R, nhint}, n,
+                           out, counters, st, false);
     if (lookup == CC_LOOKUP_COLLAPSED)
       return launch_col<T>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st, true);
     if (periodic) return launch_sep<T, Ids16Src, true>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
     return launch_sep<T, Ids16Src, false>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
   }
   if (lookup == CC_LOOKUP_COLLAPSED) {
+    if (format == CC_QUAD_IDS_I32 && dec)
+      return launch_col<T>(t, IdsDecSrc<false>{quads, t->d.idhint, t->Nb, t->p.R, nhint}, n,
+                           out, counters, st, false);
     if (format == CC_QUAD_IDS_I32) return launch_col<T>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st, true);
     return launch_col<T>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st, false);
   }
@@ -616,6 +733,12 @@ static cc_status pairs_t(cc_tables t, int64_t row0, int64_t nrows, int lookup, T
 }  // namespace cc
 
 using namespace cc;
+
+extern "C" cc_status cc_set_id_decode(int on) {
+  if (on != 0 && on != 1) return CC_ERR_ARG;
+  __atomic_store_n(&g_id_decode, on, __ATOMIC_RELEASE);
+  return CC_OK;
+}
 
 extern "C" cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n,
                                               int format, int lookup, int precision,

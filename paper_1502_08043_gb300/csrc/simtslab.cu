@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "slab_finalize.cuh"
 
 namespace cc {
 
@@ -44,19 +45,6 @@ struct SArgs {
   float* part;      // [Mg * nh][maxseg][kRows][kCols] partial E of a (slab, half)
 };
 
-__host__ __device__ inline int owner_cta(long long u, int units, int grid) {
-  int c = (int)((u * grid) / units);
-  while (c + 1 < grid && (long long)(c + 1) * units / grid <= u) ++c;
-  while (c > 0 && (long long)c * units / grid > u) --c;
-  return c;
-}
-
-__device__ __forceinline__ int isqrt_i(int v) {
-  int h = (int)sqrtf((float)v);
-  while (h * h > v) --h;
-  while ((h + 1) * (h + 1) <= v) ++h;
-  return h;
-}
 
 // shared memory of one CTA: Tb[nb][16 EW] | Rm[nb][16 ZW] | Ut[16 ZW][kUtStride] | ftab[64]
 // | hyz[nb][nb] (bytes)
@@ -85,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_simt_slab(SArgs g) {
   for (int i = tid; i < nb * nb; i += kThreads) {
     const int dy = i / nb - RF, dz = i % nb - RF;
     const int q = RF * RF - dy * dy - dz * dz;
-    hyz[i] = (signed char)(q >= 0 ? isqrt_i(q) : -1);
+    hyz[i] = (signed char)(q >= 0 ? isqrt_int(q) : -1);
   }
   for (int i = tid; i < nb * NCP; i += kThreads) Tb[i] = 0.0f;
   for (int i = tid; i < nb * NBP; i += kThreads) Rm[i] = 0.0f;
@@ -256,56 +244,6 @@ __global__ void k_simt_dbar(const double* Dbar, int Mg, int R, int RF, float* FB
   }
 }
 
-// one warp per grid row (x, y), four z per lane: the partials in order, + Dbar term, eps on
-// the basis sphere, FP64 row sum over the Fermi sphere (fixed butterfly order)
-__global__ void __launch_bounds__(256)
-    k_simt_finalize(const float* part, const float* FB, int R, int RF, int S, int nh, int units,
-                    int grid, int maxseg, int periodic, double pref, float* eps,
-                    double* row_ex) {
-  const int Mg = 2 * R + 1;
-  const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (y >= Mg) return;  // whole warps
-  const int xh = x * nh + y / kRows, r = y % kRows;
-  const int c0 = owner_cta((long long)xh * S, units, grid);
-  const int nseg = owner_cta((long long)(xh + 1) * S - 1, units, grid) - c0 + 1;
-  const int dx = x - R, dy = y - R;
-  const int qb = RF * RF - dx * dx - dy * dy;
-  const float* fb = (periodic && qb >= 0) ? FB + isqrt_i(qb) * kCols : nullptr;
-  const float* pp = part + ((long long)xh * maxseg * kRows + r) * kCols;
-  double acc = 0.0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int z = lane + 32 * i;
-    if (z >= Mg) continue;
-    float sum = 0.0f;
-    for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * kRows * kCols + z);
-    if (fb) sum += __ldg(fb + z);
-    const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
-    const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
-    eps[((long long)x * Mg + y) * Mg + z] = v;
-    if (m <= RF * RF) acc += (double)v;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
-}
-
-__global__ void __launch_bounds__(1024) k_simt_ex(const double* row_ex, int n, double* Ex) {
-  __shared__ double red[1024];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += 1024) acc += row_ex[i];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    Ex[0] = 0.5 * red[0];
-    Ex[1] = red[0];
-  }
-}
-
 int num_sms() {
   static int n = 0;
   if (n == 0) {
@@ -343,7 +281,8 @@ struct SimtSlabWs {
   float* FW = nullptr;
   float* FB = nullptr;
   float* part = nullptr;
-  double* row_ex = nullptr;
+  double* blk_ex = nullptr;
+  unsigned* ticket = nullptr;  // blocks of the finaliser done (0 between calls)
   std::vector<void*> allocs;
 };
 
@@ -385,9 +324,15 @@ cc_status simt_slab_alloc(cc_tables t, void** out) {
       (st = alloc((void**)&w->FB, sizeof(float) * kHMax * kCols)) != CC_OK ||
       (st = alloc((void**)&w->part, sizeof(float) * (size_t)Mg * w->nh * w->maxseg * kRows *
                                         kCols)) != CC_OK ||
-      (st = alloc((void**)&w->row_ex, sizeof(double) * Mg * Mg)) != CC_OK) {
+      (st = alloc((void**)&w->blk_ex, sizeof(double) * Mg * Mg)) != CC_OK ||
+      (st = alloc((void**)&w->ticket, sizeof(unsigned))) != CC_OK) {
     simt_slab_free(w);
     return st;
+  }
+  if (cudaMemset(w->ticket, 0, sizeof(unsigned)) != cudaSuccess) {
+    set_last_error("cudaMemset(finaliser ticket)", cudaGetLastError());
+    simt_slab_free(w);
+    return CC_ERR_CUDA;
   }
   *out = w;
   return CC_OK;
@@ -419,10 +364,9 @@ cc_status simt_slab_run(cc_tables t, void* ws, int R_F, float* eps, double* Ex,
     if (periodic) CC_TRY((launch_ew<8, true>(a, zw, w->grid, smem, st)));
     else CC_TRY((launch_ew<8, false>(a, zw, w->grid, smem, st)));
   }
-  k_simt_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, w->FB, R, R_F, S, w->nh,
-                                                          w->units, w->grid, w->maxseg,
-                                                          periodic, t->pref, eps, w->row_ex);
-  k_simt_ex<<<1, 1024, 0, st>>>(w->row_ex, Mg * Mg, Ex);
+  k_slab_finalize<kCols, kRows, false><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
+      w->part, w->FB, R, R_F, S, w->nh, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
+      w->blk_ex, w->ticket, Ex, nullptr, nullptr);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

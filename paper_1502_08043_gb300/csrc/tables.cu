@@ -339,6 +339,36 @@ std::vector<int8_t> make_basis(int R) {
   return v;
 }
 
+std::vector<uint32_t> make_id_hint(int R) {
+  struct Line { int x, y, zm; };
+  std::vector<Line> lines;
+  for (int x = -R; x <= R; ++x)
+    for (int y = -R; y <= R; ++y) {
+      const int r2 = R * R - x * x - y * y;
+      if (r2 < 0) continue;
+      int zm = 0;
+      while ((zm + 1) * (zm + 1) <= r2) ++zm;
+      lines.push_back({x, y, zm});
+    }
+  std::vector<uint32_t> h;
+  long long id = 0;  // first id of the current line
+  for (size_t l = 0; l < lines.size(); ++l) {
+    const Line& L = lines[l];
+    const long long len = 2 * L.zm + 1;
+    const uint32_t zm1 = l + 1 < lines.size() && lines[l + 1].x == L.x ? lines[l + 1].zm : 63;
+    // every bucket whose first id falls on this line
+    const long long B = 1LL << kIdHintShift;
+    for (long long b = (id + B - 1) >> kIdHintShift; (b << kIdHintShift) < id + len; ++b) {
+      const int z = (int)((b << kIdHintShift) - id) - L.zm;
+      const int rest = L.zm - z < 31 ? L.zm - z : 31;
+      h.push_back((uint32_t)(L.x + R) | (uint32_t)(L.y + R) << 7 | (uint32_t)(z + R) << 14 |
+                  (uint32_t)rest << 21 | zm1 << 26);
+    }
+    id += len;
+  }
+  return h;
+}
+
 static std::vector<NodeSpec> node_specs(const cc_table_params& p) {
   std::vector<NodeSpec> out;
   std::vector<double> edges;
@@ -395,7 +425,7 @@ static cc_status dmalloc(cc_tables t, T** ptr, size_t count) {
 
 static void free_tables(cc_tables t) {
   DevTables& d = t->d;
-  void* ptrs[] = {d.T64, d.w64, d.a64, d.sep64, d.sep32, d.Vm64, d.Vm32, d.basis,
+  void* ptrs[] = {d.T64, d.w64, d.a64, d.sep64, d.sep32, d.Vm64, d.Vm32, d.basis, d.idhint,
                   d.Tm64, d.WDm64, d.Dbar64, d.Tm32, d.WDm32, d.Dbar32,
                   d.G64, d.sepG64, d.sepG32};
   for (void* q : ptrs)
@@ -473,6 +503,10 @@ static cc_status build_derived(cc_tables t, cudaStream_t st) {
   std::vector<int8_t> b = make_basis(t->p.R);
   CC_TRY(dmalloc(t, &d.basis, b.size()));
   CC_CUDA(cudaMemcpyAsync(d.basis, b.data(), b.size(), cudaMemcpyHostToDevice, st));
+  const std::vector<uint32_t> hint = make_id_hint(t->p.R);
+  CC_TRY(dmalloc(t, &d.idhint, hint.size()));
+  CC_CUDA(cudaMemcpyAsync(d.idhint, hint.data(), sizeof(uint32_t) * hint.size(),
+                          cudaMemcpyHostToDevice, st));
   t->table_bytes = sizeof(float) * ((size_t)(Dmax + 1) * t->S_pad + t->m_max + 1);
   if (!periodic) CC_TRY(build_general(t, st));
   return CC_OK;

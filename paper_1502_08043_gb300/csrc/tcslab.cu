@@ -51,6 +51,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "slab_finalize.cuh"
 #include "tc_prims.cuh"
 
 namespace cc {
@@ -97,14 +98,6 @@ struct Args {
   int* err;
   int stall_test;
 };
-
-// CTA c owns work units [c U / G, (c + 1) U / G); the CTA that owns unit u
-__host__ __device__ inline int owner_cta(long long u, int units, int grid) {
-  int c = (int)((u * grid) / units);
-  while (c + 1 < grid && (long long)(c + 1) * units / grid <= u) ++c;
-  while (c > 0 && (long long)c * units / grid > u) --c;
-  return c;
-}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);
@@ -755,67 +748,6 @@ __global__ void k_tc_slab_dbar(const double* Dbar, int Mg, int R, int RF, float*
   }
 }
 
-__device__ __forceinline__ int isqrt_int(int v) {
-  int h = (int)sqrtf((float)v);
-  while (h * h > v) --h;
-  while ((h + 1) * (h + 1) <= v) ++h;
-  return h;
-}
-
-// one warp per grid row (x, y), four z per lane: partials of the pair in order, + Dbar
-// term, eps on the basis sphere; FP64 sum of the row's eps over the Fermi sphere (fixed
-// butterfly order)
-__global__ void __launch_bounds__(256)
-    k_tc_slab_finalize(const float* part, const float* FB, int R, int RF, int S, int units,
-                       int grid, int maxseg, int periodic, double pref, float* eps,
-                       double* row_ex) {
-  const int Mg = 2 * R + 1;
-  const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (y >= Mg) return;  // whole warps
-  const int p = x >> 1, j = x & 1;
-  const int c0 = owner_cta((long long)p * S, units, grid);
-  const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
-  const int dx = x - R, dy = y - R;
-  const int qb = RF * RF - dx * dx - dy * dy;  // z line at (x, y) for the Dbar term
-  const float* fb = (periodic && qb >= 0) ? FB + isqrt_int(qb) * kN : nullptr;
-  const float* pp = part + (((long long)p * maxseg * 2 + j) * kN + y) * kN;
-  double acc = 0.0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int z = lane + 32 * i;
-    if (z >= Mg) continue;
-    float sum = 0.0f;
-    for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 2 * kN * kN + z);
-    if (fb) sum += __ldg(fb + z);
-    const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
-    const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
-    eps[((long long)x * Mg + y) * Mg + z] = v;
-    if (m <= RF * RF) acc += (double)v;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
-}
-
-// E_x from the Mg^2 row sums, fixed order: thread t adds rows t, t + 1024, ..., then a tree
-__global__ void __launch_bounds__(1024)
-    k_tc_slab_ex(const double* row_ex, int n, double* Ex, const int* err, int* status) {
-  __shared__ double red[1024];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += 1024) acc += row_ex[i];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    Ex[0] = 0.5 * red[0];
-    Ex[1] = red[0];
-    if (status) *status = *err;
-  }
-}
-
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -835,7 +767,8 @@ struct TcSlabWs {
   float* FW = nullptr;
   float* FB = nullptr;
   float* part = nullptr;
-  double* row_ex = nullptr;
+  double* blk_ex = nullptr;
+  unsigned* ticket = nullptr;  // blocks of the finaliser done (0 between calls)
   float* w32 = nullptr;
   // grids of side <= 64: own 128-padded T planes and their maps (else the step chain's)
   void* T128[2] = {nullptr, nullptr};
@@ -885,10 +818,16 @@ cc_status tc_slab_alloc(cc_tables t, void** out) {
       (st = alloc((void**)&w->FW, sizeof(float) * S * kN * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->FB, sizeof(float) * kN * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->part, sizeof(float) * 2 * kN * kN * pairs * w->maxseg)) != CC_OK ||
-      (st = alloc((void**)&w->row_ex, sizeof(double) * kN * kN)) != CC_OK ||
+      (st = alloc((void**)&w->blk_ex, sizeof(double) * kN * kN)) != CC_OK ||
+      (st = alloc((void**)&w->ticket, sizeof(unsigned))) != CC_OK ||
       (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK) {
     tc_slab_free(w);
     return st;
+  }
+  if (cudaMemset(w->ticket, 0, sizeof(unsigned)) != cudaSuccess) {
+    set_last_error("cudaMemset(finaliser ticket)", cudaGetLastError());
+    tc_slab_free(w);
+    return CC_ERR_CUDA;
   }
   if (t->Mg <= 64) {
     const size_t plane = sizeof(__nv_bfloat16) * (size_t)S * kN * kN;
@@ -1029,11 +968,9 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
     else
       k_tc_slab<false, false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   }
-  k_tc_slab_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(w->part, half ? w->FB16 : w->FB,
-                                                             R, R_F, S,
-                                                             w->units, w->grid, w->maxseg,
-                                                             periodic, t->pref, eps, w->row_ex);
-  k_tc_slab_ex<<<1, 1024, 0, st>>>(w->row_ex, Mg * Mg, Ex, err, err + 1);
+  k_slab_finalize<kN, 2 * kN, true><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
+      w->part, half ? w->FB16 : w->FB, R, R_F, S, 1, w->units, w->grid, w->maxseg, periodic,
+      t->pref, eps, w->blk_ex, w->ticket, Ex, err, err + 1);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "slab_finalize.cuh"
 #include "tc_prims.cuh"
 
 namespace cc {
@@ -91,13 +92,6 @@ struct Args {
   int* err;
   int stall_test;
 };
-
-__host__ __device__ inline int owner_cta(long long u, int units, int grid) {
-  int c = (int)((u * grid) / units);
-  while (c + 1 < grid && (long long)(c + 1) * units / grid <= u) ++c;
-  while (c > 0 && (long long)c * units / grid > u) --c;
-  return c;
-}
 
 // the CTA that owns unit u: an equal split of the units, or the table of CTA starts
 __host__ __device__ inline int owner_of(long long u, const long long* cta0, int units, int grid) {
@@ -700,73 +694,6 @@ __global__ void k_tcs_dbar(const double* Dbar, int Mg, int R, int RF, float* FB)
   }
 }
 
-__device__ __forceinline__ int isqrt_int(int v) {
-  int h = (int)sqrtf((float)v);
-  while (h * h > v) --h;
-  while ((h + 1) * (h + 1) <= v) ++h;
-  return h;
-}
-
-// one warp per grid row (x, y), two z per lane: partials of the pair in order, + Dbar term,
-// eps on the basis sphere; FP64 sum of the row's eps over the Fermi sphere.  The last block
-// to finish (ticket) adds the row sums in index order into E_x (deterministic whichever
-// block is last) and resets the ticket for the next call.
-__global__ void __launch_bounds__(256)
-    k_tcs_finalize(const float* part, const float* FB, int R, int RF, int S, int units, int grid,
-                   int maxseg, int periodic, double pref, float* eps, double* row_ex,
-                   unsigned* ticket, double* Ex, const int* err, int* status) {
-  const int Mg = 2 * R + 1;
-  const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (y < Mg) {
-    const int p = x >> 1, j = x & 1;
-    const int c0 = owner_cta((long long)p * S, units, grid);
-    const int nseg = owner_cta((long long)(p + 1) * S - 1, units, grid) - c0 + 1;
-    const int dx = x - R, dy = y - R;
-    const int qb = RF * RF - dx * dx - dy * dy;
-    const float* fb = (periodic && qb >= 0) ? FB + isqrt_int(qb) * kG : nullptr;
-    const float* pp = part + ((long long)p * maxseg * 128 + 64 * j + y) * kG;
-    double acc = 0.0;
-#pragma unroll
-    for (int k2 = 0; k2 < 2; ++k2) {
-      const int z = lane + 32 * k2;
-      if (z >= Mg) continue;
-      float sum = 0.0f;
-      for (int k = 0; k < nseg; ++k) sum += __ldg(pp + (long long)k * 128 * kG + z);
-      if (fb) sum += __ldg(fb + z);
-      const int dz = z - R, m = dx * dx + dy * dy + dz * dz;
-      const float v = m <= R * R ? (float)(-pref * (double)sum) : 0.0f;
-      eps[((long long)x * Mg + y) * Mg + z] = v;
-      if (m <= RF * RF) acc += (double)v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) row_ex[(long long)x * Mg + y] = acc;
-  }
-  __shared__ bool s_last;
-  __shared__ double red[256];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0)
-    s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double a = 0.0;
-  for (int i = threadIdx.x; i < Mg * Mg; i += 256) a += __ldcg(row_ex + i);
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    Ex[0] = 0.5 * red[0];
-    Ex[1] = red[0];
-    if (status) *status = *err;
-    *ticket = 0u;
-  }
-}
-
 // batches: one block per slab (box, x), eight warps over the rows y, two z per lane; the
 // block's FP64 sum of eps over the Fermi sphere (rows in order, then warps in order), and the
 // last block of a box (ticket) adds its slab sums in order into the box's E_x
@@ -876,7 +803,7 @@ struct TcSmallWs {
   void* T[2] = {nullptr, nullptr};
   float* FB = nullptr;
   float* part = nullptr;
-  double* row_ex = nullptr;
+  double* blk_ex = nullptr;
   float* w32 = nullptr;
   unsigned* ticket = nullptr;
   alignas(64) unsigned char map_th[128], map_tl[128], map_fh[128], map_fl[128];
@@ -920,7 +847,7 @@ cc_status tc_small_alloc(cc_tables t, void** out) {
       (st = alloc(&w->T[0], plane)) != CC_OK || (st = alloc(&w->T[1], plane)) != CC_OK ||
       (st = alloc((void**)&w->FB, sizeof(float) * kG * kHMax)) != CC_OK ||
       (st = alloc((void**)&w->part, sizeof(float) * 128 * kG * pairs * w->maxseg)) != CC_OK ||
-      (st = alloc((void**)&w->row_ex, sizeof(double) * kG * kG)) != CC_OK ||
+      (st = alloc((void**)&w->blk_ex, sizeof(double) * kG * kG)) != CC_OK ||
       (st = alloc((void**)&w->w32, sizeof(float) * S)) != CC_OK ||
       (st = alloc((void**)&w->ticket, sizeof(unsigned))) != CC_OK) {
     tc_small_free(w);
@@ -989,9 +916,9 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
     k_tcs<false, false, true><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   else
     k_tcs<false, false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
-  k_tcs_finalize<<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
-      w->part, w->FB, R, R_F, S, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
-      w->row_ex, w->ticket, Ex, err, err + 1);
+  k_slab_finalize<kG, 2 * kG, true><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
+      w->part, w->FB, R, R_F, S, 1, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
+      w->blk_ex, w->ticket, Ex, err, err + 1);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

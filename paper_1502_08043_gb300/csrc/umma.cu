@@ -839,8 +839,9 @@ cc_status exchange_mixed(cc_tables t, int R_F, int precision, float* eps, double
 
 }  // namespace cc
 
-// Choice between the two bf16x3 forms (automatic: the fused slab kernel, every grid side
-// up to 127).
+// Choice of the tensor-core exchange form (0 automatic: the small-grid kernel for bf16x3 at
+// grid sides up to 64, the 128-row slab kernel above and for fp16x3; 1 the step chain;
+// 2 the 128-row slab kernel; 3 the small-grid kernel).
 extern "C" cc_status cc_set_mixed_variant(int variant) {
   if (variant < 0 || variant > 3) return CC_ERR_ARG;
   __atomic_store_n(&cc::g_mixed_variant, variant, __ATOMIC_RELEASE);
@@ -887,7 +888,6 @@ struct MxBatchImpl {
   std::vector<long long*> t123[3], t4;
   std::vector<int> n123, n4;
   std::vector<void*> allocs;
-  void* slab = nullptr;   // the batch through the fused slab kernel (tcslab.cu)
   void* small = nullptr;  // the batch through the small-grid kernel (tcsmall.cu)
 };
 
@@ -963,7 +963,6 @@ static cc_status mxb_upload(MxBatchImpl* m, V** dst, const std::vector<V>& src) 
 void mixed_batch_free(void* p) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return;
-  tc_slab_batch_free(m->slab);
   tc_small_batch_free(m->small);
   for (void* q : m->allocs) cudaFree(q);
   delete m;
@@ -1073,11 +1072,7 @@ cc_status mixed_batch_create(const std::vector<cc_tables>& tabs, const std::vect
   if (s == CC_OK) s = mxb_upload(m, &m->eps_off_dev, eps_off);
   if (s == CC_OK && cudaMemset(m->err, 0, sizeof(int) * 2) != cudaSuccess) s = CC_ERR_CUDA;
   if (s == CC_OK && cudaDeviceSynchronize() != cudaSuccess) s = CC_ERR_CUDA;
-  // the same boxes through the fused slab kernel, over the concatenated T planes above
-  if (s == CC_OK)
-    s = tc_slab_batch_create(tabs, R_F, eps_off, P.TT[0], P.TT[1], rows_x1, off_x1, Np,
-                             &m->slab);
-  // and through the small-grid kernel (every grid side <= 64)
+  // the same boxes through the small-grid kernel (every grid side <= 64)
   if (s == CC_OK && tc_small_batch_supported(tabs, R_F))
     s = tc_small_batch_create(tabs, R_F, eps_off, &m->small);
   if (s != CC_OK) {
@@ -1099,10 +1094,7 @@ cc_status mixed_batch_run(void* p, float* eps, double* Ex, cudaStream_t st) {
   MxBatchImpl* m = reinterpret_cast<MxBatchImpl*>(p);
   if (!m) return CC_ERR_NOTSUPP;
   const int variant = __atomic_load_n(&g_mixed_variant, __ATOMIC_ACQUIRE);
-  if (m->small && (variant == 0 || variant == 3))
-    return tc_small_batch_run(m->small, m->err, eps, Ex, st);
-  if (variant == 3) return CC_ERR_NOTSUPP;
-  if (m->slab && variant != 1) return tc_slab_batch_run(m->slab, m->err, eps, Ex, st);
+  if (m->small && variant != 1) return tc_small_batch_run(m->small, m->err, eps, Ex, st);
   constexpr int Np = 64;
   using E = __nv_bfloat16;
   const long long NN = (long long)Np * Np;

@@ -166,6 +166,52 @@ def test_full_size_large(dev):
     _full_size(dev, CFG5, 1_000_000_000, 4000)
 
 
+@pytest.mark.parametrize("R", [15, 24, 63])
+def test_id_decode_every_id(dev, R):
+    """Collapsed lookups of bases too large to stage decode ids on chip from line hints.
+    Every id of the basis is looked up against four anchors (0,0,0), (1,0,0), (0,1,0),
+    (0,0,1) as (a, id, id, a), whose values V(|n_id - n_a|^2) (V strictly decreasing in m)
+    fix n_id; the decoded and the gathered forms agree bit for bit in values and counters,
+    in every id format and precision, and a sample agrees with the oracle."""
+    import torch
+    import paper_1502_08043_gb300 as cc
+    L, S = 10.0, 48
+    B = ob.basis(R)
+    Nb = len(B)
+    t = cc.build_tables("periodic", R=R, L=L, S=S)
+    a, w = oracle_nodes(R, S)
+    anchors = [int(np.flatnonzero((B == v).all(axis=1))[0])
+               for v in ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    ids = np.arange(Nb, dtype=np.int32)
+    q = np.concatenate([np.stack([np.full(Nb, an, np.int32), ids, ids,
+                                  np.full(Nb, an, np.int32)], axis=1) for an in anchors])
+    planted = ci.quads(R, 4242, 50000, stream=ci.STREAM_PLANTED)
+    planted[11::4999, 1] = Nb      # out of range
+    q = np.concatenate([q, planted])
+    forms = [q] + ([as_ids16(q)] if Nb <= 65536 else [])
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, len(q), 20000)
+    ref, _ = orc.reconstruct(q[idx], R, L, "separable", a=a, w=w)
+    try:
+        for prec in (torch.float32, torch.float64):
+            for qin in forms:
+                res = []
+                for on in (1, 0):
+                    assert cc.lib().cc_set_id_decode(on) == 0
+                    res.append(_run(t, qin, "collapsed", prec, dev))
+                (got, cnt), (gat, cnt_g) = res
+                assert np.array_equal(cnt, cnt_g)
+                assert np.array_equal(got, gat)
+                assert cnt[2] == len(range(11, 50000, 4999))
+                tol = TOL_FP64 if prec == torch.float64 else TOL_FP32
+                assert np.array_equal(got[idx] == 0, ref == 0)
+                assert rel_err(got[idx], ref) < tol
+        assert cc.lib().cc_set_id_decode(2) != 0
+    finally:
+        cc.lib().cc_set_id_decode(1)
+        t.free()
+
+
 def test_box_kernel_separable(dev):
     import torch
     import paper_1502_08043_gb300 as cc
