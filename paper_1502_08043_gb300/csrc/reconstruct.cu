@@ -46,6 +46,19 @@ __device__ __forceinline__ int classify(uint32_t a, uint32_t b, uint32_t c, uint
   return f;
 }
 
+// k_col's classification: flags and m = |q|^2 (the sources below, from q's byte magnitudes)
+template <bool kPeriodic, typename Src>
+__device__ __forceinline__ int classify_m(const Src& src, const int4 v, uint32_t& m) {
+  if constexpr (Src::kHint) {
+    return src.template classify_m<kPeriodic>(v, m);
+  } else {
+    uint32_t qa;
+    const int f = src.template classify_raw<kPeriodic>(v, qa);
+    m = __dp4a(qa, qa, 0u);
+    return f;
+  }
+}
+
 struct IdsSrc {
   static constexpr bool kHint = false;
   const int4* q;
@@ -226,6 +239,24 @@ struct IdsDecSrc {
     }
     return classify<kPeriodic>(id_vector(hint, R, v.x), id_vector(hint, R, v.y),
                                id_vector(hint, R, v.z), id_vector(hint, R, v.w), qa);
+  }
+  // The decoded words have bytes in [0, 2R] (offset by +R), so byte sums stay below 256
+  // and plain 32-bit arithmetic is exact byte by byte: conservation is b + d == a + c, and
+  // ((b | 0x80..) - a) ^ 0x80.. holds the signed bytes of q = n_J - n_I, whose dot product
+  // with itself is |q|^2.
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_m(const int4 v, uint32_t& m) const {
+    if (!in_range(v)) {
+      m = 0;
+      return kRange;
+    }
+    const uint32_t a = id_vector(hint, R, v.x), b = id_vector(hint, R, v.y),
+                   c = id_vector(hint, R, v.z), d = id_vector(hint, R, v.w);
+    const uint32_t q = ((b | 0x80808080u) - a) ^ 0x80808080u;
+    m = (uint32_t)__dp4a((int)q, (int)q, 0);
+    if (b + d != a + c) return kNonCons;
+    if (kPeriodic && m == 0) return kQZero;
+    return 0;
   }
   __device__ __forceinline__ bool fetch(int64_t i, uint32_t w[4]) const {
     const int4 v = raw(i);
@@ -480,26 +511,24 @@ __global__ void __launch_bounds__(kThreads) k_col(Src src, int64_t n, const T* _
     int f[U];
     uint32_t m[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      uint32_t qa;
-      f[u] = src.template classify_raw<true>(v[u], qa);
-      m[u] = __dp4a(qa, qa, 0u);  // |q|^2
-    }
+    for (int u = 0; u < U; ++u) f[u] = classify_m<true>(src, v[u], m[u]);  // m = |q|^2
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      c0 += f[u] == kNonCons;
-      c1 += f[u] == kQZero;
-      c2 += f[u] == kRange;
+      if (f[u]) {  // rare
+        c0 += f[u] == kNonCons;
+        c1 += f[u] == kQZero;
+        c2 += f[u] == kRange;
+      }
       __stcs(out + i + u * stride, f[u] ? T(0) : Vl[m[u] * kRep]);
     }
   }
   for (; i < n; i += stride) {
-    uint32_t qa;
-    const int f = src.template decode<true>(i, qa);
+    uint32_t mm;
+    const int f = classify_m<true>(src, src.raw(i), mm);
     c0 += f == kNonCons;
     c1 += f == kQZero;
     c2 += f == kRange;
-    __stcs(out + i, f ? T(0) : Vl[__dp4a(qa, qa, 0u) * kRep]);
+    __stcs(out + i, f ? T(0) : Vl[mm * kRep]);
   }
   c0 = __reduce_add_sync(kFull, c0);
   c1 = __reduce_add_sync(kFull, c1);

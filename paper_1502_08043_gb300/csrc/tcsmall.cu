@@ -1020,7 +1020,6 @@ static cc_status small_batch_plan(TcSmallBatch* m, int order, int split) {
     for (int c = 0; c <= grid; ++c) cuts[c] = (long long)c * units / grid;
   }
   long long part = 0;
-  int slab = 0;
   std::vector<int> slab_box(m->slabs);
   std::vector<int> slab0(nb);
   for (int b = 0, sl = 0; b < nb; ++b) {
@@ -1036,7 +1035,6 @@ static cc_status small_batch_plan(TcSmallBatch* m, int order, int split) {
     fb[b] = FBox{bx[k].R, bx[k].RF, bx[k].Mg, bx[k].S, bx[k].maxseg, slab0[b], bx[k].unit0,
                  bx[k].part0, m->eps_off[b], m->tabs[b]->pref};
   }
-  (void)slab;
   const size_t pbytes = sizeof(float) * (size_t)part;
   if (pbytes > m->part_cap) {
     cudaFree(m->part);
