@@ -41,6 +41,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// non-blocking check of a phase (mbarrier.test_wait, acquire at CTA scope): several of them
+// are independent and can be in flight together, unlike a chain of try_waits
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // try_wait with a suspend-time hint: a thread whose phase is not complete sleeps until it
 // completes or the hint (ns) runs out, instead of spinning and taking issue slots and
 // barrier-unit cycles from the other warps of its scheduler (the MMA issuer among them)

@@ -24,15 +24,20 @@
 // tensor memory over the CTA's run of nodes and leaves once as a partial; a second kernel
 // adds the partials of each pair in a fixed order, the Dbar term, and forms eps and E_x.
 //
-// Pipeline: T_s (read by both products) has three buffers and F_s, the R^T operand, D1 and
-// the U operand two each, so the MMA warp issues MMA1(i), MMA2(i - 1), MMA1(i + 1), ...
-// while the builders form R^T of unit i + 1, the epilogue converts D1 of unit i, and the
-// TMA loads of unit i + 2 need only MMA2(i - 1) (T) and MMA1(i) (F) to have finished.
+// Pipeline: one warp issues MMA1 of unit after unit, another MMA2, while the builders form
+// R^T of unit i + 1 and the epilogue converts D1 of unit i; with two issuing warps neither
+// product waits for the other's issue (an N = 64 MMA issues no faster than the pipe runs
+// it, and the hand-offs between them would otherwise leave the pipe idle).  T_s (read by
+// both products) has three buffers, so the TMA load of unit i + 2 needs only MMA2(i - 1) to
+// have finished; F_s, R^T, D1 and the U operand have two each.  The issuers first test all
+// the barriers of a product at once (independent test_waits) and only then wait for what
+// is not ready, and every role steps its unit's (pair, node) place without a 64-bit
+// division.
 // Tensor memory (256 columns): [0, 64) D1[0], [64, 128) D1[1], [128, 192) E.
 // Warps: 0-7 epilogue (warp w: lanes 32 (w % 4) .., columns 32 (w / 4) ..), 8-10 and 12-14
-// build R^T and P, 11 TMA producer, 15 MMA issuer.  Every wait is bounded (global timer);
-// on expiry the error word is set, all roles stop, the MMA issuer drains its MMAs and tensor
-// memory is freed before the CTA returns.
+// build R^T and P, 11 TMA producer, 15 issues MMA1 and 16 MMA2.  Every wait is bounded
+// (global timer); on expiry the error word is set, all roles stop, the MMA issuers drain
+// their MMAs and tensor memory is freed before the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -48,24 +53,28 @@ namespace cc {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 544;
 constexpr int kEpiWarps = 8;
 constexpr int kBldWarps = 6;
 constexpr int kBldThreads = 32 * kBldWarps;
 constexpr int kProdWarp = 11;
-constexpr int kMmaWarp = 15;
+constexpr int kMmaWarp = 15;   // issues MMA1
+constexpr int kMma2Warp = 16;  // issues MMA2
 constexpr int kG = 64;                        // padded grid side
 constexpr int kHMax = 64;                     // window half-lengths h = 0 .. R_F <= 31
 constexpr uint32_t kPl64 = kG * kG * 2;       // 64 x 64 bf16 plane: 8 KB
 constexpr uint32_t kPl128 = 128 * kG * 2;     // 128 x 64 bf16 plane: 16 KB
 // shared memory (1024-byte aligned base)
+constexpr uint32_t kNT = 3;                         // T buffers
+constexpr uint32_t kNF = 2;                         // F buffers
+constexpr uint32_t kNU = 2;                         // U buffers
 constexpr uint32_t kOffU = 0;                       // 2 x (U hi, U lo) MN-major: 64 KB
-constexpr uint32_t kOffT = kOffU + 4 * kPl128;      // 3 x (T hi, T lo): 48 KB
-constexpr uint32_t kOffF = kOffT + 6 * kPl64;       // 2 x (F hi, F lo): 32 KB
-constexpr uint32_t kOffA = kOffF + 4 * kPl64;       // 2 x (R^T hi, R^T lo): 64 KB
+constexpr uint32_t kOffT = kOffU + 2 * kNU * kPl128; // 3 x (T hi, T lo): 48 KB
+constexpr uint32_t kOffF = kOffT + 2 * kNT * kPl64; // 2 x (F hi, F lo): 32 KB
+constexpr uint32_t kOffA = kOffF + 2 * kNF * kPl64; // 2 x (R^T hi, R^T lo): 64 KB
 constexpr uint32_t kOffP = kOffA + 4 * kPl128;      // P one-hot: 16 KB
 constexpr uint32_t kOffBar = kOffP + kPl128;        // mbarriers, tensor-memory slot
-constexpr int kNumBars = 29;
+constexpr int kNumBars = 36;
 constexpr uint32_t kOffIsq = kOffBar + 8 * kNumBars + 16;  // floor(sqrt(v)), v <= R_F^2
 constexpr uint32_t kSmemBytes = kOffIsq + 1024 + 1024;     // isq (R_F <= 31) + alignment
 constexpr uint32_t kTmemCols = 256;
@@ -141,6 +150,31 @@ struct BoxCursor {
   }
 };
 
+// place of a unit in its box: node s and slab pair p (a box's units are pair-major,
+// node-minor), stepped from unit to unit without a 64-bit division in the loops
+struct UnitPos {
+  int s = 0, p = 0;
+  __device__ __forceinline__ void set(long long loc, int S) {
+    p = (int)(loc / S);
+    s = (int)(loc - (long long)p * S);
+  }
+  __device__ __forceinline__ void step(int S) {
+    if (++s == S) {
+      s = 0;
+      ++p;
+    }
+  }
+  // the place of unit u: the box cursor moved to u (set at a new box), else one step on
+  template <bool kBatch>
+  __device__ __forceinline__ void next(BoxCursor<kBatch>& C, const Args& g, long long u,
+                                       long long u0, bool* new_box = nullptr) {
+    const bool nb = C.advance(g, u);
+    if (new_box) *new_box = nb;
+    if (nb) set(u - C.X.unit0, C.X.S);
+    else if (u != u0) step(C.X.S);
+  }
+};
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_k, float hi_k) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -180,37 +214,41 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* gb = smem_raw + (base - raw);
   const uint8_t* isq = gb + kOffIsq;
   const uint32_t bar = base + kOffBar;
-  auto ffull = [&](int k) { return bar + 8u * (0 + k); };    // 0, 1 (F buffer k)
-  auto ffree = [&](int k) { return bar + 8u * (2 + k); };    // 2, 3
-  auto afull = [&](int k) { return bar + 8u * (4 + k); };    // 4, 5
-  auto afree = [&](int k) { return bar + 8u * (6 + k); };    // 6, 7
-  auto d1full = [&](int k) { return bar + 8u * (8 + k); };   // 8, 9
-  auto d1free = [&](int k) { return bar + 8u * (10 + k); };  // 10, 11
-  auto ufull = [&](int k) { return bar + 8u * (12 + k); };   // 12, 13
-  auto ufree = [&](int k) { return bar + 8u * (14 + k); };   // 14, 15
+  auto ffull = [&](int k) { return bar + 8u * (0 + k); };    // 0, 1, 2 (F buffer k)
+  auto ffree = [&](int k) { return bar + 8u * (3 + k); };    // 3, 4, 5
+  auto afull = [&](int k) { return bar + 8u * (6 + k); };    // 6, 7
+  auto afree = [&](int k) { return bar + 8u * (8 + k); };    // 8, 9
+  auto d1full = [&](int k) { return bar + 8u * (10 + k); };  // 10, 11
+  auto d1free = [&](int k) { return bar + 8u * (12 + k); };  // 12, 13
+  auto ufull = [&](uint32_t k) { return bar + 8u * (31 + k); };  // 31, 32 (U buffer k)
+  auto ufree = [&](uint32_t k) { return bar + 8u * (33 + k); };  // 33, 34
   const uint32_t efull = bar + 8u * 16, edone = bar + 8u * 17;
   const uint32_t pfull = bar + 8u * 18, pfree = bar + 8u * 19;
-  const uint32_t never = bar + 8u * 20, drain = bar + 8u * 21;
-  auto tfull = [&](int k) { return bar + 8u * (22 + k); };   // 22, 23, 24 (T buffer k)
-  auto tfree = [&](int k) { return bar + 8u * (25 + k); };   // 25, 26, 27
-  const uint32_t zbar = bar + 8u * 28;  // builders: an R^T buffer is cleared for a new box
+  const uint32_t never = bar + 8u * 20, drain = bar + 8u * 21, drain2 = bar + 8u * 35;
+  auto tfull = [&](int k) { return bar + 8u * (22 + k); };   // 22 .. 25 (T buffer k)
+  auto tfree = [&](int k) { return bar + 8u * (26 + k); };   // 26 .. 29
+  const uint32_t zbar = bar + 8u * 30;  // builders: an R^T buffer is cleared for a new box
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + kOffBar + 8 * kNumBars);
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     s_abort = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < (int)kNT; ++k) {
       mbar_init(tfull(k), 1);
       mbar_init(tfree(k), 1);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < (int)kNF; ++k) {
       mbar_init(ffull(k), 1);
       mbar_init(ffree(k), 1);
+    }
+    for (int k = 0; k < 2; ++k) {
       mbar_init(afull(k), kBldWarps);
       mbar_init(afree(k), 1);
       mbar_init(d1full(k), 1);
       mbar_init(d1free(k), kEpiWarps);
+    }
+    for (int k = 0; k < (int)kNU; ++k) {
       mbar_init(ufull(k), kEpiWarps);
       mbar_init(ufree(k), 1);
     }
@@ -220,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(pfree, 1);
     mbar_init(never, 1);
     mbar_init(drain, 1);
+    mbar_init(drain2, 1);
     mbar_init(zbar, kBldWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -239,10 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // R^T operands start all zero (builders only ever write the band of the current box and
   // clear a buffer when a new box starts using it), and so do the U operands (the epilogue
   // writes every K index of the band it reads)
-  for (uint32_t o = 16u * tid; o < 4 * kPl128; o += 16u * kThreads) {
+  for (uint32_t o = 16u * tid; o < 4 * kPl128; o += 16u * kThreads)
     *reinterpret_cast<uint4*>(gb + kOffA + o) = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t o = 16u * tid; o < 2 * kNU * kPl128; o += 16u * kThreads)
     *reinterpret_cast<uint4*>(gb + kOffU + o) = make_uint4(0u, 0u, 0u, 0u);
-  }
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -262,16 +301,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == kProdWarp) {
     if (lane == 0) {
-      // ---------------- TMA producer: T_s hi + lo into T buffer (unit % 3), F_s hi + lo
-      // (periodic) into F buffer (unit & 1)
+      // ---------------- TMA producer: T_s hi + lo into T buffer (unit % 4), F_s hi + lo
+      // (periodic) into F buffer (unit % 3)
       BoxCursor<kBatch> C;
-      if (u0 < u1) C.init(g, u0);
+      UnitPos P;
+      if (u0 < u1) {
+        C.init(g, u0);
+        P.set(u0 - C.X.unit0, C.X.S);
+      }
       uint32_t n = 0;
       for (long long u = u0; u < u1 && !s_abort; ++u, ++n) {
-        C.advance(g, u);
-        const int s = (int)((u - C.X.unit0) % C.X.S), kt = (int)(n % 3u), kf = (int)(n & 1u);
+        P.next(C, g, u, u0);
+        const int s = P.s, kt = (int)(n % kNT), kf = (int)(n % kNF);
         const int row = (int)(C.X.fr0 / kG) + s * kG;
-        if (!mbar_wait(tfree(kt), ((n / 3u) & 1u) ^ 1u, g.err, 41, &s_abort)) {
+        if (!mbar_wait(tfree(kt), ((n / kNT) & 1u) ^ 1u, g.err, 41, &s_abort)) {
           s_abort = 1;
           break;
         }
@@ -280,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_2d(dt, &mTh, 0, row, tfull(kt));
         tma_load_2d(dt + kPl64, &mTl, 0, row, tfull(kt));
         if (kPeriodic) {
-          if (!mbar_wait(ffree(kf), ((n >> 1) & 1u) ^ 1u, g.err, 41, &s_abort)) {
+          if (!mbar_wait(ffree(kf), ((n / kNF) & 1u) ^ 1u, g.err, 41, &s_abort)) {
             s_abort = 1;
             break;
           }
@@ -291,17 +334,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // copies still in flight land before the CTA leaves
-      for (uint32_t m = n > 3 ? n - 3 : 0; m < n; ++m)
-        mbar_wait(tfull(m % 3u), (m / 3u) & 1u, g.err, 42, nullptr, 100000000ull);
+      for (uint32_t m = n > kNT ? n - kNT : 0; m < n; ++m)
+        mbar_wait(tfull(m % kNT), (m / kNT) & 1u, g.err, 42, nullptr, 100000000ull);
       if (kPeriodic)
-        for (uint32_t m = n > 2 ? n - 2 : 0; m < n; ++m)
-          mbar_wait(ffull(m & 1u), (m >> 1) & 1u, g.err, 42, nullptr, 100000000ull);
+        for (uint32_t m = n > kNF ? n - kNF : 0; m < n; ++m)
+          mbar_wait(ffull(m % kNF), (m / kNF) & 1u, g.err, 42, nullptr, 100000000ull);
     }
-  } else if (warp == kMmaWarp) {
-    // ---------------- MMA issuer (the whole warp; every wait result made warp-uniform)
+  } else if (warp == kMmaWarp || warp == kMma2Warp) {
+    // ---------------- MMA issuers: warp 15 issues MMA1, warp 16 MMA2, so that neither
+    // product waits for the other's issue (whole warps; every wait result warp-uniform)
     auto all = [](bool v) { return __all_sync(0xffffffffu, v); };
     constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
-    if (g.stall_test && !all(mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull))) s_abort = 1;
+    if (warp == kMmaWarp && g.stall_test &&
+        !all(mbar_wait(never, 0, g.err, 5, nullptr, 20000000ull)))
+      s_abort = 1;
     const uint64_t dP = sdesc(base + kOffP);
     // K steps and N of the box of each MMA (unit i's box for MMA1, i - 1's for MMA2)
     struct Geo {
@@ -321,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto mma1 = [&](uint32_t i, const Geo& q) {
       const uint32_t k = i & 1u, d = tmem + 64u * k;
       const uint64_t dA = sdesc(base + kOffA + k * 2 * kPl128);
-      const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
+      const uint64_t dT = sdesc(base + kOffT + (i % kNT) * 2 * kPl64);
 #pragma unroll 1
       for (int m = q.ms; m < q.me; ++m) {
         if constexpr (kX1) mma_x1_w(d, dA + 2u * m, dT + 2u * m, q.idesc1, m > q.ms ? 1u : 0u);
@@ -329,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       m > q.ms ? 1u : 0u);
       }
       if constexpr (kPeriodic) {
-        const uint64_t dF = sdesc(base + kOffF + k * 2 * kPl64);
+        const uint64_t dF = sdesc(base + kOffF + (i % kNF) * 2 * kPl64);
 #pragma unroll 1
         for (int m = 0; m < q.nh; ++m) {
           if constexpr (kX1) mma_x1_w(d, dP + 2u * m, dF + 2u * m, q.idesc1, 1u);
@@ -338,9 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     auto mma2 = [&](uint32_t i, bool first, const Geo& q) {
-      const uint32_t k = i & 1u;
-      const uint64_t dU = sdesc_mn(base + kOffU + k * 2 * kPl128);
-      const uint64_t dT = sdesc(base + kOffT + (i % 3u) * 2 * kPl64);
+      const uint64_t dU = sdesc_mn(base + kOffU + (i % kNU) * 2 * kPl128);
+      const uint64_t dT = sdesc(base + kOffT + (i % kNT) * 2 * kPl64);
 #pragma unroll 1
       for (int m = q.ms; m < q.me; ++m) {
         const uint32_t acc = (first && m == q.ms) ? 0u : 1u;
@@ -352,76 +397,86 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = all(!s_abort);
     uint32_t pc = 0, segc = 0;
     BoxCursor<kBatch> C;
-    if (u0 < u1) C.init(g, u0);
-    Geo q = geo(C.X), qp = q;  // geometry of unit i and of unit i - 1
-    bool have_prev = false, prev_first = false, prev_last = false;
+    UnitPos P;
+    if (u0 < u1) {
+      C.init(g, u0);
+      P.set(u0 - C.X.unit0, C.X.S);
+    }
+    Geo q = geo(C.X);
     uint32_t i = 0;
-    for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      if (C.advance(g, u)) q = geo(C.X);
-      const long long loc = u - C.X.unit0;
-      const bool first = u == u0 || loc % C.X.S == 0;
-      const bool last = u + 1 == u1 || (loc + 1) % C.X.S == 0;
-      // MMA1(i)
-      ok = all(mbar_wait(tfull(i % 3u), (i / 3u) & 1u, g.err, 43, &s_abort) &&
-               (!kPeriodic || mbar_wait(ffull(i & 1u), (i >> 1) & 1u, g.err, 43, &s_abort)) &&
-               mbar_wait(afull(i & 1u), (i >> 1) & 1u, g.err, 44, &s_abort) &&
-               (!first || !kPeriodic || mbar_wait(pfull, pc & 1u, g.err, 45, &s_abort)) &&
-               (i < 2 || mbar_wait(d1free(i & 1u), ((i >> 1) & 1u) ^ 1u, g.err, 46, &s_abort)));
-      if (!ok) break;
-      if (first) ++pc;
-      tc_fence_after();
-      mma1(i, q);
-      mma_commit_w(afree(i & 1u));
-      if (kPeriodic) mma_commit_w(ffree(i & 1u));
-      mma_commit_w(d1full(i & 1u));
-      if (last && kPeriodic) mma_commit_w(pfree);
-      // MMA2(i - 1)
-      if (have_prev) {
-        const uint32_t ip = i - 1;
-        ok = all(mbar_wait(ufull(ip & 1u), (ip >> 1) & 1u, g.err, 47, &s_abort) &&
-                 (!prev_first || segc == 0 ||
-                  mbar_wait(edone, (segc - 1) & 1u, g.err, 48, &s_abort)));
+    if (warp == kMmaWarp) {
+      for (long long u = u0; u < u1 && ok; ++u, ++i) {
+        bool nbox = false;
+        P.next(C, g, u, u0, &nbox);
+        if (nbox) q = geo(C.X);
+        const bool first = u == u0 || P.s == 0;
+        const bool last = u + 1 == u1 || P.s + 1 == C.X.S;
+        // MMA1(i): the operands are usually ready by now, so all of them are first tested
+        // together (independent test_waits, no chain of dependent waits), and only what is
+        // not ready is waited for
+        const bool ready1 =
+            all(mbar_test(tfull(i % kNT), (i / kNT) & 1u) &
+                (!kPeriodic || mbar_test(ffull(i % kNF), (i / kNF) & 1u)) &
+                mbar_test(afull(i & 1u), (i >> 1) & 1u) &
+                (!first || !kPeriodic || mbar_test(pfull, pc & 1u)) &
+                (i < 2 || mbar_test(d1free(i & 1u), ((i >> 1) & 1u) ^ 1u)));
+        if (!ready1)
+          ok = all(mbar_wait(tfull(i % kNT), (i / kNT) & 1u, g.err, 43, &s_abort) &&
+                   (!kPeriodic || mbar_wait(ffull(i % kNF), (i / kNF) & 1u, g.err, 43, &s_abort)) &&
+                   mbar_wait(afull(i & 1u), (i >> 1) & 1u, g.err, 44, &s_abort) &&
+                   (!first || !kPeriodic || mbar_wait(pfull, pc & 1u, g.err, 45, &s_abort)) &&
+                   (i < 2 || mbar_wait(d1free(i & 1u), ((i >> 1) & 1u) ^ 1u, g.err, 46, &s_abort)));
+        if (!ok) break;
+        if (first) ++pc;
+        tc_fence_after();
+        mma1(i, q);
+        mma_commit_w(afree(i & 1u));
+        if (kPeriodic) mma_commit_w(ffree(i % kNF));
+        mma_commit_w(d1full(i & 1u));
+        if (last && kPeriodic) mma_commit_w(pfree);
+      }
+      if (!ok) s_abort = 1;
+      mma_commit_w(drain);
+      mbar_wait(drain, 0, g.err, 49, nullptr, 100000000ull);
+    } else {
+      // MMA2(i) once the epilogue has written U(i) (which follows MMA1(i)); T(i) is free
+      // when MMA2(i) completes, since MMA1(i) completed before U(i) was written
+      for (long long u = u0; u < u1 && ok; ++u, ++i) {
+        bool nbox = false;
+        P.next(C, g, u, u0, &nbox);
+        if (nbox) q = geo(C.X);
+        const bool first = u == u0 || P.s == 0;
+        const bool last = u + 1 == u1 || P.s + 1 == C.X.S;
+        const bool ready2 = all(mbar_test(ufull(i % kNU), (i / kNU) & 1u) &
+                                (!first || segc == 0 || mbar_test(edone, (segc - 1) & 1u)));
+        if (!ready2)
+          ok = all(mbar_wait(ufull(i % kNU), (i / kNU) & 1u, g.err, 47, &s_abort) &&
+                   (!first || segc == 0 ||
+                    mbar_wait(edone, (segc - 1) & 1u, g.err, 48, &s_abort)));
         if (!ok) break;
         tc_fence_after();
-        mma2(ip, prev_first, qp);
-        mma_commit_w(ufree(ip & 1u));
-        mma_commit_w(tfree(ip % 3u));
-        if (prev_last) {
+        mma2(i, first, q);
+        mma_commit_w(ufree(i % kNU));
+        mma_commit_w(tfree(i % kNT));
+        if (last) {
           mma_commit_w(efull);
           ++segc;
         }
       }
-      have_prev = true;
-      prev_first = first;
-      prev_last = last;
-      qp = q;
+      if (!ok) s_abort = 1;
+      mma_commit_w(drain2);
+      mbar_wait(drain2, 0, g.err, 49, nullptr, 100000000ull);
     }
-    if (ok && have_prev) {
-      const uint32_t ip = i - 1;
-      ok = all(mbar_wait(ufull(ip & 1u), (ip >> 1) & 1u, g.err, 47, &s_abort) &&
-               (!prev_first || segc == 0 ||
-                mbar_wait(edone, (segc - 1) & 1u, g.err, 48, &s_abort)));
-      if (ok) {
-        tc_fence_after();
-        mma2(ip, prev_first, qp);
-        mma_commit_w(ufree(ip & 1u));
-        mma_commit_w(tfree(ip % 3u));
-        mma_commit_w(efull);
-        ++segc;
-      }
-    }
-    if (!ok) s_abort = 1;
-    mma_commit_w(drain);
-    mbar_wait(drain, 0, g.err, 49, nullptr, 100000000ull);
   } else if (warp >= kEpiWarps) {
     // ---------------- R^T and P builders (warps 8-10, 12-14)
     // R^T[(j, z)][y'] = F_s[x_j][h(y', z)]: rows z and 2R - z are equal, so a task forms one
-    // 16-byte chunk (8 consecutive y') of a row z <= R and stores it into both mirror rows.
+    // 16-byte chunk (8 consecutive y') of a row z <= R for both slabs j and stores it into
+    // the mirror rows too.
     // The h values of a task are fixed for a box; the row of F_s comes from one register per
     // lane (h = lane; R_F <= 31) by shuffles.
     const int bw = warp < kProdWarp ? warp - kEpiWarps : warp - kEpiWarps - 1;
     const int bt = 32 * bw + lane;
-    constexpr int kMaxTasks = 3;  // 2 (2 R_F + 1 rows, halved by the mirror) 8 chunks <= 576
+    constexpr int kMaxTasks = 2;  // (R_F + 1 rows, halved by the mirror) 8 chunks <= 256
     uint32_t hb[kMaxTasks][2];
     int zlo = 0, nzh = 0, clo = 0, nc = 0, tasks = 0;
     auto setup = [&](const SBox& X) {
@@ -429,14 +484,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       nzh = X.RF + 1;
       clo = (X.R - X.RF) >> 3;
       nc = ((X.R + X.RF) >> 3) - clo + 1;
-      tasks = 2 * nzh * nc;
+      tasks = nzh * nc;
 #pragma unroll
       for (int k = 0; k < kMaxTasks; ++k) {
         const int t = bt + k * kBldThreads;
         hb[k][0] = hb[k][1] = 0xffffffffu;
         if (t < tasks) {
-          const int tt = t % (nzh * nc);
-          const int z = zlo + tt / nc, c = clo + tt % nc, dz = z - X.R;
+          const int z = zlo + t / nc, c = clo + t % nc, dz = z - X.R;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int dy = 8 * c + e - X.R;
@@ -448,33 +502,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     BoxCursor<kBatch> C, Cn;  // the box of this unit and of the next (F rows loaded ahead)
+    UnitPos P, Pn;
     if (u0 < u1) {
       C.init(g, u0);
       Cn.init(g, u0);
+      P.set(u0 - C.X.unit0, C.X.S);
+      Pn = P;
       setup(C.X);
     }
-    auto frow = [&](const SBox& X, long long u, int j) {
-      const long long loc = u - X.unit0;
-      return g.FR + X.fr0 + ((loc % X.S) * kG + 2 * (loc / X.S) + j) * kHMax;
+    auto frow = [&](const SBox& X, const UnitPos& Q, int j) {
+      return g.FR + X.fr0 + ((long long)Q.s * kG + 2 * Q.p + j) * kHMax;
     };
     uint32_t nf0 = 0, nf1 = 0;
     if (u0 < u1) {
-      nf0 = __ldg(frow(C.X, u0, 0) + lane);
-      nf1 = __ldg(frow(C.X, u0, 1) + lane);
+      nf0 = __ldg(frow(C.X, P, 0) + lane);
+      nf1 = __ldg(frow(C.X, P, 1) + lane);
     }
     int abox[2] = {0, 0};  // the box each R^T buffer was last built for (zero at start)
     if (kBatch && u0 < u1) abox[0] = abox[1] = C.b;
     uint32_t pc = 0, i = 0, zc = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      if (C.advance(g, u)) setup(C.X);
-      const long long loc = u - C.X.unit0;
-      const bool first = u == u0 || loc % C.X.S == 0;
+      bool nbox = false;
+      P.next(C, g, u, u0, &nbox);
+      if (nbox) setup(C.X);
+      const bool first = u == u0 || P.s == 0;
       const uint32_t f0 = nf0, f1 = nf1;
       if (u + 1 < u1) {
-        Cn.advance(g, u + 1);
-        nf0 = __ldg(frow(Cn.X, u + 1, 0) + lane);
-        nf1 = __ldg(frow(Cn.X, u + 1, 1) + lane);
+        Pn = P;
+        Pn.next(Cn, g, u + 1, u0);
+        nf0 = __ldg(frow(Cn.X, Pn, 0) + lane);
+        nf1 = __ldg(frow(Cn.X, Pn, 1) + lane);
       }
       if (kPeriodic && first) {
         // P_j[z][h] = [h(x_j, z) = h] for the pair of u: row r = 64 j + z, one thread a row
@@ -482,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         if (bt < 128) {
           const int j = bt >> 6, z = bt & 63;
-          const int dx = (int)(2 * (loc / C.X.S) + j) - C.X.R, dz = z - C.X.R;
+          const int dx = 2 * P.p + j - C.X.R, dz = z - C.X.R;
           const int q = C.X.RF * C.X.RF - dx * dx - dz * dz;
           const int h = q >= 0 ? (int)isq[q] : -1;
           uint8_t* row = gb + kOffP + bt * 128;
@@ -521,36 +579,40 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < kMaxTasks; ++k) {
         const int t = bt + k * kBldThreads;
         if (k * kBldThreads >= tasks) break;  // warp-uniform
-        // every lane shuffles (the source lane is its h); idle lanes use h = 0
-        const int j = t < tasks ? t / (nzh * nc) : 0;
-        uint32_t v[8];
+        // every lane shuffles (the source lane is its h); idle lanes use h = 0.  The h of a
+        // chunk does not depend on the slab, so one task fills the chunk in both slabs' rows.
+        uint32_t v0[8], v1[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const uint32_t h = (hb[k][e >> 2] >> (8 * (e & 3))) & 0xffu;
           const uint32_t a = __shfl_sync(0xffffffffu, f0, (int)(h & 31u));
           const uint32_t b = __shfl_sync(0xffffffffu, f1, (int)(h & 31u));
-          v[e] = h == 0xffu ? 0u : (j ? b : a);
+          v0[e] = h == 0xffu ? 0u : a;
+          v1[e] = h == 0xffu ? 0u : b;
         }
         if (t < tasks) {
-          const int tt = t % (nzh * nc);
-          const int z = zlo + tt / nc, c = clo + tt % nc;
-          uint4 hi, lo;
-          hi.x = __byte_perm(v[0], v[1], 0x5410);
-          hi.y = __byte_perm(v[2], v[3], 0x5410);
-          hi.z = __byte_perm(v[4], v[5], 0x5410);
-          hi.w = __byte_perm(v[6], v[7], 0x5410);
-          lo.x = __byte_perm(v[0], v[1], 0x7632);
-          lo.y = __byte_perm(v[2], v[3], 0x7632);
-          lo.z = __byte_perm(v[4], v[5], 0x7632);
-          lo.w = __byte_perm(v[6], v[7], 0x7632);
-          const int r = 64 * j + z, rm = 64 * j + 2 * C.X.R - z;
-          const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((c & 7) ^ (r & 7)) << 4);
-          *reinterpret_cast<uint4*>(A + off) = hi;
-          *reinterpret_cast<uint4*>(A + off + kPl128) = lo;
-          if (rm != r) {
-            const uint32_t offm = (uint32_t)rm * 128u + ((uint32_t)((c & 7) ^ (rm & 7)) << 4);
-            *reinterpret_cast<uint4*>(A + offm) = hi;
-            *reinterpret_cast<uint4*>(A + offm + kPl128) = lo;
+          const int z = zlo + t / nc, c = clo + t % nc;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t* v = j ? v1 : v0;
+            uint4 hi, lo;
+            hi.x = __byte_perm(v[0], v[1], 0x5410);
+            hi.y = __byte_perm(v[2], v[3], 0x5410);
+            hi.z = __byte_perm(v[4], v[5], 0x5410);
+            hi.w = __byte_perm(v[6], v[7], 0x5410);
+            lo.x = __byte_perm(v[0], v[1], 0x7632);
+            lo.y = __byte_perm(v[2], v[3], 0x7632);
+            lo.z = __byte_perm(v[4], v[5], 0x7632);
+            lo.w = __byte_perm(v[6], v[7], 0x7632);
+            const int r = 64 * j + z, rm = 64 * j + 2 * C.X.R - z;
+            const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((c & 7) ^ (r & 7)) << 4);
+            *reinterpret_cast<uint4*>(A + off) = hi;
+            *reinterpret_cast<uint4*>(A + off + kPl128) = lo;
+            if (rm != r) {
+              const uint32_t offm = (uint32_t)rm * 128u + ((uint32_t)((c & 7) ^ (rm & 7)) << 4);
+              *reinterpret_cast<uint4*>(A + offm) = hi;
+              *reinterpret_cast<uint4*>(A + offm + kPl128) = lo;
+            }
           }
         }
       }
@@ -565,15 +627,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int j = quad >> 1, zr = 32 * (quad & 1) + lane;  // D1 row (j, z = zr)
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
     BoxCursor<kBatch> C;
-    if (u0 < u1) C.init(g, u0);
+    UnitPos P;
+    if (u0 < u1) {
+      C.init(g, u0);
+      P.set(u0 - C.X.unit0, C.X.S);
+    }
     bool in_band = zr >= band_lo(C.X) && zr < band_hi(C.X);
     uint32_t i = 0, segc = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u, ++i) {
-      if (C.advance(g, u)) in_band = zr >= band_lo(C.X) && zr < band_hi(C.X);
-      const long long loc = u - C.X.unit0;
-      const bool last = u + 1 == u1 || (loc + 1) % C.X.S == 0;
-      const float ws = g.w[C.X.w0 + loc % C.X.S];
+      bool nbox = false;
+      P.next(C, g, u, u0, &nbox);
+      if (nbox) in_band = zr >= band_lo(C.X) && zr < band_hi(C.X);
+      const bool last = u + 1 == u1 || P.s + 1 == C.X.S;
+      const float ws = g.w[C.X.w0 + P.s];
       ok = mbar_wait(d1full(i & 1u), (i >> 1) & 1u, g.err, 61, &s_abort);
       if (!ok) break;
       tc_fence_after();
@@ -582,12 +649,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(d1free(i & 1u));
-      ok = mbar_wait(ufree(i & 1u), ((i >> 1) & 1u) ^ 1u, g.err, 62, &s_abort);
+      // the U buffer of unit i was last read by MMA2(i - kNU)
+      ok = mbar_wait(ufree(i % kNU), ((i / kNU) & 1u) ^ 1u, g.err, 62, &s_abort);
       if (!ok) break;
       if (in_band) {
         // U[(j, y)][z] for y = 32 half + e: MN-major atom row z & 7 of K atom z >> 3 in
         // M block j, 16-byte chunk c = y >> 3 at position c ^ (z & 7)
-        uint8_t* U = gb + kOffU + (i & 1u) * 2 * kPl128 + j * 8192 + (zr >> 3) * 1024 +
+        uint8_t* U = gb + kOffU + (i % kNU) * 2 * kPl128 + j * 8192 + (zr >> 3) * 1024 +
                      (zr & 7) * 128;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
@@ -607,13 +675,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(ufull(i & 1u));
+      if (lane == 0) mbar_arrive(ufull(i % kNU));
       if (!last) continue;
       // the pair's E leaves tensor memory once, as a partial of this CTA
       ok = mbar_wait(efull, segc & 1u, g.err, 63, &s_abort);
       if (!ok) break;
       tc_fence_after();
-      const long long p = loc / C.X.S;
+      const long long p = P.p;
       const int kseg =
           (int)blockIdx.x - owner_of(C.X.unit0 + p * C.X.S, g.cta0, g.units, gridDim.x);
       tmem_ld32(tmem + lane_off + 128u + 32u * half, v);
