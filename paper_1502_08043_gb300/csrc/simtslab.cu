@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_simt_slab(SArgs g) {
                           E[i][j + 2] - C[i][j + 2], E[i][j + 3] - C[i][j + 3]);
     }
   }
+  signal_finalizer();
 }
 
 // w_s F_s[a][h] (FP64 window sums of D_s = T_s - I, or of T_s for the box kernel, rounded
@@ -364,9 +365,10 @@ cc_status simt_slab_run(cc_tables t, void* ws, int R_F, float* eps, double* Ex,
     if (periodic) CC_TRY((launch_ew<8, true>(a, zw, w->grid, smem, st)));
     else CC_TRY((launch_ew<8, false>(a, zw, w->grid, smem, st)));
   }
-  k_slab_finalize<kCols, kRows, false><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
-      w->part, w->FB, R, R_F, S, w->nh, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
-      w->blk_ex, w->ticket, Ex, nullptr, nullptr);
+  CC_CUDA((launch_slab_finalize<kCols, kRows, false>(
+      Mg, st, (const float*)w->part, (const float*)w->FB, R, R_F, S, w->nh, w->units, w->grid,
+      w->maxseg, periodic, t->pref, eps, w->blk_ex, w->ticket, Ex, (const int*)nullptr,
+      (int*)nullptr)));
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

@@ -49,6 +49,9 @@ __global__ void __launch_bounds__(256)
                     double* blk_ex, unsigned* ticket, double* Ex, const int* err,
                     int* status) {
   static_assert(W % 32 == 0, "row width must be whole warps");
+  // launched as a programmatic dependent of the slab kernel: wait until that grid has
+  // completed and its partials are visible (no-op for an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int Mg = 2 * R + 1;
   const int x = blockIdx.y, y = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   __shared__ double wsum[8];
@@ -130,6 +133,29 @@ __global__ void __launch_bounds__(256)
     if (status) *status = err ? *err : 0;
     *ticket = 0u;
   }
+}
+
+// the finaliser, launched as a programmatic dependent of the slab kernel launched just
+// before it on st (its launch overlaps that kernel's last CTAs; every CTA of the slab kernel
+// signals with griddepcontrol.launch_dependents when its own work is done)
+template <int W, int GR, bool kPairs, typename... Args>
+inline cudaError_t launch_slab_finalize(int Mg, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((Mg + 7) / 8, Mg);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_slab_finalize<W, GR, kPairs>, args...);
+}
+
+// a slab kernel's CTA is done with everything the finaliser reads
+__device__ __forceinline__ void signal_finalizer() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 }  // namespace

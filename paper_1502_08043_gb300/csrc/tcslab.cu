@@ -611,6 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  signal_finalizer();
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
@@ -968,9 +969,10 @@ cc_status tc_slab_run(cc_tables t, void* ws, const void* map_hi, const void* map
     else
       k_tc_slab<false, false, false><<<w->grid, kThreads, smem, st>>>(mh, ml, a);
   }
-  k_slab_finalize<kN, 2 * kN, true><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
-      w->part, half ? w->FB16 : w->FB, R, R_F, S, 1, w->units, w->grid, w->maxseg, periodic,
-      t->pref, eps, w->blk_ex, w->ticket, Ex, err, err + 1);
+  CC_CUDA((launch_slab_finalize<kN, 2 * kN, true>(
+      Mg, st, (const float*)w->part, (const float*)(half ? w->FB16 : w->FB), R, R_F, S, 1,
+      w->units, w->grid, w->maxseg, periodic, t->pref, eps, w->blk_ex, w->ticket, Ex,
+      (const int*)err, err + 1)));
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }

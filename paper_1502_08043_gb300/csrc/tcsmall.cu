@@ -701,6 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  signal_finalizer();
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -984,9 +985,9 @@ cc_status tc_small_run(cc_tables t, void* ws, int* err, int stall_test, int R_F,
     k_tcs<false, false, true><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
   else
     k_tcs<false, false, false><<<w->grid, kThreads, kSmemBytes, st>>>(th, tl, fh, fl, a);
-  k_slab_finalize<kG, 2 * kG, true><<<dim3((Mg + 7) / 8, Mg), 256, 0, st>>>(
-      w->part, w->FB, R, R_F, S, 1, w->units, w->grid, w->maxseg, periodic, t->pref, eps,
-      w->blk_ex, w->ticket, Ex, err, err + 1);
+  CC_CUDA((launch_slab_finalize<kG, 2 * kG, true>(
+      Mg, st, (const float*)w->part, (const float*)w->FB, R, R_F, S, 1, w->units, w->grid,
+      w->maxseg, periodic, t->pref, eps, w->blk_ex, w->ticket, Ex, (const int*)err, err + 1)));
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }
