@@ -32,8 +32,9 @@ sys.path.insert(0, ROOT)
 
 R, L, S, R_F = 13, 20.0, 64, 8
 N_QUADS = 100_000_000
-# ncu DRAM bytes of a 2e7-quadruple k_col launch, per quadruple encoding
-TRAFFIC_2E7 = {"ids": 370.3e6, "vec": 370.2e6, "ids16": 200.9e6}
+# ncu DRAM bytes (read + written) of a 2e7-quadruple k_col launch of the current kernel, per
+# quadruple encoding (only the encoding that was captured; the others report null)
+TRAFFIC_2E7 = {"ids16": 201.3e6}
 METRIC = "pair-Coulomb evals/s and integrals/s on 1 GB300, mixed vs FP32 at <=1e-4 rel err"
 UNIT = "Coulomb evals/s"
 WORKLOAD = ("paper scale: |n|<=13 (9171 planewaves), L=20 bohr, 64 nodes, R_F=8 (2109 occ); "
