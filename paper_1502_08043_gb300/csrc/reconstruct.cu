@@ -49,7 +49,7 @@ __device__ __forceinline__ int classify(uint32_t a, uint32_t b, uint32_t c, uint
 // k_col's classification: flags and m = |q|^2 (the sources below, from q's byte magnitudes)
 template <bool kPeriodic, typename Src>
 __device__ __forceinline__ int classify_m(const Src& src, const int4 v, uint32_t& m) {
-  if constexpr (Src::kHint) {
+  if constexpr (Src::kOwnClassify) {
     return src.template classify_m<kPeriodic>(v, m);
   } else {
     uint32_t qa;
@@ -61,6 +61,7 @@ __device__ __forceinline__ int classify_m(const Src& src, const int4 v, uint32_t
 
 struct IdsSrc {
   static constexpr bool kHint = false;
+  static constexpr bool kOwnClassify = false, kOffsetWords = false;
   const int4* q;
   const char4* basis;
   int Nb;
@@ -96,6 +97,7 @@ struct IdsSrc {
 // uint16 ids: 8 bytes per quadruple (basis of at most 65536 functions)
 struct Ids16Src {
   static constexpr bool kHint = false;
+  static constexpr bool kOwnClassify = false, kOffsetWords = false;
   const uint2* q;
   const char4* basis;
   int Nb;
@@ -130,6 +132,7 @@ struct Ids16Src {
 
 struct VecSrc {
   static constexpr bool kHint = false;
+  static constexpr bool kOwnClassify = false, kOffsetWords = false;
   const int4* q;
   const char4* basis;  // unused
   int R2;
@@ -211,6 +214,7 @@ __device__ __forceinline__ uint32_t id_vector(const uint32_t* hint, int R, int i
 template <bool k16>  // uint16 ids (8 bytes per quadruple) or int32 ids (16 bytes)
 struct IdsDecSrc {
   static constexpr bool kHint = true;
+  static constexpr bool kOwnClassify = true, kOffsetWords = false;
   const void* q;
   const uint32_t* hint;  // [nhint], moved to shared memory by the kernel
   int Nb, R, nhint;
@@ -266,6 +270,30 @@ struct IdsDecSrc {
     w[2] = id_vector(hint, R, v.z);
     w[3] = id_vector(hint, R, v.w);
     return true;
+  }
+};
+
+// uint16 or int32 ids of a basis staged in shared memory by k_col with every component
+// offset by +R (bytes 0 .. 2R): the bookkeeping runs on whole words without carries, as for
+// decoded ids (conservation b + d == a + c; q's signed bytes from one subtraction)
+template <class Base>
+struct OffsetIds : Base {
+  static constexpr bool kOwnClassify = true, kOffsetWords = true;
+  int R;
+  template <bool kPeriodic>
+  __device__ __forceinline__ int classify_m(const int4 v, uint32_t& m) const {
+    if ((unsigned)v.x >= (unsigned)this->Nb || (unsigned)v.y >= (unsigned)this->Nb ||
+        (unsigned)v.z >= (unsigned)this->Nb || (unsigned)v.w >= (unsigned)this->Nb) {
+      m = 0;
+      return kRange;
+    }
+    const uint32_t a = ld_word(this->basis, v.x), b = ld_word(this->basis, v.y),
+                   c = ld_word(this->basis, v.z), d = ld_word(this->basis, v.w);
+    const uint32_t q = ((b | 0x80808080u) - a) ^ 0x80808080u;
+    m = (uint32_t)__dp4a((int)q, (int)q, 0);
+    if (b + d != a + c) return kNonCons;
+    if (kPeriodic && m == 0) return kQZero;
+    return 0;
   }
 };
 
@@ -495,7 +523,14 @@ __global__ void __launch_bounds__(kThreads) k_col(Src src, int64_t n, const T* _
     src.hint = sh;
   } else if (basis_smem > 0) {
     char4* sb = reinterpret_cast<char4*>(smem + off);
-    for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
+    if constexpr (Src::kOffsetWords) {
+      const uint32_t offR = (uint32_t)src.R * 0x010101u;
+      uint32_t* sw = reinterpret_cast<uint32_t*>(sb);
+      for (int i = threadIdx.x; i < basis_smem; i += blockDim.x)
+        sw[i] = __vadd4(ld_word(src.basis, i), offR) & kXYZ;
+    } else {
+      for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
+    }
     src.basis = sb;
   }
   __syncthreads();
@@ -675,12 +710,25 @@ static cc_status launch_col(cc_tables t, Src src, int64_t n, T* out, unsigned lo
   if constexpr (Src::kHint) smem = tb + (size_t)src.nhint * 4;
   // decoding sources hold one 1024-thread block per SM (the hints fill shared memory)
   constexpr int kThreads = Src::kHint ? 1024 : 512;
-  auto kern = rep ? k_col<T, Src, kRep, kThreads> : k_col<T, Src, 1, kThreads>;
-  int blocks = 0;
-  CC_TRY(grid_for(kern, kThreads, smem, (n + 7) / 8, &blocks));
-  kern<<<blocks, kThreads, smem, st>>>(src, n, Vm, t->m_max, out, counters, basis_smem);
-  CC_CUDA(cudaGetLastError());
-  return CC_OK;
+  auto go = [&](auto s) -> cc_status {
+    using S = decltype(s);
+    auto kern = rep ? k_col<T, S, kRep, kThreads> : k_col<T, S, 1, kThreads>;
+    int blocks = 0;
+    CC_TRY(grid_for(kern, kThreads, smem, (n + 7) / 8, &blocks));
+    kern<<<blocks, kThreads, smem, st>>>(s, n, Vm, t->m_max, out, counters, basis_smem);
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+  };
+  // ids whose basis is staged: offset words, carry-free bookkeeping
+  if constexpr (std::is_same<Src, IdsSrc>::value || std::is_same<Src, Ids16Src>::value) {
+    if (basis_smem > 0) {
+      OffsetIds<Src> os;
+      static_cast<Src&>(os) = src;
+      os.R = t->p.R;
+      return go(os);
+    }
+  }
+  return go(src);
 }
 
 template <typename T>
