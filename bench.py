@@ -685,10 +685,9 @@ def large_lookups(n=1_000_000_000, reps=3):
     ci.quads_device(63, 0, n, q)
     vals = torch.empty(n, dtype=torch.float32, device=dev)
     out = {"quadruples": n, "S_eff": t.info["S_eff"],
-           "note": "ids collapsed: the four ids decoded on chip from 128 KB of line hints in "
-                   "shared memory; ids separable and ids_l2gather: 4 basis vectors gathered "
-                   "from the 4.2 MB basis table (L2); vec: the quadruple carries its four "
-                   "int8x4 vectors"}
+           "note": "ids: the four ids decoded on chip from 128 KB of line hints in shared "
+                   "memory; ids_l2gather: 4 basis vectors gathered from the 4.2 MB basis "
+                   "table (L2); vec: the quadruple carries its four int8x4 vectors"}
     peak, _ = _peaks()
     # the same quadruples in vector form (16 B each as well)
     vecs = torch.from_numpy(cc.basis(63)).to(dev)[q.long().view(-1)].view(n, 4, 4)

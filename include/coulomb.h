@@ -234,15 +234,16 @@ cc_status cc_reconstruct_integrals(cc_tables t, const void* quads_dev, int64_t n
                                    int lookup, int precision, void* out_dev,
                                    unsigned long long* counters_dev, void* stream);
 
-/* How the collapsed lookup finds the index vectors of ids (uint16 or int32) when the basis
- * and the table do not fit in 48 KB of shared memory (R >= 15 in FP32, R >= 14 in FP64;
- * not part of the paper, a comparison switch of this implementation, process-wide):
- * 1 (the default) = decoded on chip from a table of one 32-bit hint per 32 ids staged in
- * shared memory (the line (n_x, n_y) and place of the bucket's first id in the
- * lexicographic basis order of Sec. III, and the next line's length; ids further on walk
- * over whole lines), when table and hints fit in 200 KB (FP32 up to R = 63, FP64 up to
- * R = 57); 0 = a gather from the basis table in global memory.  Results are identical.
- * CC_ERR_ARG for any other value. */
+/* How the lookups find the index vectors of ids (uint16 or int32) when the basis cannot be
+ * staged in shared memory with their table (collapsed: basis and table over 48 KB, R >= 15
+ * in FP32, R >= 14 in FP64; separable: over 96 KB; not part of the paper, a comparison
+ * switch of this implementation, process-wide): 1 (the default) = decoded on chip from a
+ * table of one 32-bit hint per 32 ids staged in shared memory (the line (n_x, n_y) and
+ * place of the bucket's first id in the lexicographic basis order of Sec. III, and the next
+ * line's length; ids further on walk over whole lines), when table and hints fit in 200 KB
+ * (collapsed FP32 up to R = 63, FP64 up to R = 57; separable FP32 at R = 63 with up to 128
+ * padded nodes); 0 = a gather from the basis table in global memory.  Results are
+ * identical.  CC_ERR_ARG for any other value. */
 cc_status cc_set_id_decode(int on);
 
 /* Exchange-type pair integrals (ij|ji) = V(n_j - n_i) for basis rows

@@ -299,6 +299,8 @@ struct OffsetIds : Base {
 
 // exchange-type pairs (ij|ji): item = row * Nb + col, q = n_col - n_row
 struct PairSrc {
+  static constexpr bool kHint = false;
+  static constexpr bool kOwnClassify = false, kOffsetWords = false;
   const int4* q;  // unused
   const char4* basis;
   int Nb;
@@ -357,16 +359,21 @@ __device__ __forceinline__ T node_chunk(const T* rx, const T* ry, const T* rz, i
   return a;
 }
 
-template <typename T, typename Src, bool kPeriodic, int NCH>
-__global__ void __launch_bounds__(256) k_sep(Src src, int64_t n, const T* __restrict__ gtab,
-                                             int Dmax, int S_pad, T* __restrict__ out,
-                                             unsigned long long* counters, int basis_smem) {
+template <typename T, typename Src, bool kPeriodic, int NCH, int kThreads = 256>
+__global__ void __launch_bounds__(kThreads) k_sep(Src src, int64_t n, const T* __restrict__ gtab,
+                                                  int Dmax, int S_pad, T* __restrict__ out,
+                                                  unsigned long long* counters,
+                                                  int basis_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* tab = reinterpret_cast<T*>(smem);
   const int tab_elems = (Dmax + 1) * S_pad;
   for (int i = threadIdx.x; i < tab_elems; i += blockDim.x) tab[i] = gtab[i];
-  if (basis_smem > 0) {
-    const size_t off = ((size_t)tab_elems * sizeof(T) + 15) & ~(size_t)15;
+  const size_t off = ((size_t)tab_elems * sizeof(T) + 15) & ~(size_t)15;
+  if constexpr (Src::kHint) {  // decoded ids: the words carry +R offsets, |q| is unchanged
+    uint32_t* sh = reinterpret_cast<uint32_t*>(smem + off);
+    for (int i = threadIdx.x; i < src.nhint; i += blockDim.x) sh[i] = src.hint[i];
+    src.hint = sh;
+  } else if (basis_smem > 0) {
     char4* sb = reinterpret_cast<char4*>(smem + off);
     for (int i = threadIdx.x; i < basis_smem; i += blockDim.x) sb[i] = src.basis[i];
     src.basis = sb;
@@ -643,17 +650,24 @@ static cc_status launch_sep(cc_tables t, Src src, int64_t n, T* out,
   const size_t tb = (((size_t)(t->Dmax + 1) * t->S_pad * sizeof(T)) + 15) & ~(size_t)15;
   if (tb > kSmemCap) return CC_ERR_RANGE;
   int basis_smem = 0;
-  if (tb + (size_t)t->Nb * 4 <= 96 * 1024) basis_smem = t->Nb;
-  const size_t smem = tb + (size_t)basis_smem * 4;
+  size_t smem = tb;
+  if constexpr (Src::kHint) {
+    smem = tb + (size_t)src.nhint * 4;
+  } else if (tb + (size_t)t->Nb * 4 <= 96 * 1024) {
+    basis_smem = t->Nb;
+    smem = tb + (size_t)basis_smem * 4;
+  }
   const int nch = t->S_pad / 32;
-  auto kern = nch == 1 ? k_sep<T, Src, kPeriodic, 1>
-            : nch == 2 ? k_sep<T, Src, kPeriodic, 2>
-            : nch == 3 ? k_sep<T, Src, kPeriodic, 3>
-            : nch == 4 ? k_sep<T, Src, kPeriodic, 4>
-                       : k_sep<T, Src, kPeriodic, 0>;
+  // decoding sources hold one 512-thread block per SM (table and hints fill shared memory)
+  constexpr int kThr = Src::kHint ? 512 : 256;
+  auto kern = nch == 1 ? k_sep<T, Src, kPeriodic, 1, kThr>
+            : nch == 2 ? k_sep<T, Src, kPeriodic, 2, kThr>
+            : nch == 3 ? k_sep<T, Src, kPeriodic, 3, kThr>
+            : nch == 4 ? k_sep<T, Src, kPeriodic, 4, kThr>
+                       : k_sep<T, Src, kPeriodic, 0, kThr>;
   int blocks = 0;
-  CC_TRY(grid_for(kern, 256, smem, (n + 7) / 8, &blocks));
-  kern<<<blocks, 256, smem, st>>>(src, n, tab, t->Dmax, t->S_pad, out, counters, basis_smem);
+  CC_TRY(grid_for(kern, kThr, smem, (n + 7) / 8, &blocks));
+  kern<<<blocks, kThr, smem, st>>>(src, n, tab, t->Dmax, t->S_pad, out, counters, basis_smem);
   CC_CUDA(cudaGetLastError());
   return CC_OK;
 }
@@ -750,12 +764,22 @@ static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int fo
   const int nhint = (t->Nb + (1 << kIdHintShift) - 1) >> kIdHintShift;
   const bool dec = tbc + (size_t)t->Nb * 4 > 48 * 1024 && tbc + (size_t)nhint * 4 <= kSmemCap &&
                    __atomic_load_n(&g_id_decode, __ATOMIC_ACQUIRE);
+  // ... and so do separable lookups, with their table
+  const size_t tbs = (((size_t)(t->Dmax + 1) * t->S_pad * sizeof(T)) + 15) & ~(size_t)15;
+  const bool dec_s = tbs + (size_t)t->Nb * 4 > 96 * 1024 &&
+                     tbs + (size_t)nhint * 4 <= kSmemCap &&
+                     __atomic_load_n(&g_id_decode, __ATOMIC_ACQUIRE);
   if (format == CC_QUAD_IDS_U16) {
     if (lookup == CC_LOOKUP_COLLAPSED && dec)
       return launch_col<T>(t, IdsDecSrc<true>{quads, t->d.idhint, t->Nb, t->p.R, nhint}, n,
                            out, counters, st, false);
     if (lookup == CC_LOOKUP_COLLAPSED)
       return launch_col<T>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st, true);
+    if (dec_s) {
+      const IdsDecSrc<true> d{quads, t->d.idhint, t->Nb, t->p.R, nhint};
+      if (periodic) return launch_sep<T, IdsDecSrc<true>, true>(t, d, n, out, counters, st);
+      return launch_sep<T, IdsDecSrc<true>, false>(t, d, n, out, counters, st);
+    }
     if (periodic) return launch_sep<T, Ids16Src, true>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
     return launch_sep<T, Ids16Src, false>(t, Ids16Src{q16, basis, t->Nb}, n, out, counters, st);
   }
@@ -767,6 +791,11 @@ static cc_status reconstruct_t(cc_tables t, const void* quads, int64_t n, int fo
     return launch_col<T>(t, VecSrc{q, basis, t->p.R * t->p.R}, n, out, counters, st, false);
   }
   if (format == CC_QUAD_IDS_I32) {
+    if (dec_s) {
+      const IdsDecSrc<false> d{quads, t->d.idhint, t->Nb, t->p.R, nhint};
+      if (periodic) return launch_sep<T, IdsDecSrc<false>, true>(t, d, n, out, counters, st);
+      return launch_sep<T, IdsDecSrc<false>, false>(t, d, n, out, counters, st);
+    }
     if (periodic) return launch_sep<T, IdsSrc, true>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
     return launch_sep<T, IdsSrc, false>(t, IdsSrc{q, basis, t->Nb}, n, out, counters, st);
   }

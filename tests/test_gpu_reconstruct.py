@@ -168,7 +168,8 @@ def test_full_size_large(dev):
 
 @pytest.mark.parametrize("R", [15, 24, 63])
 def test_id_decode_every_id(dev, R):
-    """Collapsed lookups of bases too large to stage decode ids on chip from line hints.
+    """Lookups of bases too large to stage decode ids on chip from line hints (collapsed and
+    separable).
     Every id of the basis is looked up against four anchors (0,0,0), (1,0,0), (0,1,0),
     (0,0,1) as (a, id, id, a), whose values V(|n_id - n_a|^2) (V strictly decreasing in m)
     fix n_id; the decoded and the gathered forms agree bit for bit in values and counters,
@@ -193,19 +194,20 @@ def test_id_decode_every_id(dev, R):
     idx = rng.integers(0, len(q), 20000)
     ref, _ = orc.reconstruct(q[idx], R, L, "separable", a=a, w=w)
     try:
-        for prec in (torch.float32, torch.float64):
-            for qin in forms:
-                res = []
-                for on in (1, 0):
-                    assert cc.lib().cc_set_id_decode(on) == 0
-                    res.append(_run(t, qin, "collapsed", prec, dev))
-                (got, cnt), (gat, cnt_g) = res
-                assert np.array_equal(cnt, cnt_g)
-                assert np.array_equal(got, gat)
-                assert cnt[2] == len(range(11, 50000, 4999))
-                tol = TOL_FP64 if prec == torch.float64 else TOL_FP32
-                assert np.array_equal(got[idx] == 0, ref == 0)
-                assert rel_err(got[idx], ref) < tol
+        cases = [(p_, f_, l_) for p_ in (torch.float32, torch.float64) for f_ in forms
+                 for l_ in ("collapsed", "separable")]
+        for prec, qin, lookup in cases:
+            res = []
+            for on in (1, 0):
+                assert cc.lib().cc_set_id_decode(on) == 0
+                res.append(_run(t, qin, lookup, prec, dev))
+            (got, cnt), (gat, cnt_g) = res
+            assert np.array_equal(cnt, cnt_g)
+            assert np.array_equal(got, gat)
+            assert cnt[2] == len(range(11, 50000, 4999))
+            tol = TOL_FP64 if prec == torch.float64 else TOL_FP32
+            assert np.array_equal(got[idx] == 0, ref == 0)
+            assert rel_err(got[idx], ref) < tol
         assert cc.lib().cc_set_id_decode(2) != 0
     finally:
         cc.lib().cc_set_id_decode(1)
