@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- TMA producer: T_s hi + lo, both K blocks, into buffer (unit & 1)
       uint32_t n = 0;
-      for (long long u = u0; u < u1 && !s_abort; ++u, ++n) {
-        const int s = (int)(u % S), k = (int)(n & 1u);
+      int s = (int)(u0 % S);  // node of unit u, stepped (no 64-bit division per unit)
+      for (long long u = u0; u < u1 && !s_abort; ++u, ++n, s = s + 1 == S ? 0 : s + 1) {
+        const int k = (int)(n & 1u);
         if (!mbar_wait(tfree(k), ((n >> 1) & 1u) ^ 1u, g.err, 11, &s_abort)) {
           s_abort = 1;
           break;
@@ -365,22 +366,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    auto frow = [&](long long u, int j) {
-      return g.FR + ((long long)(u % S) * kN + 2 * (u / S) + j) * kHMax;
+    // the window-sum row of slab 2 p + j at node s; the unit's (node, pair) place is stepped
+    // from unit to unit (no 64-bit division per build)
+    auto frow = [&](int sn, int pn, int j) {
+      return g.FR + ((long long)sn * kN + 2 * pn + j) * kHMax;
     };
+    int su = (int)(u0 % S), pu = (int)(u0 / S);  // place of unit u
     // this warp fills entries h = hw0 .. hw0 + 10 (11 per warp, 6 warps cover 64)
     const int hw0 = 11 * bw;
-    uint32_t nf0 = __ldg(frow(u0, 0) + lane), nf1 = __ldg(frow(u0, 0) + lane + 32);
+    uint32_t nf0 = __ldg(frow(su, pu, 0) + lane), nf1 = __ldg(frow(su, pu, 0) + lane + 32);
     uint32_t r = 0;
     int p_h = -1;  // the h of this thread's row of P as it stands (-1: zero row)
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u) {
+      const int sn = su + 1 == S ? 0 : su + 1, pn = su + 1 == S ? pu + 1 : pu;  // unit u + 1
       for (int j = 0; j < 2 && ok; ++j, ++r) {
         const uint32_t f0 = nf0, f1 = nf1;
         const long long un = j == 0 ? u : u + 1;
         if (un < u1) {  // the next build's row
-          nf0 = __ldg(frow(un, j ^ 1) + lane);
-          nf1 = __ldg(frow(un, j ^ 1) + lane + 32);
+          const int ss = j == 0 ? su : sn, ps = j == 0 ? pu : pn;
+          nf0 = __ldg(frow(ss, ps, j ^ 1) + lane);
+          nf1 = __ldg(frow(ss, ps, j ^ 1) + lane + 32);
         }
         // every warp has finished build r - 2, so table (r & 1) is free
         uint32_t* ft = reinterpret_cast<uint32_t*>(gb + kOffFtab + (r & 1u) * kFtabBytes);
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the previous h is cleared, the chunk of the new h written (at most two 16-byte
           // stores; bf16 skips both while h stays)
           if (bt < nact) {
-            const int rr = bt, dz = zs + rr - R, dx = (int)(2 * (u / S) + j) - R;
+            const int rr = bt, dz = zs + rr - R, dx = 2 * pu + j - R;
             const int q = RF * RF - dx * dx - dz * dz;
             const int h = q >= 0 ? (int)isq[q] : -1;
             if (p_h >= 0 && p_h != h)
@@ -447,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   make_uint4(0u, 0u, 0u, 0u);
             if (h >= 0 && (kHalf || h != p_h)) {
               const uint32_t v1 =
-                  kHalf ? (uint32_t)(0x3C00 + 1024 * g.aexp[(int)(u % S)]) : 0x3F80u;
+                  kHalf ? (uint32_t)(0x3C00 + 1024 * g.aexp[su]) : 0x3F80u;
               const uint32_t one = v1 << (16 * (h & 1)), wi = (uint32_t)(h & 7) >> 1;
               *reinterpret_cast<uint4*>(gb + kOffP + rr * 128 + (((h >> 3) ^ (rr & 7)) << 4)) =
                   make_uint4(wi == 0 ? one : 0u, wi == 1 ? one : 0u, wi == 2 ? one : 0u,
@@ -460,6 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(rfull);
       }
+      su = sn;
+      pu = pn;
     }
     if (!ok) s_abort = 1;
   } else {
@@ -477,9 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // (kFlo + c) holds the bf16 hi (lo) pair of h = 2 c, 2 c + 1; this warp writes
     // h = 32 half .. 32 half + 31 of its lanes from the window-sum rows F_s[y][.]
     uint4 fpre[8];  // the next unit's row segment, loaded a unit ahead of its staging
-    auto load_f = [&](long long uu) {
+    auto load_f = [&](int su) {  // node su
       const uint4* src = reinterpret_cast<const uint4*>(
-          g.FR + ((long long)(uu % S) * kN + yrow) * kHMax + 32 * half);
+          g.FR + ((long long)su * kN + yrow) * kHMax + 32 * half);
 #pragma unroll
       for (int i = 0; i < 8; ++i) fpre[i] = __ldg(src + i);
     };
@@ -502,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     if constexpr (kMmaA) {
       if (u0 < u1) {
-        load_f(u0);
+        load_f((int)(u0 % S));
         stage_f();
       }
     }
@@ -521,11 +529,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           hz[j][k] = q >= 0 ? (int)isq[q] : -1;
         }
       for (; u < ue && ok; ++u, ++n) {
-        const int s = (int)(u % S);
+        const int s = (int)(u - p * S);
         const float ws = g.w[s];
         const float* FWs = g.FW + (long long)s * kHMax * kN + yrow;
         if constexpr (kMmaA) {
-          if (u + 1 < u1) load_f(u + 1);
+          if (u + 1 < u1) load_f(s + 1 == S ? 0 : s + 1);
         }
         for (int j = 0; j < 2; ++j) {
           // the A-term values of this warp's columns, requested before the MMA result is
