@@ -284,10 +284,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < U && ok; ++i, ++n) {
           const uint32_t k = n & 1u, tb = base + kOffT + k * kOp;
           const uint32_t tbp = base + kOffT + (k ^ 1u) * kOp;
-          // MMA1(i, 0)
-          ok = all(mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
-                   mbar_wait(rfull, r & 1u, g.err, 15, &s_abort) &&
-                   (!kMmaA || mbar_wait(ffull, n & 1u, g.err, 18, &s_abort)));
+          // MMA1(i, 0): the three barriers are tested together first; otherwise waited for
+          // with the R operand (the critical path) last, so that its completion is followed
+          // by the issue without further waits
+          if (!all(mbar_test(tfull(k), (n >> 1) & 1u) & mbar_test(rfull, r & 1u) &
+                   (!kMmaA || mbar_test(ffull, n & 1u))))
+            ok = all(mbar_wait(tfull(k), (n >> 1) & 1u, g.err, 14, &s_abort) &&
+                     (!kMmaA || mbar_wait(ffull, n & 1u, g.err, 18, &s_abort)) &&
+                     mbar_wait(rfull, r & 1u, g.err, 15, &s_abort));
           if (!ok) break;
           tc_fence_after();
           mma1(tb, 0);
