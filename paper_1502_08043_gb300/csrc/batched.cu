@@ -132,12 +132,12 @@ static cc_status plan_build(const std::vector<BoxIn>& boxes, int ctas_per_sm, in
     const int periodic = t->p.kernel == CC_KERNEL_PERIODIC;
     const int n_items = t->Mg * groups[b];
     b32[b] = FusedBox<float>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, groups[b], n_items,
-                             t->pref, t->d.Tm32, t->d.Tm64, t->d.w64, t->d.Dbar64,
+                             t->pref, t->d.Tm32, t->d.FW32, t->d.w64, t->d.FDb32,
                              reinterpret_cast<float*>(p.part) + part_off[b],
                              slab_done + slab0[b], p.slab_ex + slab0[b], boxes[b].eps_off,
                              (int)b};
     b64[b] = FusedBox<double>{t->p.R, boxes[b].R_F, t->Mg, t->S_eff, periodic, groups[b],
-                              n_items, t->pref, t->d.Tm64, t->d.Tm64, t->d.w64, t->d.Dbar64,
+                              n_items, t->pref, t->d.Tm64, t->d.FW64, t->d.w64, t->d.FDb64,
                               reinterpret_cast<double*>(p.part) + part_off[b],
                               slab_done + slab0[b], p.slab_ex + slab0[b], boxes[b].eps_off,
                               (int)b};

@@ -9,10 +9,10 @@
 // Box kernel: E = sum_s w_s (R_s x2 T_s) x3 T_s with R_s = O x1 T_s, no A, no Dbar term.
 // The occupation is a Fermi sphere, so every line of O along an axis is 1 on one
 // contiguous range [R - h, R + h] (h = floor(sqrt(R_F^2 - u^2 - v^2)) for the other two
-// coordinates u, v).  A mode product of O with M is therefore a difference of two prefix
-// sums of the rows of M; the prefix sums are formed in FP64, so the difference keeps full
-// precision.  What is left per node and x slab are two Mg x Mg x Mg products
-// (U = T R_x + A_x, then U T), all in shared memory.
+// coordinates u, v).  A mode product of O with M therefore takes, per line, the window sum
+// F[a][h] = sum_{k = R - h}^{R + h} M[a][k]; the table builder forms these in FP64 once
+// (k_windows), rounded to T only here.  What is left per node and x slab are two
+// Mg x Mg x Mg products (U = T R_x + A_x, then U T), all in shared memory.
 // Work item = (box, x slab, group of nodes); the item's slab of E (Kahan-summed over
 // its nodes) goes to a partial buffer; the CTA that completes the last group of a slab
 // adds the slab's partials (Kahan), writes its eps and its FP64 share of E_x, and the
@@ -32,9 +32,9 @@ struct FusedBox {
   int R, R_F, Mg, S_eff, periodic, n_groups, n_items;
   double pref;
   const T* Tm;         // [S_eff][Mg][Mg]  T_s
-  const double* T64;   // [S_eff][Mg][Mg]  T_s in FP64 (prefix sums)
+  const T* Fw;         // [S_eff][Mg][R + 1]  window sums of the rows of D_s (T_s for the box)
   const double* w64;   // [S_eff]
-  const double* Db64;  // [Mg][Mg] sum_s w_s D_s (periodic)
+  const T* FDb;        // [Mg][R + 1]  window sums of the rows of sum_s w_s D_s (periodic)
   T* part;             // [n_groups][Mg][Mg][Mg] slab partials
   int* slab_done;      // [Mg] finished groups per slab
   double* slab_ex;     // [Mg] FP64 sum of eps over the Fermi sphere, per slab
@@ -48,17 +48,14 @@ struct FusedItem {
 
 constexpr int kFusedThreads = 128;
 
-// shared-memory layout of one item (Mg = the box's grid side, mm = Mg * Mg):
-//   double CD[Mg][Mg + 1]   prefix sums of the rows of the node's D (or T)
-//   short  H[Mg][Mg]        sphere half-lengths, -1 for an empty line
+// shared-memory layout of one item (Mg = 2R + 1 = the box's grid side, mm = Mg * Mg):
 //   T      sT[mm], sR[mm], sU[mm], sE[mm], sC[mm]
+//   T      sF[Mg][R + 1]     the node's window sums (periodic: the A term)
+//   short  H[Mg][Mg]         sphere half-lengths, -1 for an empty line
 template <typename T>
 __host__ __device__ inline size_t slab_smem_bytes(int Mg) {
   const size_t mm = (size_t)Mg * Mg;
-  size_t b = sizeof(double) * Mg * (Mg + 1);
-  b += ((sizeof(short) * mm + 15) / 16) * 16;
-  b += 5 * mm * sizeof(T);
-  return b;
+  return (5 * mm + (size_t)Mg * ((Mg + 1) / 2)) * sizeof(T) + sizeof(short) * mm;
 }
 
 __device__ __forceinline__ int isqrt_floor(int v) {
@@ -93,15 +90,14 @@ __global__ void __launch_bounds__(kFusedThreads)
     const FusedItem item = items[it];
     FusedBox<T> bx = boxes[item.box];
     if (rf_override > 0) bx.R_F = rf_override;
-    const int Mg = bx.Mg, R = bx.R, mm = Mg * Mg, x = item.x;
-    double* CD = reinterpret_cast<double*>(fsmem);
-    short* H = reinterpret_cast<short*>(CD + Mg * (Mg + 1));
-    T* sT = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(H) +
-                                 ((sizeof(short) * mm + 15) / 16) * 16);
+    const int Mg = bx.Mg, R = bx.R, nh = R + 1, mm = Mg * Mg, x = item.x;
+    T* sT = reinterpret_cast<T*>(fsmem);
     T* sR = sT + mm;
     T* sU = sR + mm;
     T* sE = sU + mm;
     T* sC = sE + mm;
+    T* sF = sC + mm;
+    short* H = reinterpret_cast<short*>(sF + Mg * nh);
     for (int i = threadIdx.x; i < mm; i += blockDim.x) {
       const int u = i / Mg - R, v = i % Mg - R;
       const int h2 = bx.R_F * bx.R_F - u * u - v * v;
@@ -112,24 +108,16 @@ __global__ void __launch_bounds__(kFusedThreads)
     __syncthreads();
     const int cb = (Mg + 3) / 4;
     for (int s = item.s0; s < item.s1; ++s) {
-      const double* Ts64 = bx.T64 + (long long)s * mm;
-      // prefix sums of the rows of X = D_s (periodic) or T_s (box), FP64
-      for (int a = threadIdx.x; a < Mg; a += blockDim.x) {
-        double acc = 0.0;
-        CD[a * (Mg + 1)] = 0.0;
-        for (int k = 0; k < Mg; ++k) {
-          acc += (bx.periodic && k == a) ? 0.0 : Ts64[a * Mg + k];
-          CD[a * (Mg + 1) + k + 1] = acc;
-        }
-      }
-      for (int i = threadIdx.x; i < mm; i += blockDim.x) sT[i] = bx.Tm[(long long)s * mm + i];
-      __syncthreads();
-      // R_x[y][z] = sum_{x' on the x line at (y, z)} X[x][x']
+      // T_s; R_x[y][z] = sum_{x' on the x line at (y, z)} X[x][x'] = F_s[x][h(y, z)] with
+      // X = D_s (periodic) or T_s (box); the node's window sums for the A term
+      const T* Fs = bx.Fw + (long long)s * Mg * nh;
       for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+        sT[i] = bx.Tm[(long long)s * mm + i];
         const int h = H[i];
-        sR[i] = h < 0 ? T(0)
-                      : (T)(CD[x * (Mg + 1) + R + h + 1] - CD[x * (Mg + 1) + R - h]);
+        sR[i] = h < 0 ? T(0) : Fs[x * nh + h];
       }
+      if (bx.periodic)
+        for (int i = threadIdx.x; i < Mg * nh; i += blockDim.x) sF[i] = Fs[i];
       __syncthreads();
       // U[y'][z] = sum_y T[y'][y] R_x[y][z] + A_x[y'][z],
       // A_x[y'][z] = sum_{y on the y line at (x, z)} D[y'][y]   (periodic only)
@@ -149,7 +137,7 @@ __global__ void __launch_bounds__(kFusedThreads)
           T a = T(0);
           if (bx.periodic) {
             const int h = H[x * Mg + z];
-            if (h >= 0) a = (T)(CD[yp * (Mg + 1) + R + h + 1] - CD[yp * (Mg + 1) + R - h]);
+            if (h >= 0) a = sF[yp * nh + h];
           }
           sU[yp * Mg + z] = acc[j] + a;
         }
@@ -175,20 +163,11 @@ __global__ void __launch_bounds__(kFusedThreads)
     // I x I x D term (periodic, once per slab): E[y][z'] += sum_{z on the z line at (x, y)}
     // Dbar[z'][z]
     if (bx.periodic && item.g == 0) {
-      for (int a = threadIdx.x; a < Mg; a += blockDim.x) {
-        double acc = 0.0;
-        CD[a * (Mg + 1)] = 0.0;
-        for (int k = 0; k < Mg; ++k) {
-          acc += bx.Db64[a * Mg + k];
-          CD[a * (Mg + 1) + k + 1] = acc;
-        }
-      }
-      __syncthreads();
       for (int i = threadIdx.x; i < mm; i += blockDim.x) {
         const int y = i / Mg, zp = i % Mg;
         const int h = H[x * Mg + y];
         if (h < 0) continue;
-        kahan_add(sE, sC, i, (T)(CD[zp * (Mg + 1) + R + h + 1] - CD[zp * (Mg + 1) + R - h]));
+        kahan_add(sE, sC, i, bx.FDb[zp * nh + h]);
       }
       __syncthreads();
     }

@@ -54,6 +54,13 @@ struct DevTables {
   float* Tm32 = nullptr;
   float* WDm32 = nullptr;
   float* Dbar32 = nullptr;
+  // window sums over the centred ranges [R - h, R + h], h = 0..R, of the rows of D_s
+  // (periodic; T_s for the box kernel) and of Dbar: the product of a Fermi-sphere line of
+  // the occupation with those matrices (grid side <= kFusedMaxMg only)
+  double* FW64 = nullptr;     // [S_eff][Mg][R + 1]
+  float* FW32 = nullptr;
+  double* FDb64 = nullptr;    // [Mg][R + 1]
+  float* FDb32 = nullptr;
   // BOX kernel, general (not necessarily momentum-conserving) integrals: the two-index
   // per-axis tables A(alpha_s, D1, D2) of Sec. II Eq. 8 over the canonical codes
   // c = d1^2 + d1 + d2 (d1 >= |d2|, see gen_code), Gc = (2R + 1)^2 codes per node

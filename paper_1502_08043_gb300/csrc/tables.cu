@@ -236,6 +236,36 @@ __global__ void k_dbar(const double* WDm64, int S_eff, int Mg, double* D64, floa
   D32[ab] = (float)acc;
 }
 
+// Window sums F_s[a][h] = sum_{k = R - h}^{R + h} X_s[a][k], h = 0..R, in FP64, for
+// X_s = D_s (periodic: T_s without its diagonal) or T_s (box), and for Dbar (the row
+// after the last node).  A line of the Fermi-sphere occupation O along one axis is 1 on
+// [R - h, R + h], so these are the entries of the mode products O x_k X_s of the Sec. III
+// exchange; they depend on the table only, not on the Fermi radius (h <= R_F <= R).
+__global__ void k_windows(const double* Tm64, const double* Dbar64, int S_eff, int Mg, int R,
+                          int periodic, double* FW64, float* FW32, double* FDb64,
+                          float* FDb32) {
+  const int nh = R + 1;
+  const long long n = (long long)(S_eff + 1) * Mg * nh;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(i % nh);
+    const long long r = i / nh;
+    const int a = (int)(r % Mg), s = (int)(r / Mg);
+    const bool bar = s == S_eff;
+    const double* X = bar ? Dbar64 + (long long)a * Mg : Tm64 + ((long long)s * Mg + a) * Mg;
+    double acc = 0.0;
+    for (int k = R - h; k <= R + h; ++k)
+      if (bar || !periodic || k != a) acc += X[k];
+    if (bar) {
+      FDb64[a * nh + h] = acc;
+      FDb32[a * nh + h] = (float)acc;
+    } else {
+      FW64[i] = acc;
+      FW32[i] = (float)acc;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host helpers
 // Host copy of the node set of a mesh (same construction as k_mesh_nodes).
 static void host_mesh(int S, int n_sub, int q_tail, double alpha_c, double ratio,
@@ -427,7 +457,7 @@ static void free_tables(cc_tables t) {
   DevTables& d = t->d;
   void* ptrs[] = {d.T64, d.w64, d.a64, d.sep64, d.sep32, d.Vm64, d.Vm32, d.basis, d.idhint,
                   d.Tm64, d.WDm64, d.Dbar64, d.Tm32, d.WDm32, d.Dbar32,
-                  d.G64, d.sepG64, d.sepG32};
+                  d.FW64, d.FW32, d.FDb64, d.FDb32, d.G64, d.sepG64, d.sepG32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   d = DevTables();
@@ -499,6 +529,16 @@ static cc_status build_derived(cc_tables t, cudaStream_t st) {
   k_toeplitz<<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(d.T64, d.w64, S_eff, Dmax, Mg, periodic,
                                                            d.Tm64, d.WDm64, d.Tm32, d.WDm32);
   k_dbar<<<(Mg * Mg + 255) / 256, 256, 0, st>>>(d.WDm64, S_eff, Mg, d.Dbar64, d.Dbar32);
+  if (Mg <= kFusedMaxMg) {
+    const size_t nh = (size_t)t->p.R + 1;
+    CC_TRY(dmalloc(t, &d.FW64, (size_t)S_eff * Mg * nh));
+    CC_TRY(dmalloc(t, &d.FW32, (size_t)S_eff * Mg * nh));
+    CC_TRY(dmalloc(t, &d.FDb64, (size_t)Mg * nh));
+    CC_TRY(dmalloc(t, &d.FDb32, (size_t)Mg * nh));
+    const long long n = (long long)(S_eff + 1) * Mg * nh;
+    k_windows<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
+        d.Tm64, d.Dbar64, S_eff, Mg, t->p.R, periodic, d.FW64, d.FW32, d.FDb64, d.FDb32);
+  }
   CC_CUDA(cudaGetLastError());
   std::vector<int8_t> b = make_basis(t->p.R);
   CC_TRY(dmalloc(t, &d.basis, b.size()));
