@@ -53,7 +53,7 @@ struct BoxIn {
   long long eps_off;
 };
 
-constexpr int kMaxGroups = 16;
+constexpr int kMaxGroups = kFusedMaxGroups;
 
 // Build a plan: about slots x oversub items in total, shared among the boxes in
 // proportion to their cost Mg^4 S; a box gets Mg slabs x n_groups node groups

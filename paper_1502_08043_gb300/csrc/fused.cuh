@@ -47,6 +47,7 @@ struct FusedItem {
 };
 
 constexpr int kFusedThreads = 128;
+constexpr int kFusedMaxGroups = 16;  // node groups per box at most
 
 // shared-memory layout of one item (Mg = 2R + 1 = the box's grid side, mm = Mg * Mg):
 //   T      sT[mm], sR[mm], sU[mm], sE[mm], sC[mm]
@@ -185,10 +186,16 @@ __global__ void __launch_bounds__(kFusedThreads)
       double acc = 0.0;
       const long long base = (long long)x * mm;
       for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+        // every group's partial in flight at once, then added in group order
+        T pv[kFusedMaxGroups];
+#pragma unroll
+        for (int g = 0; g < kFusedMaxGroups; ++g)
+          pv[g] = g < bx.n_groups ? __ldcg(bx.part + (long long)g * G3 + base + i) : T(0);
         T sum = T(0), cmp = T(0);
-        for (int g = 0; g < bx.n_groups; ++g) {
-          const T v = __ldcg(bx.part + (long long)g * G3 + base + i);
-          const T yv = v - cmp;
+#pragma unroll
+        for (int g = 0; g < kFusedMaxGroups; ++g) {
+          if (g >= bx.n_groups) break;
+          const T yv = pv[g] - cmp;
           const T t = sum + yv;
           cmp = (t - sum) - yv;
           sum = t;
@@ -212,12 +219,16 @@ __global__ void __launch_bounds__(kFusedThreads)
         s_last = (atomicAdd(done + item.box, 1) == Mg - 1);
       }
       __syncthreads();
-      if (s_last && threadIdx.x == 0) {
+      if (s_last) {  // the box's last slab: its shares read at once, added in slab order
         __threadfence();
-        double tot = 0.0;
-        for (int k = 0; k < Mg; ++k) tot += __ldcg(bx.slab_ex + k);
-        ex_out[2 * bx.ex_idx] = 0.5 * tot;
-        ex_out[2 * bx.ex_idx + 1] = tot;
+        for (int k = threadIdx.x; k < Mg; k += blockDim.x) s_red[k] = __ldcg(bx.slab_ex + k);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tot = 0.0;
+          for (int k = 0; k < Mg; ++k) tot += s_red[k];
+          ex_out[2 * bx.ex_idx] = 0.5 * tot;
+          ex_out[2 * bx.ex_idx + 1] = tot;
+        }
       }
     }
     __syncthreads();
