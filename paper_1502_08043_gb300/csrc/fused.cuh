@@ -46,7 +46,7 @@ struct FusedItem {
   int box, x, s0, s1, g;
 };
 
-constexpr int kFusedThreads = 128;
+constexpr int kFusedThreads = 256;
 constexpr int kFusedMaxGroups = 16;  // node groups per box at most
 
 // shared-memory layout of one item (Mg = 2R + 1 = the box's grid side, mm = Mg * Mg):
