@@ -278,11 +278,12 @@ cc_status cc_exchange_sums(cc_tables t, int R_F, int precision, void* eps_dev, d
  * the process exits) and calls no cudaMalloc, cudaFree or allocating library routine.
  * Limit: R <= 31 (grid side 63); larger handles get CC_ERR_RANGE.  The handle's device
  * must be the current device (CC_ERR_ARG otherwise).
- * The first call on a device looks up that device's address of the array
- * (cudaGetSymbolAddress, device current) and caches it for the rest of the process: the
- * cache assumes the device's primary context lives as long as the process (after a
- * cudaDeviceReset the cached address is stale).  Make that first call before any stream
- * capture.  Every call shares the array and leaves the last call's contents in it:
+ * Building or loading a handle of R <= 31 looks up the device's address of the array
+ * (cudaGetSymbolAddress, device current), which under CUDA's lazy module loading is what
+ * allocates it, and loads the chain's kernels, so that the calls themselves do neither;
+ * the address is cached for the rest of the process (the cache assumes the device's
+ * primary context lives as long as the process: after a cudaDeviceReset it is stale).
+ * Every call shares the array and leaves the last call's contents in it:
  * calls that overlap on the GPU (any device-side overlap, on any stream, from any
  * thread) race and must be ordered by the caller. */
 cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_dev, double* Ex_dev,

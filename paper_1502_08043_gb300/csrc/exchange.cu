@@ -518,6 +518,28 @@ static cc_status noalloc_scratch(cc_tables t, void** out) {
   *out = p;
   return CC_OK;
 }
+
+// Called when a handle is built, where allocating is allowed.  With lazy module loading
+// (the CUDA default) the first use of this file's module allocates the scratch array and
+// loads the kernels; an allocation-free call that came first would pay for both.  So the
+// array's address is resolved and the FP32 chain's kernels are loaded here.  Best effort:
+// a failure leaves the lookup to the first call and clears the error.
+void noalloc_preload(cc_tables t) {
+  if (t->p.R > kNoAllocMaxR) return;
+  void* p = nullptr;
+  if (noalloc_scratch(t, &p) != CC_OK) {
+    (void)cudaGetLastError();
+    return;
+  }
+  const void* kernels[] = {(const void*)k_occ<float>, (const void*)k_gemm<float, 32, 32, 64>,
+                           (const void*)k_gemm<float, 64, 32, 128>,
+                           (const void*)k_gemm<float, 64, 64, 256>,
+                           (const void*)k_finalize<float, float>, (const void*)k_reduce_ex};
+  for (const void* k : kernels) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, k) != cudaSuccess) (void)cudaGetLastError();
+  }
+}
 }  // namespace cc
 
 extern "C" cc_status cc_exchange_sums_noalloc(cc_tables t, int R_F, float* eps_dev,

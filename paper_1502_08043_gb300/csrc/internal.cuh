@@ -123,6 +123,7 @@ cc_status build_tables_internal(const cc_table_params* params, cudaStream_t st,
                                 bool workspaces, cc_tables* out);
 // batched.cu
 cc_status fused_single_alloc(cc_tables t);
+void noalloc_preload(cc_tables t);  // exchange.cu: the allocation-free path's module
 void fused_single_free(cc_tables t);
 cc_status fused_single_exchange(cc_tables t, int R_F, int precision, void* eps, double* Ex,
                                 cudaStream_t st);

@@ -655,6 +655,7 @@ static cc_status build_impl(const cc_table_params* params, cudaStream_t st, cc_t
     CC_TRY(workspace_alloc(t));
     if (t->Mg <= 128) CC_TRY(mixed_workspace_alloc(t));
     CC_TRY(fused_single_alloc(t));
+    noalloc_preload(t);
     CC_TRY(simt_slab_alloc(t, &t->simt));
   }
   return CC_OK;
@@ -1020,6 +1021,7 @@ cc_status cc_tables_load(const char* path, void* stream, cc_tables* out) {
     if (s == CC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = CC_ERR_CUDA;
     if (s == CC_OK && t->Mg <= 128) s = mixed_workspace_alloc(t);
     if (s == CC_OK) s = fused_single_alloc(t);
+    if (s == CC_OK) noalloc_preload(t);
     if (s == CC_OK) s = simt_slab_alloc(t, &t->simt);
   }
   if (s != CC_OK) {
